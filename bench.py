@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched in-line atomistic EOS evaluation.
+
+One step = one pass of the whole hot path (lifting, MD, restriction) over the
+batched uneven workload: 4096 Lennard-Jones boxes, N = 4n^3 with n ~ U{3..10},
+rho* ~ U[0.3, 1.2], T* log-uniform on [0.7, 3.0], 1000 lifting + 1000 production
+steps, run as one persistent kernel inside one CUDA graph launch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own full batch
+(independent boxes, weak scaling, no data-path collective); timings are the max over
+ranks.  `--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_PAIR = 27  # nominal FP32 flops per in-cutoff pair
+WORKLOAD = ("batched uneven MD-EOS: 4096 LJ boxes, N=4n^3 n~U{3..10} (108-4000 atoms), "
+            "rho*~U[0.3,1.2], T*~logU[0.7,3.0], rc=2.5, dt=0.005, 1000 lifting + 1000 "
+            "production steps, one persistent graph-captured launch")
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [t.strip() for t in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a per-rank float over all ranks (1 rank: identity)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def gpu_requests(m, boxes):
+    return [dict(rho=b["rho"], e=m.e_from_temperature(b["T"], b["natoms"]), natoms=b["natoms"],
+                 steps_equil=b["steps_equil"], steps_avg=b["steps_avg"], seed=b["seed"],
+                 element_id=b["element_id"]) for b in boxes]
+
+
+def cpu_sample(per_class=2, steps_equil=100, steps_avg=100):
+    """Bounded sample of the workload for the CPU oracle: 2 boxes of every atom
+    count with 200 of the 2000 steps; EOS/s is scaled by the step fraction."""
+    from paper_2508_06012_gb300 import workloads as w
+    boxes = w.stratified(w.config2(), per_class, steps_equil, steps_avg)
+    frac = (steps_equil + steps_avg) / 2000.0
+    desc = (f"{len(boxes)} boxes ({per_class} per atom count 108..4000) x "
+            f"{steps_equil + steps_avg} of 2000 steps, FP64 linked-cell oracle, OpenMP")
+    return boxes, frac, desc
+
+
+def run_cpu_sample(orc, boxes, nthreads=0):
+    reqs = [dict(rho=b["rho"], e=orc.e_from_temperature(b["T"], b["natoms"]),
+                 natoms=b["natoms"], steps_equil=b["steps_equil"], steps_avg=b["steps_avg"],
+                 seed=b["seed"]) for b in boxes]
+    t0 = time.perf_counter()
+    res = orc.eos_batch(reqs, orc.make_params(force_mode=orc.FORCE_CELL), nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    assert all(r["status"] == 0 for r in res)
+    return dt
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle timed on this host's cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as orc
+    orc.build()
+    boxes, frac, desc = cpu_sample()
+    for _ in range(args.warmup):
+        run_cpu_sample(orc, boxes)
+    times = [run_cpu_sample(orc, boxes) for _ in range(args.steps)]
+    t = float(np.mean(times))
+    value = len(boxes) * frac / t
+    cores = orc.max_threads()
+    line = {
+        "metric": "MD-EOS evals/s", "value": value, "unit": "EOS/s", "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "EOS/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "EOS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ours(args):
+    import torch
+
+    import paper_2508_06012_gb300 as m
+    from paper_2508_06012_gb300 import workloads as w
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    m.build()
+    boxes = w.config2(base_seed=20250807 + rank)
+    reqs = gpu_requests(m, boxes)
+    nbox = len(reqs)
+    h = m.mdeos_create(m.mdeos_config_default(device=local))
+    b = m.mdeos_batch_create(h, reqs)
+    info = m.mdeos_batch_info(b)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def launch():
+        m.mdeos_batch_launch(b, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        launch()
+    torch.cuda.synchronize()
+    res = m.mdeos_batch_results(b, nbox)
+    assert (res["status"] == 0).all(), np.unique(res["status"], return_counts=True)
+    total_steps = np.array([r["steps_equil"] + r["steps_avg"] for r in reqs], dtype=np.float64)
+    pairs_per_launch = float((res["pairs_per_step"] * total_steps).sum())
+    cand_per_launch = float((res["cand_per_step"] * total_steps).sum())
+
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+    clocks = ClockSampler(gpu_idx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))  # evict L2 between timed iterations (outside the events)
+            ev[k][0].record(stream)
+            launch()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    kms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    dev_ms = float(np.sum(kms))
+    dev_ms_max = max_over_ranks(dev_ms, world)
+    value = nbox * args.steps * world / (dev_ms_max / 1000.0)
+    ms_per_step = dev_ms_max / args.steps
+    kernel_s = float(np.mean(kms)) / 1000.0
+
+    # end to end through the public API with host buffers (copies inside the region)
+    e2e = None
+    if not args.no_e2e:
+        arr = m.as_requests(reqs)
+        barrier(world)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            t = m.mdeos_submit(h, arr)
+            out = m.mdeos_poll(h, t, nbox, -1)
+        e2e_s = time.perf_counter() - t1
+        e2e_s = max_over_ranks(e2e_s, world)
+        st = m.mdeos_stats(h)
+        assert (out["status"] == 0).all()
+        e2e = {"value": nbox * args.steps * world / e2e_s, "unit": "EOS/s",
+               "h2d_bytes_per_step": int(st["h2d"]), "d2h_bytes_per_step": int(st["d2h"]),
+               "api": "mdeos_submit + mdeos_poll (host request/result arrays)"}
+
+    peaks = load_peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    fmax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = nsm * 128 * 2 * fmax * 1e6 / 1e12
+    achieved = pairs_per_launch * FLOPS_PER_PAIR / kernel_s / 1e12
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+        "frac": achieved / peak_tflops, "traffic": None,
+        "kernel": "eos_batch_kernel",
+        "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flop x {fmax:.0f} MHz (max SM clock)",
+        "flops_basis": f"{FLOPS_PER_PAIR} flop x in-cutoff ordered pairs counted in this run",
+        "pairs_per_launch": pairs_per_launch, "candidates_per_launch": cand_per_launch,
+    }
+    if clk.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = achieved / (nsm * 256 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as orc
+        orc.build()
+        sboxes, frac, desc = cpu_sample()
+        t = run_cpu_sample(orc, sboxes)
+        v = len(sboxes) * frac / t
+        cpu = {"value": v, "unit": "EOS/s", "cores": orc.max_threads(), "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "MD-EOS evals/s", "value": value, "unit": "EOS/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded LJ boxes; no datasets or trained weights)",
+            "config": {"workload": WORKLOAD, "boxes_per_gpu": nbox,
+                       "l2": "flushed between timed iterations (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world} (independent boxes)",
+                       "plan": info},
+            "pairs_per_s": pairs_per_launch * args.steps * world / (dev_ms_max / 1000.0),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps, "clocks": clk, "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    m.mdeos_batch_destroy(b)
+    m.mdeos_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,311 @@
+"""GB300-native batched in-line atomistic EOS evaluation (arXiv 2508.06012, Sec. III).
+
+Thin Python binding over the C ABI in ``include/mdeos.h``: ctypes marshalling only.
+Every step of the lifting -> MD -> restriction path runs in the CUDA library
+``libmdeos.so`` (built for sm_103a by :func:`build`).  There is no CPU fallback: if
+the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdeos.so")
+
+MDEOS_OK, MDEOS_PENDING = 0, 1
+MDEOS_EINVAL, MDEOS_ENOMEM, MDEOS_EUNPHYS, MDEOS_EBOX = -1, -2, -3, -4
+MDEOS_ETIMEDOUT, MDEOS_ECUDA, MDEOS_ECANCELLED, MDEOS_ENBR = -5, -6, -7, -8
+MDEOS_REF_ECOLD, MDEOS_REF_FIXED = 0, 1
+MDEOS_REQ_TEMPERATURE = 1
+PATH_ALLPAIRS, PATH_ALLPAIRS_MI, PATH_NLIST = 0, 1, 2
+
+EXPORTED = [
+    "mdeos_config_default", "mdeos_create", "mdeos_submit", "mdeos_poll", "mdeos_destroy",
+    "mdeos_last_error", "mdeos_batch_create", "mdeos_batch_launch",
+    "mdeos_batch_device_results", "mdeos_batch_results", "mdeos_batch_destroy",
+    "mdeos_batch_info", "mdeos_stats", "mdeos_debug_lift", "mdeos_debug_forces",
+    "mdeos_debug_md",
+]
+
+
+class mdeos_config(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int32), ("lift_iters", ctypes.c_int32),
+        ("rescale_every_equil", ctypes.c_int32), ("rescale_every_avg", ctypes.c_int32),
+        ("se_blocks", ctypes.c_int32), ("energy_ref_mode", ctypes.c_int32),
+        ("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("mass", ctypes.c_double),
+        ("rc", ctypes.c_double), ("dt", ctypes.c_double), ("skin", ctypes.c_double),
+        ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class mdeos_request(ctypes.Structure):
+    _fields_ = [
+        ("rho", ctypes.c_double), ("e", ctypes.c_double), ("e_ref", ctypes.c_double),
+        ("natoms", ctypes.c_int32), ("steps_equil", ctypes.c_int32),
+        ("steps_avg", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64), ("element_id", ctypes.c_uint64),
+    ]
+
+
+class mdeos_result(ctypes.Structure):
+    _fields_ = [
+        ("P", ctypes.c_double), ("T", ctypes.c_double), ("sigma", ctypes.c_double * 6),
+        ("epot", ctypes.c_double), ("ekin", ctypes.c_double), ("e_achieved", ctypes.c_double),
+        ("P_se", ctypes.c_double), ("T_se", ctypes.c_double), ("T_target", ctypes.c_double),
+        ("e_cold", ctypes.c_double), ("L", ctypes.c_double), ("pairs_per_step", ctypes.c_double),
+        ("cand_per_step", ctypes.c_double), ("element_id", ctypes.c_uint64),
+        ("natoms", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("nlist_builds", ctypes.c_int32), ("path", ctypes.c_int32),
+    ]
+
+
+RESULT_DTYPE = np.dtype([
+    ("P", "f8"), ("T", "f8"), ("sigma", "f8", (6,)), ("epot", "f8"), ("ekin", "f8"),
+    ("e_achieved", "f8"), ("P_se", "f8"), ("T_se", "f8"), ("T_target", "f8"),
+    ("e_cold", "f8"), ("L", "f8"), ("pairs_per_step", "f8"), ("cand_per_step", "f8"),
+    ("element_id", "u8"), ("natoms", "i4"), ("status", "i4"), ("nlist_builds", "i4"),
+    ("path", "i4"),
+])
+REQUEST_DTYPE = np.dtype([
+    ("rho", "f8"), ("e", "f8"), ("e_ref", "f8"), ("natoms", "i4"), ("steps_equil", "i4"),
+    ("steps_avg", "i4"), ("flags", "u4"), ("seed", "u8"), ("element_id", "u8"),
+])
+assert RESULT_DTYPE.itemsize == ctypes.sizeof(mdeos_result)
+assert REQUEST_DTYPE.itemsize == ctypes.sizeof(mdeos_request)
+
+
+class MdeosError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mdeos status {status}: {msg}")
+        self.status = status
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library (nvcc, sm_103a) in-tree."""
+    from . import buildlib as _b
+    return _b.build(force=force, verbose=verbose)
+
+
+_lib = None
+
+
+def lib():
+    """Load libmdeos.so; raise if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MdeosError(MDEOS_ECUDA, f"{LIB_PATH} missing: run build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        L.mdeos_config_default.argtypes = [P(mdeos_config)]
+        L.mdeos_config_default.restype = None
+        L.mdeos_create.argtypes = [P(mdeos_config), P(vp)]
+        L.mdeos_submit.argtypes = [vp, vp, i32, P(ctypes.c_uint64)]
+        L.mdeos_poll.argtypes = [vp, ctypes.c_uint64, vp, i32]
+        L.mdeos_destroy.argtypes = [vp]
+        L.mdeos_last_error.restype = ctypes.c_char_p
+        L.mdeos_batch_create.argtypes = [vp, vp, i32, P(vp)]
+        L.mdeos_batch_launch.argtypes = [vp, vp]
+        L.mdeos_batch_device_results.argtypes = [vp]
+        L.mdeos_batch_device_results.restype = vp
+        L.mdeos_batch_results.argtypes = [vp, vp]
+        L.mdeos_batch_destroy.argtypes = [vp]
+        L.mdeos_batch_info.argtypes = [vp, P(i32), P(i32), P(i32), P(ctypes.c_size_t)]
+        L.mdeos_stats.argtypes = [vp, P(ctypes.c_size_t), P(ctypes.c_size_t),
+                                  P(ctypes.c_longlong), P(ctypes.c_size_t)]
+        L.mdeos_debug_lift.argtypes = [P(mdeos_config), i32, d, d, ctypes.c_uint64, vp, vp, vp,
+                                       P(d), vp]
+        L.mdeos_debug_forces.argtypes = [P(mdeos_config), vp, i32, d, i32, d, vp, vp, vp, vp]
+        L.mdeos_debug_md.argtypes = [P(mdeos_config), vp, vp, i32, d, i32, d, i32, i32, d, vp,
+                                     vp, vp]
+        for name in EXPORTED:
+            fn = getattr(L, name)
+            if name not in ("mdeos_config_default", "mdeos_last_error",
+                            "mdeos_batch_device_results"):
+                fn.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def mdeos_last_error() -> str:
+    return lib().mdeos_last_error().decode()
+
+
+def _check(st: int):
+    if st != MDEOS_OK:
+        raise MdeosError(st, mdeos_last_error())
+
+
+def mdeos_config_default(**over) -> mdeos_config:
+    c = mdeos_config()
+    lib().mdeos_config_default(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+def mdeos_create(cfg: mdeos_config | None = None) -> ctypes.c_void_p:
+    cfg = cfg or mdeos_config_default()
+    h = ctypes.c_void_p()
+    _check(lib().mdeos_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def mdeos_destroy(h) -> None:
+    _check(lib().mdeos_destroy(h))
+
+
+def as_requests(reqs) -> np.ndarray:
+    """Structured request array (REQUEST_DTYPE) from a list of dicts or an array."""
+    if isinstance(reqs, np.ndarray) and reqs.dtype == REQUEST_DTYPE:
+        return np.ascontiguousarray(reqs)
+    arr = np.zeros(len(reqs), dtype=REQUEST_DTYPE)
+    for k, r in enumerate(reqs):
+        for f in REQUEST_DTYPE.names:
+            if f in r:
+                arr[k][f] = r[f]
+    return arr
+
+
+def mdeos_submit(h, reqs) -> int:
+    arr = as_requests(reqs)
+    t = ctypes.c_uint64()
+    _check(lib().mdeos_submit(h, arr.ctypes.data_as(ctypes.c_void_p), len(arr), ctypes.byref(t)))
+    return t.value
+
+
+def mdeos_poll(h, ticket: int, n: int, timeout_us: int = -1):
+    """Results (RESULT_DTYPE array) or None while pending."""
+    out = np.zeros(n, dtype=RESULT_DTYPE)
+    st = lib().mdeos_poll(h, ticket, out.ctypes.data_as(ctypes.c_void_p), timeout_us)
+    if st == MDEOS_PENDING:
+        return None
+    _check(st)
+    return out
+
+
+def mdeos_batch_create(h, reqs) -> ctypes.c_void_p:
+    arr = as_requests(reqs)
+    b = ctypes.c_void_p()
+    _check(lib().mdeos_batch_create(h, arr.ctypes.data_as(ctypes.c_void_p), len(arr),
+                                    ctypes.byref(b)))
+    return b
+
+
+def mdeos_batch_launch(b, stream: int | None = None) -> None:
+    _check(lib().mdeos_batch_launch(b, ctypes.c_void_p(stream or 0)))
+
+
+def mdeos_batch_device_results(b) -> int:
+    return lib().mdeos_batch_device_results(b)
+
+
+def mdeos_batch_results(b, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=RESULT_DTYPE)
+    _check(lib().mdeos_batch_results(b, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def mdeos_batch_info(b) -> dict:
+    ni, nc, sm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    sc = ctypes.c_size_t()
+    _check(lib().mdeos_batch_info(b, ctypes.byref(ni), ctypes.byref(nc), ctypes.byref(sm),
+                                  ctypes.byref(sc)))
+    return {"items": ni.value, "ctas": nc.value, "smem": sm.value, "scratch_bytes": sc.value}
+
+
+def mdeos_batch_destroy(b) -> None:
+    _check(lib().mdeos_batch_destroy(b))
+
+
+def mdeos_stats(h) -> dict:
+    a, b, d = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    c = ctypes.c_longlong()
+    _check(lib().mdeos_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                             ctypes.byref(d)))
+    return {"h2d": a.value, "d2h": b.value, "launches": c.value, "device_bytes": d.value}
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    return ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+
+
+def mdeos_debug_lift(n: int, rho: float, T: float, seed: int, cfg: mdeos_config | None = None,
+                     stream=None):
+    """Device lifting of one box: (x4, v4 torch cuda float32 [n,4], E_cold, L)."""
+    import torch
+    cfg = cfg or mdeos_config_default()
+    x4 = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    v4 = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L = ctypes.c_double()
+    _check(lib().mdeos_debug_lift(ctypes.byref(cfg), n, rho, T, seed, _dptr(x4), _dptr(v4),
+                                  _dptr(e), ctypes.byref(L), _stream_ptr(stream)))
+    return x4, v4, float(e.item()), L.value
+
+
+def mdeos_debug_forces(x4, L: float, path: int, skin: float = 0.3,
+                       cfg: mdeos_config | None = None, stream=None):
+    """Device forces on positions x4 (torch cuda float32 [n,4]): (f4, ew[7], pairs)."""
+    import torch
+    cfg = cfg or mdeos_config_default()
+    n = x4.shape[0]
+    f4 = torch.zeros_like(x4)
+    ew = torch.zeros(7, dtype=torch.float64, device=x4.device)
+    pc = torch.zeros(1, dtype=torch.int64, device=x4.device)
+    _check(lib().mdeos_debug_forces(ctypes.byref(cfg), _dptr(x4), n, L, path, skin, _dptr(f4),
+                                    _dptr(ew), _dptr(pc), _stream_ptr(stream)))
+    return f4, ew, int(pc.item())
+
+
+def mdeos_debug_md(x4, v4, L: float, steps: int, path: int, skin: float = 0.3,
+                   T_target: float = 0.0, rescale_every: int = 0,
+                   cfg: mdeos_config | None = None, stream=None):
+    """Device velocity-Verlet on one box, in place; returns (epot[steps], ekin[steps])."""
+    import torch
+    cfg = cfg or mdeos_config_default()
+    n = x4.shape[0]
+    ep = torch.zeros(max(steps, 1), dtype=torch.float64, device=x4.device)
+    ek = torch.zeros(max(steps, 1), dtype=torch.float64, device=x4.device)
+    _check(lib().mdeos_debug_md(ctypes.byref(cfg), _dptr(x4), _dptr(v4), n, L, steps, T_target,
+                                rescale_every, path, skin, _dptr(ep), _dptr(ek),
+                                _stream_ptr(stream)))
+    return ep[:steps], ek[:steps]
+
+
+def e_from_temperature(T, natoms):
+    """Specific energy whose first lifting temperature (Eq. 9) is T: e = N_DOF T / (2N)."""
+    return (3.0 * natoms - 3.0) * T / (2.0 * natoms)
+
+
+class Engine:
+    """Convenience wrapper: one handle, synchronous evaluate()."""
+
+    def __init__(self, **cfg):
+        self.cfg = mdeos_config_default(**cfg)
+        self.h = mdeos_create(self.cfg)
+
+    def evaluate(self, reqs, timeout_us: int = -1) -> np.ndarray:
+        arr = as_requests(reqs)
+        t = mdeos_submit(self.h, arr)
+        return mdeos_poll(self.h, t, len(arr), timeout_us)
+
+    def close(self):
+        if self.h:
+            mdeos_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,818 @@
+// Host engine behind the C ABI (include/mdeos.h): request validation, the
+// packing planner (size classes, warps per box, box-to-CTA packing, LPT
+// ordering of the work queue), ticketed submit/poll, device-resident batches
+// replayed as CUDA graphs, and the single-box parity entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "mdeos_internal.h"
+
+namespace mdeos {
+cudaError_t set_batch_attributes(int max_smem);
+cudaError_t launch_eos_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int* counter,
+                             mdeos_result* results, uint16_t* nl, long long nl_elems_per_cta,
+                             const RunParams& rp, int grid, int smem, cudaStream_t st);
+cudaError_t set_debug_attributes(int max_smem);
+cudaError_t launch_debug_lift(const BoxDesc& bd, const RunParams& rp, double T, int apt,
+                              int ncell_cap, int smem, float4* x4, float4* v4, double* e_out,
+                              uint16_t* nl, cudaStream_t st);
+cudaError_t launch_debug_forces(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
+                                int smem, const float4* x4, float4* f4, double* ew,
+                                long long* pairs, uint16_t* nl, cudaStream_t st);
+cudaError_t launch_debug_md(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
+                            int smem, float4* x4, float4* v4, int steps, double T, int every,
+                            double* ep, double* ek, uint16_t* nl, cudaStream_t st);
+}  // namespace mdeos
+
+using namespace mdeos;
+
+// ---------------------------------------------------------------------------
+// errors
+
+static thread_local std::string g_last_error = "";
+
+static mdeos_status fail(mdeos_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+static mdeos_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return MDEOS_ECUDA;
+}
+
+#define CK(call)                                                 \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+  } while (0)
+
+extern "C" const char* mdeos_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// configuration
+
+extern "C" void mdeos_config_default(mdeos_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->device = 0;
+  c->lift_iters = 2;
+  c->rescale_every_equil = 0;
+  c->rescale_every_avg = 10;
+  c->se_blocks = 10;
+  c->energy_ref_mode = MDEOS_REF_ECOLD;
+  c->eps = 1.0;
+  c->sigma = 1.0;
+  c->mass = 1.0;
+  c->rc = 2.5;
+  c->dt = 0.005;
+  c->skin = 0.0;
+  c->hbm_budget_bytes = 0;
+  c->cuda_stream = nullptr;
+}
+
+static mdeos_status check_config(const mdeos_config* c) {
+  if (!c) return fail(MDEOS_EINVAL, "config is NULL");
+  if (!(c->eps > 0) || !(c->sigma > 0) || !(c->mass > 0) || !(c->rc > 0) || !(c->dt > 0))
+    return fail(MDEOS_EINVAL, "eps, sigma, mass, rc and dt must be > 0");
+  if (c->lift_iters < 0 || c->lift_iters > 64) return fail(MDEOS_EINVAL, "lift_iters out of range");
+  if (c->se_blocks < 2 || c->se_blocks > kMaxSeBlocks)
+    return fail(MDEOS_EINVAL, "se_blocks must be in 2..32");
+  if (c->rescale_every_equil < 0 || c->rescale_every_avg < 0)
+    return fail(MDEOS_EINVAL, "rescale periods must be >= 0");
+  if (c->energy_ref_mode != MDEOS_REF_ECOLD && c->energy_ref_mode != MDEOS_REF_FIXED)
+    return fail(MDEOS_EINVAL, "energy_ref_mode must be REF_ECOLD or REF_FIXED");
+  if (c->skin > 2.0 * c->rc) return fail(MDEOS_EINVAL, "skin larger than 2 rc");
+  return MDEOS_OK;
+}
+
+static RunParams make_run_params(const mdeos_config* c) {
+  RunParams rp;
+  double s6 = std::pow(c->sigma / c->rc, 6.0);
+  rp.eps4 = (float)(4.0 * c->eps);
+  rp.eps24 = (float)(24.0 * c->eps);
+  rp.sig6 = (float)std::pow(c->sigma, 6.0);
+  rp.rc2 = (float)(c->rc * c->rc);
+  rp.ucut = (float)(4.0 * c->eps * (s6 * s6 - s6));
+  rp.rc = (float)c->rc;
+  rp.dt = (float)c->dt;
+  rp.hdtm = (float)(0.5 * c->dt / c->mass);
+  rp.mass_f = (float)c->mass;
+  rp.mass = c->mass;
+  rp.lift_iters = c->lift_iters;
+  rp.rescale_every_equil = c->rescale_every_equil;
+  rp.rescale_every_avg = c->rescale_every_avg;
+  rp.se_blocks = c->se_blocks;
+  rp.ref_mode = c->energy_ref_mode;
+  return rp;
+}
+
+// ---------------------------------------------------------------------------
+// planner: one box
+
+struct BoxPlan {
+  BoxDesc bd;
+  int warps = 4, apt = 1;
+  int ncell = 1;
+  double cost = 0.0;
+  int status = MDEOS_OK;
+};
+
+static int round_apt(int a) { return a <= 1 ? 1 : (a <= 2 ? 2 : 4); }
+
+// Box side rounded to float so host (volume, pressure) and device (FP32
+// minimum image) simulate the same box.
+static double box_side(int n, double rho) { return (double)(float)std::cbrt((double)n / rho); }
+
+static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx) {
+  BoxPlan p;
+  BoxDesc& b = p.bd;
+  std::memset(&b, 0, sizeof(b));
+  b.rho = r.rho;
+  b.e = r.e;
+  b.e_ref = r.e_ref;
+  b.seed = r.seed;
+  b.element_id = r.element_id;
+  b.natoms = r.natoms;
+  b.steps_equil = r.steps_equil;
+  b.steps_avg = r.steps_avg;
+  b.flags = r.flags;
+  b.out_index = idx;
+  const int n = r.natoms;
+  const bool ok = n >= 2 && n <= kMaxAtoms && std::isfinite(r.rho) && r.rho > 0 &&
+                  std::isfinite(r.e) && std::isfinite(r.e_ref) && r.steps_avg >= c.se_blocks &&
+                  r.steps_equil >= 0 && (long long)r.steps_equil + r.steps_avg < (1LL << 30) &&
+                  (r.steps_equil == 0 || (c.lift_iters >= 1 && r.steps_equil >= c.lift_iters)) &&
+                  (r.flags & ~(uint32_t)MDEOS_REQ_TEMPERATURE) == 0;
+  if (!ok) {
+    p.status = MDEOS_EINVAL;
+    return p;
+  }
+  const double L = box_side(n, r.rho);
+  b.L = L;
+  int ncl = 1;
+  while (4LL * ncl * ncl * ncl < n) ++ncl;
+  b.nc_lat = ncl;
+  if (L < c.rc) {
+    p.status = MDEOS_EBOX;
+    return p;
+  }
+  const double steps = (double)r.steps_equil + r.steps_avg;
+  // path choice (autotuner defaults; a measured table can override per class)
+  double skin = c.skin > 0 ? c.skin : 0.3;
+  const double smax = 0.5 * L - c.rc;
+  if (L < 2.0 * c.rc) {
+    b.path = PATH_ALLPAIRS_MI;
+  } else if (n <= 128 || smax < 0.15) {
+    b.path = PATH_ALLPAIRS;
+  } else {
+    b.path = PATH_NLIST;
+    skin = std::min(skin, smax);
+  }
+  if (b.path == PATH_NLIST) {
+    b.skin = (float)skin;
+    const double rs = c.rc + skin;
+    int nc = (int)std::floor(L / rs);
+    while (nc > 3 && nc * nc * nc > kMaxCells) --nc;
+    b.nc_cell = nc >= 3 ? nc : 0;
+    p.ncell = nc >= 3 ? nc * nc * nc : 1;
+    const double expect = 4.18879020478639 * rs * rs * rs * r.rho;
+    int mx = (int)std::ceil(1.35 * expect + 24.0);
+    mx = std::min(mx, n - 1);
+    b.maxnb = (mx + 3) & ~3;
+    p.cost = steps * n * (expect * 1.0 + 8.0);
+  } else {
+    b.skin = 0.f;
+    b.nc_cell = 0;
+    b.maxnb = 0;
+    p.cost = steps * n * (double)n * (b.path == PATH_ALLPAIRS_MI ? 8.0 : 1.0) * 0.6;
+  }
+  // threads per box: at most 4 atoms per thread, at least 4 warps
+  int warps = 4;
+  while (warps < 32 && warps * 32 * 4 < n) warps *= 2;
+  p.warps = warps;
+  p.apt = round_apt((n + warps * 32 - 1) / (warps * 32));
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// planner: packing
+
+struct Plan {
+  std::vector<BoxDesc> boxes;
+  std::vector<WorkItem> items;
+  std::vector<int> status;  // per request: MDEOS_OK or the planning error
+  int smem = 0;
+  long long nl_per_cta = 0;
+  int grid = 0;
+};
+
+static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_config& c, int nsm,
+                              int smem_max, Plan& plan) {
+  plan.boxes.clear();
+  plan.items.clear();
+  plan.status.assign(n, MDEOS_OK);
+  std::vector<BoxPlan> bp;
+  bp.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    BoxPlan p = plan_box(reqs[i], c, i);
+    plan.status[i] = p.status;
+    if (p.status == MDEOS_OK) bp.push_back(p);
+  }
+  // size classes by (warps, apt); inside a class, sort by cost so an item's
+  // boxes finish together
+  std::sort(bp.begin(), bp.end(), [](const BoxPlan& a, const BoxPlan& b) {
+    if (a.warps != b.warps) return a.warps < b.warps;
+    if (a.apt != b.apt) return a.apt < b.apt;
+    return a.cost > b.cost;
+  });
+  struct ItemCost {
+    WorkItem wi;
+    double cost;
+  };
+  std::vector<ItemCost> items;
+  plan.smem = 0;
+  plan.nl_per_cta = 0;
+  size_t k = 0;
+  while (k < bp.size()) {
+    const int warps = bp[k].warps, apt = bp[k].apt;
+    const int npad = warps * 32 * apt;
+    const int per_cta = std::min(kCtaThreads / (warps * 32), kMaxBoxesPerItem);
+    // boxes of this class that share one item
+    WorkItem wi;
+    std::memset(&wi, 0, sizeof(wi));
+    wi.warps_per_box = warps;
+    wi.apt = apt;
+    int ncell_cap = 1, maxnb = 4;
+    double cost = 0.0;
+    int nb = 0;
+    while (k < bp.size() && bp[k].warps == warps && bp[k].apt == apt && nb < per_cta) {
+      const int nc2 = std::max(ncell_cap, bp[k].ncell);
+      const int stride = group_smem_bytes(warps, apt, nc2);
+      if ((nb + 1) * stride > smem_max) break;
+      ncell_cap = nc2;
+      maxnb = std::max(maxnb, bp[k].bd.maxnb);
+      wi.box[nb++] = (int)plan.boxes.size();
+      plan.boxes.push_back(bp[k].bd);
+      cost += bp[k].cost;
+      ++k;
+    }
+    if (nb == 0) return fail(MDEOS_EINVAL, "a box does not fit in shared memory");
+    wi.nbox = nb;
+    wi.ncell_cap = ncell_cap;
+    wi.smem_stride = group_smem_bytes(warps, apt, ncell_cap);
+    wi.nl_stride = ((maxnb + 3) & ~3) * npad;
+    plan.smem = std::max(plan.smem, nb * wi.smem_stride);
+    plan.nl_per_cta = std::max(plan.nl_per_cta, (long long)nb * wi.nl_stride);
+    items.push_back({wi, cost});
+  }
+  // longest-processing-time first
+  std::stable_sort(items.begin(), items.end(),
+                   [](const ItemCost& a, const ItemCost& b) { return a.cost > b.cost; });
+  for (auto& it : items) plan.items.push_back(it.wi);
+  plan.grid = std::max(1, std::min(nsm, (int)plan.items.size()));
+  return MDEOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// handle
+
+struct PinnedBlock {
+  void* p = nullptr;
+  size_t size = 0;
+};
+
+struct TicketState {
+  int n = 0;
+  cudaEvent_t done = nullptr;
+  void* d_mem = nullptr;      // boxes | items | results | counter
+  PinnedBlock h_in, h_out;
+  std::vector<int> status;    // planning status per request
+  std::vector<uint64_t> element_id;
+  std::vector<int> natoms;
+  bool any_device = false;
+  size_t bytes = 0;
+};
+
+struct mdeos_handle {
+  mdeos_config cfg;
+  RunParams rp;
+  int device = 0, nsm = 0, smem_max = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint16_t* d_nl = nullptr;
+  size_t nl_bytes = 0;
+  size_t used_bytes = 0;
+  uint64_t next_ticket = 1;
+  std::unordered_map<uint64_t, TicketState> tickets;
+  std::vector<PinnedBlock> pinned_free;
+  std::mutex mu;
+  // statistics of the last submit
+  size_t last_h2d = 0, last_d2h = 0;
+  long long launches = 0;
+};
+
+struct mdeos_batch {
+  mdeos_handle* h = nullptr;
+  int n = 0;
+  Plan plan;
+  void* d_mem = nullptr;
+  BoxDesc* d_boxes = nullptr;
+  WorkItem* d_items = nullptr;
+  mdeos_result* d_results = nullptr;
+  int* d_counter = nullptr;
+  uint16_t* d_nl = nullptr;
+  size_t bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<mdeos_result> init_results;
+};
+
+static mdeos_status pinned_get(mdeos_handle* h, size_t size, PinnedBlock& out) {
+  for (size_t i = 0; i < h->pinned_free.size(); ++i) {
+    if (h->pinned_free[i].size >= size) {
+      out = h->pinned_free[i];
+      h->pinned_free.erase(h->pinned_free.begin() + i);
+      return MDEOS_OK;
+    }
+  }
+  size_t sz = std::max<size_t>(size, 4096);
+  CK(cudaMallocHost(&out.p, sz));
+  out.size = sz;
+  return MDEOS_OK;
+}
+
+static void pinned_put(mdeos_handle* h, PinnedBlock& b) {
+  if (b.p) h->pinned_free.push_back(b);
+  b.p = nullptr;
+  b.size = 0;
+}
+
+static mdeos_status ensure_scratch(mdeos_handle* h, size_t bytes) {
+  if (bytes <= h->nl_bytes) return MDEOS_OK;
+  const size_t extra = bytes - h->nl_bytes;
+  if (h->cfg.hbm_budget_bytes && h->used_bytes + extra > h->cfg.hbm_budget_bytes)
+    return fail(MDEOS_ENOMEM, "neighbour-list scratch exceeds the HBM budget");
+  if (h->d_nl) {
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaFree(h->d_nl));
+    h->used_bytes -= h->nl_bytes;
+    h->d_nl = nullptr;
+    h->nl_bytes = 0;
+  }
+  CK(cudaMalloc(&h->d_nl, bytes));
+  h->nl_bytes = bytes;
+  h->used_bytes += bytes;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_create(const mdeos_config* cfg, mdeos_handle** out) {
+  if (!out) return fail(MDEOS_EINVAL, "out is NULL");
+  *out = nullptr;
+  mdeos_status st = check_config(cfg);
+  if (st != MDEOS_OK) return st;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return fail(MDEOS_ECUDA, "no CUDA device available");
+  if (cfg->device < 0 || cfg->device >= ndev) return fail(MDEOS_EINVAL, "device out of range");
+  mdeos_handle* h = new mdeos_handle();
+  h->cfg = *cfg;
+  h->rp = make_run_params(cfg);
+  h->device = cfg->device;
+  e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaSetDevice");
+  }
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
+  cudaDeviceGetAttribute(&h->smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  h->smem_max -= 1024;  // static shared memory of the kernels
+  e = set_batch_attributes(h->smem_max);
+  if (e == cudaSuccess) e = set_debug_attributes(h->smem_max);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "kernel attributes (is this an sm_103 GPU?)");
+  }
+  if (cfg->cuda_stream) {
+    h->stream = (cudaStream_t)cfg->cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    h->own_stream = true;
+  }
+  *out = h;
+  return MDEOS_OK;
+}
+
+static void release_ticket(mdeos_handle* h, TicketState& t) {
+  if (t.done) cudaEventDestroy(t.done);
+  if (t.d_mem) cudaFreeAsync(t.d_mem, h->stream);
+  h->used_bytes -= t.bytes;
+  pinned_put(h, t.h_in);
+  pinned_put(h, t.h_out);
+}
+
+extern "C" mdeos_status mdeos_destroy(mdeos_handle* h) {
+  if (!h) return MDEOS_OK;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->tickets) release_ticket(h, kv.second);
+  h->tickets.clear();
+  cudaStreamSynchronize(h->stream);
+  for (auto& b : h->pinned_free) cudaFreeHost(b.p);
+  if (h->d_nl) cudaFree(h->d_nl);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return MDEOS_OK;
+}
+
+// fill results of requests rejected by the planner
+static void planning_result(mdeos_result& r, int status, const mdeos_request& q) {
+  std::memset(&r, 0, sizeof(r));
+  r.status = status;
+  r.natoms = q.natoms;
+  r.element_id = q.element_id;
+  r.path = -1;
+}
+
+extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs, int32_t n,
+                                     uint64_t* ticket) {
+  if (!h || !reqs || !ticket || n < 1) return fail(MDEOS_EINVAL, "bad submit arguments");
+  std::lock_guard<std::mutex> lock(h->mu);
+  CK(cudaSetDevice(h->device));
+  Plan plan;
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan);
+  if (st != MDEOS_OK) return st;
+  TicketState t;
+  t.n = n;
+  t.status = plan.status;
+  t.element_id.resize(n);
+  t.natoms.resize(n);
+  for (int i = 0; i < n; ++i) {
+    t.element_id[i] = reqs[i].element_id;
+    t.natoms[i] = reqs[i].natoms;
+  }
+  const size_t nb = plan.boxes.size(), ni = plan.items.size();
+  const size_t off_items = (nb * sizeof(BoxDesc) + 255) & ~size_t(255);
+  const size_t in_bytes = off_items + ni * sizeof(WorkItem);
+  const size_t off_res = (in_bytes + 255) & ~size_t(255);
+  const size_t off_cnt = off_res + (((size_t)n * sizeof(mdeos_result) + 255) & ~size_t(255));
+  const size_t dev_bytes = off_cnt + 256;
+  if (h->cfg.hbm_budget_bytes && h->used_bytes + dev_bytes > h->cfg.hbm_budget_bytes)
+    return fail(MDEOS_ENOMEM, "batch exceeds the HBM budget");
+  if ((st = pinned_get(h, in_bytes, t.h_in)) != MDEOS_OK) return st;
+  if ((st = pinned_get(h, (size_t)n * sizeof(mdeos_result), t.h_out)) != MDEOS_OK) {
+    pinned_put(h, t.h_in);
+    return st;
+  }
+  std::memcpy(t.h_in.p, plan.boxes.data(), nb * sizeof(BoxDesc));
+  std::memcpy((char*)t.h_in.p + off_items, plan.items.data(), ni * sizeof(WorkItem));
+  t.any_device = nb > 0;
+  h->last_h2d = 0;
+  h->last_d2h = 0;
+  if (t.any_device) {
+    const size_t scratch = (size_t)plan.grid * plan.nl_per_cta * sizeof(uint16_t);
+    if ((st = ensure_scratch(h, scratch)) != MDEOS_OK) {
+      pinned_put(h, t.h_in);
+      pinned_put(h, t.h_out);
+      return st;
+    }
+    cudaError_t e = cudaMallocAsync(&t.d_mem, dev_bytes, h->stream);
+    if (e != cudaSuccess) {
+      pinned_put(h, t.h_in);
+      pinned_put(h, t.h_out);
+      return cuda_fail(e, "cudaMallocAsync");
+    }
+    t.bytes = dev_bytes;
+    h->used_bytes += dev_bytes;
+    char* d = (char*)t.d_mem;
+    CK(cudaMemcpyAsync(d, t.h_in.p, in_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream));
+    e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni, (int*)(d + off_cnt),
+                         (mdeos_result*)(d + off_res), h->d_nl, plan.nl_per_cta, h->rp, plan.grid,
+                         plan.smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "eos_batch_kernel launch");
+    h->launches += 1;
+    CK(cudaMemcpyAsync(t.h_out.p, d + off_res, (size_t)n * sizeof(mdeos_result),
+                       cudaMemcpyDeviceToHost, h->stream));
+    h->last_h2d = in_bytes;
+    h->last_d2h = (size_t)n * sizeof(mdeos_result);
+  }
+  CK(cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming));
+  CK(cudaEventRecord(t.done, h->stream));
+  const uint64_t id = h->next_ticket++;
+  h->tickets.emplace(id, std::move(t));
+  *ticket = id;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_poll(mdeos_handle* h, uint64_t ticket, mdeos_result* out,
+                                   int32_t timeout_us) {
+  if (!h || !out) return fail(MDEOS_EINVAL, "bad poll arguments");
+  std::unique_lock<std::mutex> lock(h->mu);
+  auto it = h->tickets.find(ticket);
+  if (it == h->tickets.end()) return fail(MDEOS_EINVAL, "unknown ticket");
+  cudaEvent_t ev = it->second.done;
+  lock.unlock();
+  cudaSetDevice(h->device);
+  cudaError_t e;
+  if (timeout_us < 0) {
+    e = cudaEventSynchronize(ev);
+  } else {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      e = cudaEventQuery(ev);
+      if (e != cudaErrorNotReady) break;
+      auto el = std::chrono::duration_cast<std::chrono::microseconds>(
+                    std::chrono::steady_clock::now() - t0)
+                    .count();
+      if (el >= timeout_us) return MDEOS_PENDING;
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  }
+  lock.lock();
+  it = h->tickets.find(ticket);
+  if (it == h->tickets.end()) return fail(MDEOS_EINVAL, "ticket released concurrently");
+  TicketState& t = it->second;
+  mdeos_status ret = MDEOS_OK;
+  if (e != cudaSuccess) {
+    ret = cuda_fail(e, "batch execution");
+  } else {
+    const mdeos_result* dev = (const mdeos_result*)t.h_out.p;
+    for (int i = 0; i < t.n; ++i) {
+      if (t.status[i] == MDEOS_OK) {
+        out[i] = dev[i];
+      } else {
+        mdeos_request q;
+        std::memset(&q, 0, sizeof(q));
+        q.natoms = t.natoms[i];
+        q.element_id = t.element_id[i];
+        planning_result(out[i], t.status[i], q);
+      }
+    }
+  }
+  release_ticket(h, t);
+  h->tickets.erase(it);
+  return ret;
+}
+
+// ---------------------------------------------------------------------------
+// device-resident batches
+
+extern "C" mdeos_status mdeos_batch_create(mdeos_handle* h, const mdeos_request* reqs, int32_t n,
+                                           mdeos_batch** out) {
+  if (!h || !reqs || !out || n < 1) return fail(MDEOS_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  std::lock_guard<std::mutex> lock(h->mu);
+  CK(cudaSetDevice(h->device));
+  mdeos_batch* b = new mdeos_batch();
+  b->h = h;
+  b->n = n;
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, b->plan);
+  if (st != MDEOS_OK) {
+    delete b;
+    return st;
+  }
+  const Plan& p = b->plan;
+  const size_t nb = p.boxes.size(), ni = p.items.size();
+  const size_t off_items = (nb * sizeof(BoxDesc) + 255) & ~size_t(255);
+  const size_t off_res = (off_items + ni * sizeof(WorkItem) + 255) & ~size_t(255);
+  const size_t off_cnt = off_res + (((size_t)n * sizeof(mdeos_result) + 255) & ~size_t(255));
+  const size_t off_nl = off_cnt + 256;
+  const size_t nl_bytes = (size_t)p.grid * p.nl_per_cta * sizeof(uint16_t);
+  const size_t total = off_nl + nl_bytes;
+  if (h->cfg.hbm_budget_bytes && h->used_bytes + total > h->cfg.hbm_budget_bytes) {
+    delete b;
+    return fail(MDEOS_ENOMEM, "batch exceeds the HBM budget");
+  }
+  cudaError_t e = cudaMalloc(&b->d_mem, total);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "cudaMalloc batch");
+  }
+  b->bytes = total;
+  h->used_bytes += total;
+  char* d = (char*)b->d_mem;
+  b->d_boxes = (BoxDesc*)d;
+  b->d_items = (WorkItem*)(d + off_items);
+  b->d_results = (mdeos_result*)(d + off_res);
+  b->d_counter = (int*)(d + off_cnt);
+  b->d_nl = (uint16_t*)(d + off_nl);
+  b->init_results.resize(n);
+  for (int i = 0; i < n; ++i) planning_result(b->init_results[i], p.status[i], reqs[i]);
+  CK(cudaMemcpy(b->d_boxes, p.boxes.data(), nb * sizeof(BoxDesc), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->d_items, p.items.data(), ni * sizeof(WorkItem), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->d_results, b->init_results.data(), (size_t)n * sizeof(mdeos_result),
+                cudaMemcpyHostToDevice));
+  // capture: reset the queue counter, run the persistent kernel
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
+  if (ni > 0)
+    launch_eos_batch(b->d_boxes, b->d_items, (int)ni, b->d_counter, b->d_results, b->d_nl,
+                     p.nl_per_cta, h->rp, p.grid, p.smem, cs);
+  e = cudaStreamEndCapture(cs, &b->graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    mdeos_batch_destroy(b);
+    return cuda_fail(e, "graph capture");
+  }
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    mdeos_batch_destroy(b);
+    return cuda_fail(e, "graph instantiate");
+  }
+  *out = b;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_batch_launch(mdeos_batch* b, void* stream) {
+  if (!b) return fail(MDEOS_EINVAL, "batch is NULL");
+  cudaStream_t s = stream ? (cudaStream_t)stream : b->h->stream;
+  CK(cudaSetDevice(b->h->device));
+  CK(cudaGraphLaunch(b->exec, s));
+  b->h->launches += b->plan.items.empty() ? 0 : 1;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_result* mdeos_batch_device_results(mdeos_batch* b) {
+  return b ? b->d_results : nullptr;
+}
+
+extern "C" mdeos_status mdeos_batch_results(mdeos_batch* b, mdeos_result* out) {
+  if (!b || !out) return fail(MDEOS_EINVAL, "bad batch_results arguments");
+  CK(cudaSetDevice(b->h->device));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(out, b->d_results, (size_t)b->n * sizeof(mdeos_result), cudaMemcpyDeviceToHost));
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_batch_info(const mdeos_batch* b, int32_t* n_items, int32_t* n_ctas,
+                                         int32_t* smem_bytes, size_t* scratch_bytes) {
+  if (!b) return fail(MDEOS_EINVAL, "batch is NULL");
+  if (n_items) *n_items = (int32_t)b->plan.items.size();
+  if (n_ctas) *n_ctas = b->plan.grid;
+  if (smem_bytes) *smem_bytes = b->plan.smem;
+  if (scratch_bytes) *scratch_bytes = (size_t)b->plan.grid * b->plan.nl_per_cta * sizeof(uint16_t);
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_batch_destroy(mdeos_batch* b) {
+  if (!b) return MDEOS_OK;
+  cudaSetDevice(b->h->device);
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_mem) cudaFree(b->d_mem);
+  b->h->used_bytes -= b->bytes;
+  delete b;
+  return MDEOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// single-box parity entry points
+
+static mdeos_status debug_setup(const mdeos_config* cfg, int n, double L, int path, double skin,
+                                BoxDesc& bd, RunParams& rp, int& apt, int& ncell, int& smem,
+                                size_t& nl_bytes) {
+  mdeos_status st = check_config(cfg);
+  if (st != MDEOS_OK) return st;
+  if (n < 2 || n > kMaxAtoms) return fail(MDEOS_EINVAL, "n must be in 2..4096");
+  if (!(L >= cfg->rc)) return fail(MDEOS_EBOX, "box side below the cutoff");
+  if (path < 0 || path > 2) return fail(MDEOS_EINVAL, "path must be 0, 1 or 2");
+  if (path == PATH_ALLPAIRS && L < 2 * cfg->rc)
+    return fail(MDEOS_EBOX, "all-pairs minimum image needs L >= 2 rc");
+  if (path == PATH_NLIST && (!(skin >= 0) || L < 2 * (cfg->rc + skin)))
+    return fail(MDEOS_EBOX, "Verlet list needs L >= 2 (rc + skin)");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return fail(MDEOS_ECUDA, "no CUDA device available");
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  smem_max -= 1024;
+  if (dev < 64 && !attr_done[dev]) {
+    CK(set_debug_attributes(smem_max));
+    attr_done[dev] = true;
+  }
+  rp = make_run_params(cfg);
+  std::memset(&bd, 0, sizeof(bd));
+  bd.natoms = n;
+  bd.L = L;
+  bd.path = path;
+  bd.skin = (float)skin;
+  int ncl = 1;
+  while (4LL * ncl * ncl * ncl < n) ++ncl;
+  bd.nc_lat = ncl;
+  apt = round_apt((n + kCtaThreads - 1) / kCtaThreads);
+  ncell = 1;
+  nl_bytes = 0;
+  if (path == PATH_NLIST) {
+    const double rs = cfg->rc + skin;
+    int nc = (int)std::floor(L / rs);
+    while (nc > 3 && nc * nc * nc > kMaxCells) --nc;
+    bd.nc_cell = nc >= 3 ? nc : 0;
+    ncell = nc >= 3 ? nc * nc * nc : 1;
+    bd.maxnb = std::max(4, ((n - 1) + 3) & ~3);  // room for every atom: no overflow in tests
+    nl_bytes = (size_t)bd.maxnb * kCtaThreads * apt * sizeof(uint16_t);
+  }
+  smem = group_smem_bytes(32, apt, ncell);
+  if (smem > smem_max) return fail(MDEOS_EINVAL, "box does not fit in shared memory");
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_debug_lift(const mdeos_config* cfg, int32_t n, double rho, double T,
+                                         uint64_t seed, float* x4, float* v4, double* e_out,
+                                         double* L_out, void* stream) {
+  if (!x4 || !v4 || !e_out || !(rho > 0) || !(T > 0)) return fail(MDEOS_EINVAL, "bad arguments");
+  const double L = box_side(n, rho);
+  if (L_out) *L_out = L;
+  const int path = (L < 2 * cfg->rc) ? PATH_ALLPAIRS_MI : PATH_ALLPAIRS;
+  BoxDesc bd;
+  RunParams rp;
+  int apt, ncell, smem;
+  size_t nlb;
+  mdeos_status st = debug_setup(cfg, n, L, path, 0.0, bd, rp, apt, ncell, smem, nlb);
+  if (st != MDEOS_OK) return st;
+  bd.seed = seed;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_debug_lift(bd, rp, T, apt, ncell, smem, (float4*)x4, (float4*)v4, e_out, nullptr, s));
+  CK(cudaStreamSynchronize(s));
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_debug_forces(const mdeos_config* cfg, const float* x4, int32_t n,
+                                           double L, int32_t path, double skin, float* f4,
+                                           double* ew, long long* pairs, void* stream) {
+  if (!x4 || !f4 || !ew) return fail(MDEOS_EINVAL, "bad arguments");
+  BoxDesc bd;
+  RunParams rp;
+  int apt, ncell, smem;
+  size_t nlb;
+  mdeos_status st = debug_setup(cfg, n, L, path, skin, bd, rp, apt, ncell, smem, nlb);
+  if (st != MDEOS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint16_t* nl = nullptr;
+  if (nlb) CK(cudaMallocAsync(&nl, nlb, s));
+  cudaError_t e = launch_debug_forces(bd, rp, apt, ncell, smem, (const float4*)x4, (float4*)f4, ew,
+                                      pairs, nl, s);
+  if (nl) cudaFreeAsync(nl, s);
+  if (e != cudaSuccess) return cuda_fail(e, "debug_forces launch");
+  CK(cudaStreamSynchronize(s));
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float* v4, int32_t n,
+                                       double L, int32_t steps, double T_target,
+                                       int32_t rescale_every, int32_t path, double skin,
+                                       double* epot, double* ekin, void* stream) {
+  if (!x4 || !v4 || steps < 0 || rescale_every < 0) return fail(MDEOS_EINVAL, "bad arguments");
+  BoxDesc bd;
+  RunParams rp;
+  int apt, ncell, smem;
+  size_t nlb;
+  mdeos_status st = debug_setup(cfg, n, L, path, skin, bd, rp, apt, ncell, smem, nlb);
+  if (st != MDEOS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint16_t* nl = nullptr;
+  if (nlb) CK(cudaMallocAsync(&nl, nlb, s));
+  cudaError_t e = launch_debug_md(bd, rp, apt, ncell, smem, (float4*)x4, (float4*)v4, steps,
+                                  T_target, rescale_every, epot, ekin, nl, s);
+  if (nl) cudaFreeAsync(nl, s);
+  if (e != cudaSuccess) return cuda_fail(e, "debug_md launch");
+  CK(cudaStreamSynchronize(s));
+  return MDEOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// statistics for benchmarks
+
+extern "C" mdeos_status mdeos_stats(const mdeos_handle* h, size_t* last_h2d_bytes,
+                                    size_t* last_d2h_bytes, long long* kernel_launches,
+                                    size_t* device_bytes) {
+  if (!h) return fail(MDEOS_EINVAL, "handle is NULL");
+  if (last_h2d_bytes) *last_h2d_bytes = h->last_h2d;
+  if (last_d2h_bytes) *last_d2h_bytes = h->last_d2h;
+  if (kernel_launches) *kernel_launches = h->launches;
+  if (device_bytes) *device_bytes = h->used_bytes;
+  return MDEOS_OK;
+}

@@ -1,0 +1,260 @@
+// Single-box kernels for parity tests.  Each runs one box in one CTA (one
+// group of 32 warps) through the same device functions as the batch kernel.
+#include "mdeos_device.cuh"
+
+namespace mdeos {
+
+template <int APT>
+__device__ void debug_lift_body(const Group& g, const BoxDesc& bd, const RunParams& rp, double T,
+                                float4* x4, float4* v4, double* e_out) {
+  const BoxCtx b = make_ctx(bd, rp);
+  int cnt[APT];
+  for (int a = 0; a < APT; ++a) cnt[a] = 0;
+  if (g.tid < 16) g.ctrl()[g.tid] = 0;
+  lattice_own<APT>(g, bd);
+  gbar(g.bar, g.nt);
+  float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int np = 0;
+  if (bd.path == PATH_NLIST) {
+    build_nlist<APT>(g, b, cnt);
+    compute_forces<APT, PATH_NLIST, true, false, false>(g, b, rp, cnt, e0, w0, np);
+  } else if (bd.path == PATH_ALLPAIRS_MI) {
+    compute_forces<APT, PATH_ALLPAIRS_MI, true, false, false>(g, b, rp, cnt, e0, w0, np);
+  } else {
+    compute_forces<APT, PATH_ALLPAIRS, true, false, false>(g, b, rp, cnt, e0, w0, np);
+  }
+  double et[1];
+  float q[1] = {e0};
+  group_sum<1>(g, q, et);
+  init_velocities<APT>(g, b, bd.seed, T, rp);
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) {
+      x4[i] = g.x()[i];
+      v4[i] = g.v()[i];
+    }
+  }
+  if (g.tid == 0) e_out[0] = 0.5 * et[0];
+}
+
+template <int APT, int PATH>
+__device__ void debug_forces_body(const Group& g, const BoxDesc& bd, const RunParams& rp,
+                                  const float4* x4, float4* f4, double* ew, long long* pairs) {
+  const BoxCtx b = make_ctx(bd, rp);
+  int cnt[APT];
+  for (int a = 0; a < APT; ++a) {
+    cnt[a] = 0;
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) g.x()[i] = x4[i];
+  }
+  if (g.tid < 16) g.ctrl()[g.tid] = 0;
+  gbar(g.bar, g.nt);
+  if (PATH == PATH_NLIST) {
+    // the list is built from wrapped positions; forces use the originals
+    float disp[APT];
+    wrap_own<APT>(g, b, disp);
+    build_nlist<APT>(g, b, cnt);
+    for (int a = 0; a < APT; ++a) {
+      const int i = g.tid + a * g.nt;
+      if (i < b.n) g.x()[i] = x4[i];
+    }
+    gbar(g.bar, g.nt);
+  }
+  float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int np = 0;
+  compute_forces<APT, PATH, true, true, true>(g, b, rp, cnt, e, w, np);
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) f4[i] = g.f()[i];
+  }
+  float q[8] = {0.5f * e,    0.5f * w[0], 0.5f * w[1], 0.5f * w[2],
+                0.5f * w[3], 0.5f * w[4], 0.5f * w[5], (float)np};
+  double out[8];
+  group_sum<8>(g, q, out);
+  if (g.tid == 0) {
+    for (int k = 0; k < 7; ++k) ew[k] = out[k];
+    if (pairs) pairs[0] = (long long)llrint(out[7]);
+    if (g.ctrl()[CTRL_OVERFLOW]) ew[0] = __longlong_as_double(0x7ff8000000000001ll);
+  }
+}
+
+template <int APT, int PATH>
+__device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams& rp, float4* x4,
+                              float4* v4, int steps, double T_target, int rescale_every,
+                              double* epot, double* ekin) {
+  const BoxCtx b = make_ctx(bd, rp);
+  const int n = b.n;
+  const double ndof = 3.0 * n - 3.0;
+  int cnt[APT];
+  float disp[APT];
+  for (int a = 0; a < APT; ++a) {
+    cnt[a] = 0;
+    disp[a] = 0.f;
+    const int i = g.tid + a * g.nt;
+    if (i < n) {
+      g.x()[i] = x4[i];
+      g.v()[i] = v4[i];
+    }
+  }
+  if (g.tid < 16) g.ctrl()[g.tid] = 0;
+  gbar(g.bar, g.nt);
+  if (PATH == PATH_NLIST) {
+    wrap_own<APT>(g, b, disp);
+    build_nlist<APT>(g, b, cnt);
+  }
+  {
+    float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int np = 0;
+    compute_forces<APT, PATH, false, false, false>(g, b, rp, cnt, e0, w0, np);
+  }
+  for (int s = 0; s < steps; ++s) {
+    const bool need = kick_drift<APT>(g, b, rp, 1.0f, disp);
+    if (PATH == PATH_NLIST) {
+      if (gbar_or(g.bar, g.nt, need)) {
+        wrap_own<APT>(g, b, disp);
+        build_nlist<APT>(g, b, cnt);
+      }
+    } else {
+      gbar(g.bar, g.nt);
+    }
+    float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int np = 0;
+    compute_forces<APT, PATH, true, false, false>(g, b, rp, cnt, e, w, np);
+    float ke = 0.f;
+    for (int a = 0; a < APT; ++a) {
+      const int i = g.tid + a * g.nt;
+      if (i < n) {
+        const float4 fi = g.f()[i];
+        float4 vi = g.v()[i];
+        vi.x = fmaf(rp.hdtm, fi.x, vi.x);
+        vi.y = fmaf(rp.hdtm, fi.y, vi.y);
+        vi.z = fmaf(rp.hdtm, fi.z, vi.z);
+        g.v()[i] = vi;
+        ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+      }
+    }
+    float q[2] = {0.5f * e, 0.5f * rp.mass_f * ke};
+    double tot[2];
+    group_sum<2>(g, q, tot);
+    if (g.tid == 0) {
+      if (epot) epot[s] = tot[0];
+      if (ekin) ekin[s] = tot[1];
+    }
+    if (rescale_every > 0 && (s + 1) % rescale_every == 0) {
+      const float lam = (float)sqrt(T_target / (2.0 * tot[1] / ndof));
+      for (int a = 0; a < APT; ++a) {
+        const int i = g.tid + a * g.nt;
+        if (i < n) {
+          float4 vi = g.v()[i];
+          vi.x *= lam;
+          vi.y *= lam;
+          vi.z *= lam;
+          g.v()[i] = vi;
+        }
+      }
+    }
+  }
+  wrap_own<APT>(g, b, disp);
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < n) {
+      x4[i] = g.x()[i];
+      v4[i] = g.v()[i];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    debug_lift_kernel(BoxDesc bd, RunParams rp, double T, int apt, int ncell_cap, float4* x4,
+                      float4* v4, double* e_out, uint16_t* nl) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Group g = make_group(smem, threadIdx.x, 32, apt, ncell_cap, 1, nl);
+  switch (apt) {
+    case 1: debug_lift_body<1>(g, bd, rp, T, x4, v4, e_out); break;
+    case 2: debug_lift_body<2>(g, bd, rp, T, x4, v4, e_out); break;
+    default: debug_lift_body<4>(g, bd, rp, T, x4, v4, e_out); break;
+  }
+}
+
+template <int APT>
+__device__ void debug_forces_path(const Group& g, const BoxDesc& bd, const RunParams& rp,
+                                  const float4* x4, float4* f4, double* ew, long long* pairs) {
+  switch (bd.path) {
+    case PATH_NLIST: debug_forces_body<APT, PATH_NLIST>(g, bd, rp, x4, f4, ew, pairs); break;
+    case PATH_ALLPAIRS_MI:
+      debug_forces_body<APT, PATH_ALLPAIRS_MI>(g, bd, rp, x4, f4, ew, pairs);
+      break;
+    default: debug_forces_body<APT, PATH_ALLPAIRS>(g, bd, rp, x4, f4, ew, pairs); break;
+  }
+}
+
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    debug_forces_kernel(BoxDesc bd, RunParams rp, int apt, int ncell_cap, const float4* x4,
+                        float4* f4, double* ew, long long* pairs, uint16_t* nl) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Group g = make_group(smem, threadIdx.x, 32, apt, ncell_cap, 1, nl);
+  switch (apt) {
+    case 1: debug_forces_path<1>(g, bd, rp, x4, f4, ew, pairs); break;
+    case 2: debug_forces_path<2>(g, bd, rp, x4, f4, ew, pairs); break;
+    default: debug_forces_path<4>(g, bd, rp, x4, f4, ew, pairs); break;
+  }
+}
+
+template <int APT>
+__device__ void debug_md_path(const Group& g, const BoxDesc& bd, const RunParams& rp, float4* x4,
+                              float4* v4, int steps, double T, int every, double* ep, double* ek) {
+  switch (bd.path) {
+    case PATH_NLIST:
+      debug_md_body<APT, PATH_NLIST>(g, bd, rp, x4, v4, steps, T, every, ep, ek);
+      break;
+    case PATH_ALLPAIRS_MI:
+      debug_md_body<APT, PATH_ALLPAIRS_MI>(g, bd, rp, x4, v4, steps, T, every, ep, ek);
+      break;
+    default: debug_md_body<APT, PATH_ALLPAIRS>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
+  }
+}
+
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    debug_md_kernel(BoxDesc bd, RunParams rp, int apt, int ncell_cap, float4* x4, float4* v4,
+                    int steps, double T, int every, double* ep, double* ek, uint16_t* nl) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Group g = make_group(smem, threadIdx.x, 32, apt, ncell_cap, 1, nl);
+  switch (apt) {
+    case 1: debug_md_path<1>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
+    case 2: debug_md_path<2>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
+    default: debug_md_path<4>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
+  }
+}
+
+cudaError_t set_debug_attributes(int max_smem) {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(debug_lift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(debug_forces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(debug_md_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+cudaError_t launch_debug_lift(const BoxDesc& bd, const RunParams& rp, double T, int apt,
+                              int ncell_cap, int smem, float4* x4, float4* v4, double* e_out,
+                              uint16_t* nl, cudaStream_t st) {
+  debug_lift_kernel<<<1, kCtaThreads, smem, st>>>(bd, rp, T, apt, ncell_cap, x4, v4, e_out, nl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_forces(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
+                                int smem, const float4* x4, float4* f4, double* ew,
+                                long long* pairs, uint16_t* nl, cudaStream_t st) {
+  debug_forces_kernel<<<1, kCtaThreads, smem, st>>>(bd, rp, apt, ncell_cap, x4, f4, ew, pairs, nl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_md(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
+                            int smem, float4* x4, float4* v4, int steps, double T, int every,
+                            double* ep, double* ek, uint16_t* nl, cudaStream_t st) {
+  debug_md_kernel<<<1, kCtaThreads, smem, st>>>(bd, rp, apt, ncell_cap, x4, v4, steps, T, every,
+                                                ep, ek, nl);
+  return cudaGetLastError();
+}
+
+}  // namespace mdeos

@@ -1,0 +1,844 @@
+// Device code of the batched in-line atomistic EOS evaluation
+// (arXiv 2508.06012, Sec. III: lifting Eq. 6-10, MD, restriction Eq. 11).
+//
+// Execution model (GB300, sm_103a):
+//  * A group of warps runs one box start to finish: lattice, E_cold,
+//    velocities, every MD step and the restriction.  Groups are synchronised
+//    by a named barrier; several groups share a 1024-thread CTA.
+//  * The box lives in shared memory for its whole run: positions, forces and
+//    velocities as float4 (the force array doubles as the cell-sorted copy
+//    while the Verlet list is rebuilt).  Thread t owns atoms t, t + nt, ...
+//    for the whole run, so per-atom state needs no cross-thread exchange
+//    except positions.
+//  * Pair forces are FP32 (rcp.approx + FMA).  Per-thread and per-warp
+//    partial sums are FP32; the cross-warp combination and every time
+//    accumulation of energy, virial and kinetic tensors are FP64.
+//  * The Verlet list (uint16 atom indices, four per 8-byte word, words laid
+//    out so one warp load is contiguous) lives in global scratch.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mdeos_internal.h"
+
+namespace mdeos {
+
+// ---------------------------------------------------------------------------
+// primitives
+
+__device__ __forceinline__ void gbar(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// barrier that also ORs a predicate over the participating threads
+__device__ __forceinline__ bool gbar_or(int id, int n, bool p) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.s32 pi, %3, 0;\n\t"
+      "bar.red.or.pred po, %1, %2, pi;\n\t"
+      "selp.s32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"(id), "r"(n), "r"((int)p)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the two-multiplier
+// bijection, the key advanced by the Weyl increments between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    uint32_t lo0 = m0 * c[0], hi0 = __umulhi(m0, c[0]);
+    uint32_t lo1 = m1 * c[2], hi1 = __umulhi(m1, c[2]);
+    uint32_t n0 = hi1 ^ c[1] ^ k0;
+    uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// group of warps running one box; shared-memory layout as group_smem_bytes()
+
+// FP64 accumulator slots (group shared memory)
+enum { ACC_BP = 0, ACC_BT = kMaxSeBlocks, ACC_RUN = 2 * kMaxSeBlocks, ACC_BOX = 2 * kMaxSeBlocks + 16 };
+// running sums at ACC_RUN + k: 0..5 stress, 6 E_pot, 7 E_kin, 8 P, 9 T, 10 lifting E_pot sample,
+// 11 in-cutoff pairs, 12 candidates; box constants at ACC_BOX + 0..3
+enum { CTRL_STATUS = 0, CTRL_OVERFLOW = 1 };
+
+struct Group {
+  unsigned char* base;
+  uint16_t* nl;  // neighbour scratch: word (kb, i) at ((kb * npad + i) * 4) uint16 units
+  int tid, nt, bar, npad, nwarps, off_red;
+  __device__ __forceinline__ int warp() const { return tid >> 5; }
+  __device__ __forceinline__ int lane() const { return tid & 31; }
+  __device__ __forceinline__ float4* x() const { return reinterpret_cast<float4*>(base); }
+  __device__ __forceinline__ float4* f() const { return reinterpret_cast<float4*>(base) + npad; }
+  __device__ __forceinline__ float4* v() const { return reinterpret_cast<float4*>(base) + 2 * npad; }
+  __device__ __forceinline__ int* cell() const {
+    return reinterpret_cast<int*>(base + (size_t)48 * npad);
+  }
+  __device__ __forceinline__ float* red() const { return reinterpret_cast<float*>(base + off_red); }
+  __device__ __forceinline__ double* bc() const {
+    return reinterpret_cast<double*>(base + off_red + nwarps * kRedSlots * 4);
+  }
+  __device__ __forceinline__ double* acc() const { return bc() + 8; }
+  __device__ __forceinline__ int* bcnt() const { return reinterpret_cast<int*>(acc() + kAccDoubles); }
+  __device__ __forceinline__ int* ctrl() const { return bcnt() + kMaxSeBlocks; }
+};
+
+__device__ inline Group make_group(unsigned char* base, int tid, int warps, int apt, int ncell_cap,
+                                   int bar, uint16_t* nl) {
+  Group g;
+  g.base = base;
+  g.nl = nl;
+  g.tid = tid;
+  g.nt = warps * 32;
+  g.bar = bar;
+  g.npad = warps * 32 * apt;
+  g.nwarps = warps;
+  g.off_red = group_red_offset(warps, apt, ncell_cap);
+  return g;
+}
+
+// Sum NQ per-thread FP32 values over the group; every thread gets the FP64
+// totals.  Warp sums are FP32, the cross-warp combination FP64 in warp order.
+template <int NQ>
+__device__ void group_sum(const Group& g, const float (&q)[NQ], double (&out)[NQ]) {
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    float s = warp_sum(q[k]);
+    if (g.lane() == 0) g.red()[g.warp() * kRedSlots + k] = s;
+  }
+  gbar(g.bar, g.nt);
+  if (g.warp() == 0 && g.lane() < NQ) {
+    double s = 0.0;
+    for (int w = 0; w < g.nwarps; ++w) s += (double)g.red()[w * kRedSlots + g.lane()];
+    g.bc()[g.lane()] = s;
+  }
+  gbar(g.bar, g.nt);
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) out[k] = g.bc()[k];
+}
+
+// Per-box constants in registers.
+struct BoxCtx {
+  int n, maxnb, nc;
+  float L, invL, half_skin, rcs2, cinv;
+};
+
+__device__ inline BoxCtx make_ctx(const BoxDesc& bd, const RunParams& rp) {
+  BoxCtx b;
+  b.n = bd.natoms;
+  b.maxnb = bd.maxnb;
+  b.nc = bd.nc_cell;
+  b.L = (float)bd.L;
+  b.invL = (float)(1.0 / bd.L);
+  b.half_skin = 0.5f * bd.skin;
+  float rs = rp.rc + bd.skin;
+  b.rcs2 = rs * rs;
+  b.cinv = bd.nc_cell > 0 ? (float)(bd.nc_cell / bd.L) : 0.f;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Lennard-Jones 12-6 pair term, truncated and shifted:
+//   u(r) = 4 eps [(s/r)^12 - (s/r)^6] - u(rc),
+//   f_ij = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2 * r_ij
+// `ok` masks the term (the atom itself, padding).
+
+template <bool EN, bool VIR>
+__device__ __forceinline__ void lj_pair(float dx, float dy, float dz, bool ok, const RunParams& rp,
+                                        float& fx, float& fy, float& fz, float& e, float (&w)[6],
+                                        int& npair) {
+  float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  bool in = ok && (r2 < rp.rc2);
+  float ir2 = rcp_approx(r2);
+  float s6 = rp.sig6 * ir2 * ir2 * ir2;
+  float fr = rp.eps24 * s6 * fmaf(2.0f, s6, -1.0f) * ir2;
+  fr = in ? fr : 0.0f;
+  fx = fmaf(fr, dx, fx);
+  fy = fmaf(fr, dy, fy);
+  fz = fmaf(fr, dz, fz);
+  if (EN) {
+    float u = fmaf(rp.eps4 * s6, s6 - 1.0f, -rp.ucut);
+    e += in ? u : 0.0f;
+  }
+  if (VIR) {
+    float tx = fr * dx, ty = fr * dy, tz = fr * dz;
+    w[0] = fmaf(tx, dx, w[0]);
+    w[1] = fmaf(ty, dy, w[1]);
+    w[2] = fmaf(tz, dz, w[2]);
+    w[3] = fmaf(tx, dy, w[3]);
+    w[4] = fmaf(tx, dz, w[4]);
+    w[5] = fmaf(ty, dz, w[5]);
+  }
+  npair += in ? 1 : 0;
+}
+
+__device__ __forceinline__ float min_img(float d, float L, float invL) {
+  return fmaf(-L, rintf(d * invL), d);
+}
+
+template <bool EN, bool VIR>
+__device__ __forceinline__ void nl_pair(const float4* __restrict__ xs, int j, const float4& xi,
+                                        const BoxCtx& b, const RunParams& rp, float& fx, float& fy,
+                                        float& fz, float& e, float (&w)[6], int& np) {
+  const float4 xj = xs[j];
+  float dx = min_img(xi.x - xj.x, b.L, b.invL);
+  float dy = min_img(xi.y - xj.y, b.L, b.invL);
+  float dz = min_img(xi.z - xj.z, b.L, b.invL);
+  lj_pair<EN, VIR>(dx, dy, dz, true, rp, fx, fy, fz, e, w, np);
+}
+
+// Forces on the thread's own atoms (written to g.f()), with optional energy,
+// virial and pair-count partials over ordered pairs (the caller halves E, W).
+template <int APT, int PATH, bool EN, bool VIR, bool CNT>
+__device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, const RunParams& rp,
+                                               const int (&cnt)[APT], float& e_acc,
+                                               float (&w_acc)[6], int& pair_acc) {
+  const float4* __restrict__ xs = g.x();
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) {
+      const float4 xi = xs[i];
+      float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+      float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      int np = 0;
+      if (PATH == PATH_NLIST) {
+        const uint2* __restrict__ p = reinterpret_cast<const uint2*>(g.nl) + i;
+        const int c = cnt[a];
+        const int nfull = c >> 2;
+#pragma unroll 2
+        for (int kb = 0; kb < nfull; ++kb) {
+          const uint2 q = p[(size_t)kb * g.npad];
+          nl_pair<EN, VIR>(xs, (int)(q.x & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
+          nl_pair<EN, VIR>(xs, (int)(q.x >> 16), xi, b, rp, fx, fy, fz, e, w, np);
+          nl_pair<EN, VIR>(xs, (int)(q.y & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
+          nl_pair<EN, VIR>(xs, (int)(q.y >> 16), xi, b, rp, fx, fy, fz, e, w, np);
+        }
+        const int rem = c & 3;
+        if (rem) {
+          const uint2 q = p[(size_t)nfull * g.npad];
+          nl_pair<EN, VIR>(xs, (int)(q.x & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
+          if (rem > 1) nl_pair<EN, VIR>(xs, (int)(q.x >> 16), xi, b, rp, fx, fy, fz, e, w, np);
+          if (rem > 2) nl_pair<EN, VIR>(xs, (int)(q.y & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
+        }
+      } else if (PATH == PATH_ALLPAIRS) {
+        for (int j = 0; j < b.n; ++j) {
+          const float4 xj = xs[j];
+          float dx = min_img(xi.x - xj.x, b.L, b.invL);
+          float dy = min_img(xi.y - xj.y, b.L, b.invL);
+          float dz = min_img(xi.z - xj.z, b.L, b.invL);
+          lj_pair<EN, VIR>(dx, dy, dz, j != i, rp, fx, fy, fz, e, w, np);
+        }
+      } else {  // PATH_ALLPAIRS_MI: rc <= L < 2 rc, the two nearest images per axis
+        for (int j = 0; j < b.n; ++j) {
+          const float4 xj = xs[j];
+          float d0x = min_img(xi.x - xj.x, b.L, b.invL);
+          float d0y = min_img(xi.y - xj.y, b.L, b.invL);
+          float d0z = min_img(xi.z - xj.z, b.L, b.invL);
+          float d1x = d0x - copysignf(b.L, d0x);
+          float d1y = d0y - copysignf(b.L, d0y);
+          float d1z = d0z - copysignf(b.L, d0z);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            float dx = (c & 1) ? d1x : d0x;
+            float dy = (c & 2) ? d1y : d0y;
+            float dz = (c & 4) ? d1z : d0z;
+            bool ok = (j != i) || (c != 0);
+            lj_pair<EN, VIR>(dx, dy, dz, ok, rp, fx, fy, fz, e, w, np);
+          }
+        }
+      }
+      g.f()[i] = make_float4(fx, fy, fz, 0.f);
+      if (EN) e_acc += e;
+      if (VIR) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w_acc[k] += w[k];
+      }
+      if (CNT) pair_acc += np;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Verlet list build from positions wrapped into [0, L).  With >= 3 cells of
+// side >= rc + skin per axis a shared-memory cell list (counting sort; each
+// cell ordered by atom index, so the list order is deterministic) feeds the
+// search; smaller boxes scan every atom.  Thread t writes only the rows of
+// the atoms it owns, which only it reads back.
+__device__ __forceinline__ void nl_store(uint16_t* row, int k, int npad, int j) {
+  row[(size_t)(k >> 2) * npad * 4 + (k & 3)] = (uint16_t)j;
+}
+
+template <int APT>
+__device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
+  const int n = b.n;
+  float4* xs = g.x();
+  float4* srt = g.f();  // cell-sorted copy (the forces are dead during a rebuild)
+  if (b.nc >= 3) {
+    const int nc = b.nc, ncell = nc * nc * nc;
+    int* ccount = g.cell();            // counts, then insertion cursors
+    int* cstart = g.cell() + ncell + 1;  // [ncell + 1]
+    for (int c = g.tid; c < ncell; c += g.nt) ccount[c] = 0;
+    gbar(g.bar, g.nt);
+    int mycell[APT];
+#pragma unroll
+    for (int a = 0; a < APT; ++a) {
+      const int i = g.tid + a * g.nt;
+      mycell[a] = 0;
+      if (i < n) {
+        const float4 xi = xs[i];
+        const int cx = min((int)(xi.x * b.cinv), nc - 1);
+        const int cy = min((int)(xi.y * b.cinv), nc - 1);
+        const int cz = min((int)(xi.z * b.cinv), nc - 1);
+        const int c = (cz * nc + cy) * nc + cx;
+        mycell[a] = c;
+        atomicAdd(&ccount[c], 1);
+      }
+    }
+    gbar(g.bar, g.nt);
+    if (g.warp() == 0) {
+      const int lane = g.lane();
+      const int per = (ncell + 31) / 32;
+      const int lo = lane * per, hi = min(lo + per, ncell);
+      int s = 0;
+      for (int c = lo; c < hi; ++c) s += ccount[c];
+      int incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      int run = incl - s;
+      for (int c = lo; c < hi; ++c) {
+        const int k = ccount[c];
+        cstart[c] = run;
+        ccount[c] = run;
+        run += k;
+      }
+      if (lane == 31) cstart[ncell] = incl;
+    }
+    gbar(g.bar, g.nt);
+#pragma unroll
+    for (int a = 0; a < APT; ++a) {
+      const int i = g.tid + a * g.nt;
+      if (i < n) {
+        const int slot = atomicAdd(&ccount[mycell[a]], 1);
+        const float4 xi = xs[i];
+        srt[slot] = make_float4(xi.x, xi.y, xi.z, __int_as_float(i));
+      }
+    }
+    gbar(g.bar, g.nt);
+    for (int c = g.tid; c < ncell; c += g.nt) {  // order each cell by atom index
+      const int s0 = cstart[c], s1 = cstart[c + 1];
+      for (int s = s0 + 1; s < s1; ++s) {
+        const float4 key = srt[s];
+        const int kk = __float_as_int(key.w);
+        int t = s - 1;
+        while (t >= s0 && __float_as_int(srt[t].w) > kk) {
+          srt[t + 1] = srt[t];
+          --t;
+        }
+        srt[t + 1] = key;
+      }
+    }
+    gbar(g.bar, g.nt);
+#pragma unroll
+    for (int a = 0; a < APT; ++a) {
+      const int i = g.tid + a * g.nt;
+      if (i < n) {
+        const float4 xi = xs[i];
+        const int c = mycell[a];
+        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+        uint16_t* row = g.nl + (size_t)i * 4;
+        int k = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+          const int qz = (cz + dz + nc) % nc;
+          for (int dy = -1; dy <= 1; ++dy) {
+            const int qy = (cy + dy + nc) % nc;
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int qx = (cx + dx + nc) % nc;
+              const int q = (qz * nc + qy) * nc + qx;
+              const int s1 = cstart[q + 1];
+              for (int s = cstart[q]; s < s1; ++s) {
+                const float4 xo = srt[s];
+                const int j = __float_as_int(xo.w);
+                const float ddx = min_img(xi.x - xo.x, b.L, b.invL);
+                const float ddy = min_img(xi.y - xo.y, b.L, b.invL);
+                const float ddz = min_img(xi.z - xo.z, b.L, b.invL);
+                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                if (j != i && r2 < b.rcs2) {
+                  if (k < b.maxnb) nl_store(row, k, g.npad, j);
+                  ++k;
+                }
+              }
+            }
+          }
+        }
+        if (k > b.maxnb) {
+          atomicOr(&g.ctrl()[CTRL_OVERFLOW], 1);
+          k = b.maxnb;
+        }
+        cnt[a] = k;
+      }
+    }
+    gbar(g.bar, g.nt);  // the sorted copy aliases the force array
+  } else {
+    gbar(g.bar, g.nt);  // positions just wrapped by their owners
+#pragma unroll
+    for (int a = 0; a < APT; ++a) {
+      const int i = g.tid + a * g.nt;
+      if (i < n) {
+        const float4 xi = xs[i];
+        uint16_t* row = g.nl + (size_t)i * 4;
+        int k = 0;
+        for (int j = 0; j < n; ++j) {
+          const float4 xo = xs[j];
+          const float ddx = min_img(xi.x - xo.x, b.L, b.invL);
+          const float ddy = min_img(xi.y - xo.y, b.L, b.invL);
+          const float ddz = min_img(xi.z - xo.z, b.L, b.invL);
+          const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+          if (j != i && r2 < b.rcs2) {
+            if (k < b.maxnb) nl_store(row, k, g.npad, j);
+            ++k;
+          }
+        }
+        if (k > b.maxnb) {
+          atomicOr(&g.ctrl()[CTRL_OVERFLOW], 1);
+          k = b.maxnb;
+        }
+        cnt[a] = k;
+      }
+    }
+    gbar(g.bar, g.nt);
+  }
+}
+
+// wrap own positions into [0, L) and reset their displacement bounds
+template <int APT>
+__device__ __forceinline__ void wrap_own(const Group& g, const BoxCtx& b, float (&disp)[APT]) {
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    disp[a] = 0.f;
+    if (i < b.n) {
+      float4 xi = g.x()[i];
+      xi.x -= b.L * floorf(xi.x * b.invL);
+      xi.y -= b.L * floorf(xi.y * b.invL);
+      xi.z -= b.L * floorf(xi.z * b.invL);
+      xi.x = fmaxf((xi.x >= b.L) ? xi.x - b.L : xi.x, 0.f);
+      xi.y = fmaxf((xi.y >= b.L) ? xi.y - b.L : xi.y, 0.f);
+      xi.z = fmaxf((xi.z >= b.L) ? xi.z - b.L : xi.z, 0.f);
+      g.x()[i] = xi;
+    }
+  }
+}
+
+// Lifted FCC lattice (Eq. 6-7): first n sites of nc^3 cells in the order
+// (cell z, cell y, cell x, basis), cell side L / nc.
+template <int APT>
+__device__ void lattice_own(const Group& g, const BoxDesc& bd) {
+  const int nc = bd.nc_lat;
+  const double a = bd.L / nc;
+#pragma unroll
+  for (int k = 0; k < APT; ++k) {
+    const int i = g.tid + k * g.nt;
+    if (i < bd.natoms) {
+      const int c = i >> 2, bb = i & 3;
+      const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+      const double bx = (bb == 1 || bb == 2) ? 0.5 : 0.0;
+      const double by = (bb == 1 || bb == 3) ? 0.5 : 0.0;
+      const double bz = (bb == 2 || bb == 3) ? 0.5 : 0.0;
+      g.x()[i] = make_float4((float)(a * (cx + bx)), (float)(a * (cy + by)), (float)(a * (cz + bz)),
+                             0.f);
+    }
+  }
+}
+
+// Energy lifting, first guess (Eq. 9): Gaussian velocities at temperature T
+// (Philox key = seed, counter = (atom, 0, 0, 0), Box-Muller), zero total
+// momentum, exact rescale to T with N_DOF = 3N - 3.  Writes g.v().
+template <int APT>
+__device__ void init_velocities(const Group& g, const BoxCtx& b, unsigned long long seed, double T,
+                                const RunParams& rp) {
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffull), k1 = (uint32_t)(seed >> 32);
+  const double sd = sqrt(T / rp.mass);
+  const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
+  float3 v[APT];
+  float p[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    v[a] = make_float3(0.f, 0.f, 0.f);
+    if (i < b.n) {
+      uint32_t c[4] = {(uint32_t)i, 0u, 0u, 0u};
+      philox4x32_10(c, k0, k1);
+      // uniforms in the open interval (0, 1); Box-Muller in FP64 (once per atom)
+      const double u0 = ((double)c[0] + 0.5) * two_m32, u1 = ((double)c[1] + 0.5) * two_m32;
+      const double u2 = ((double)c[2] + 0.5) * two_m32, u3 = ((double)c[3] + 0.5) * two_m32;
+      const double r01 = sqrt(-2.0 * log(u0)), r23 = sqrt(-2.0 * log(u2));
+      double s1, c1, s3, c3;
+      sincospi(2.0 * u1, &s1, &c1);
+      sincospi(2.0 * u3, &s3, &c3);
+      v[a] = make_float3((float)(sd * r01 * c1), (float)(sd * r01 * s1), (float)(sd * r23 * c3));
+      p[0] += v[a].x;
+      p[1] += v[a].y;
+      p[2] += v[a].z;
+    }
+  }
+  double ptot[3];
+  group_sum<3>(g, p, ptot);
+  const float mx = (float)(ptot[0] / b.n), my = (float)(ptot[1] / b.n), mz = (float)(ptot[2] / b.n);
+  float ke[1] = {0.f};
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) {
+      v[a].x -= mx;
+      v[a].y -= my;
+      v[a].z -= mz;
+      ke[0] += v[a].x * v[a].x + v[a].y * v[a].y + v[a].z * v[a].z;
+    }
+  }
+  double ketot[1];
+  group_sum<1>(g, ke, ketot);
+  const double Tinst = rp.mass * ketot[0] / (3.0 * b.n - 3.0);
+  const float lam = (float)sqrt(T / Tinst);
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) g.v()[i] = make_float4(lam * v[a].x, lam * v[a].y, lam * v[a].z, 0.f);
+  }
+}
+
+// the three force variants the step loop uses
+template <int APT, int PATH>
+__device__ __forceinline__ void forces_step(const Group& g, const BoxCtx& b, const RunParams& rp,
+                                            const int (&cnt)[APT], bool en, bool vir, float& e,
+                                            float (&w)[6], int& np) {
+  if (vir)
+    compute_forces<APT, PATH, true, true, true>(g, b, rp, cnt, e, w, np);
+  else if (en)
+    compute_forces<APT, PATH, true, false, false>(g, b, rp, cnt, e, w, np);
+  else
+    compute_forces<APT, PATH, false, false, false>(g, b, rp, cnt, e, w, np);
+}
+
+// first half kick with the pending thermostat factor, then drift; returns
+// whether any own atom's displacement bound passed half the skin
+template <int APT>
+__device__ __forceinline__ bool kick_drift(const Group& g, const BoxCtx& b, const RunParams& rp,
+                                           float lam, float (&disp)[APT]) {
+  bool need = false;
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) {
+      const float4 fi = g.f()[i];
+      float4 vi = g.v()[i];
+      vi.x = fmaf(lam, vi.x, rp.hdtm * fi.x);
+      vi.y = fmaf(lam, vi.y, rp.hdtm * fi.y);
+      vi.z = fmaf(lam, vi.z, rp.hdtm * fi.z);
+      g.v()[i] = vi;
+      float4 xi = g.x()[i];
+      xi.x = fmaf(rp.dt, vi.x, xi.x);
+      xi.y = fmaf(rp.dt, vi.y, xi.y);
+      xi.z = fmaf(rp.dt, vi.z, xi.z);
+      g.x()[i] = xi;
+      disp[a] += rp.dt * sqrtf(vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+      need = need || (disp[a] > b.half_skin);
+    }
+  }
+  return need;
+}
+
+// ---------------------------------------------------------------------------
+// One box, start to finish.  Every thread of the group runs the same control
+// flow; branch decisions depend only on values all threads hold identically.
+template <int APT, int PATH>
+__device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const RunParams& rp,
+                        mdeos_result* out) {
+  const BoxCtx b = make_ctx(bd, rp);
+  const int n = b.n;
+  const double ndof = 3.0 * n - 3.0;
+  const float ndof_f = (float)ndof;
+  const double V = bd.L * bd.L * bd.L;
+  const bool temp_mode = (bd.flags & MDEOS_REQ_TEMPERATURE) != 0;
+  float disp[APT];
+  int cnt[APT];
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    disp[a] = 0.f;
+    cnt[a] = 0;
+  }
+  double* acc = g.acc();
+  if (g.tid < 16) g.ctrl()[g.tid] = 0;
+  for (int k = g.tid; k < kAccDoubles; k += g.nt) acc[k] = 0.0;
+  for (int k = g.tid; k < kMaxSeBlocks; k += g.nt) g.bcnt()[k] = 0;
+  lattice_own<APT>(g, bd);
+  gbar(g.bar, g.nt);
+  int builds = 0;
+  if (PATH == PATH_NLIST) {
+    build_nlist<APT>(g, b, cnt);
+    ++builds;
+  }
+  // E_cold: potential energy of the lifted lattice at rest (Sec. III)
+  double E_cold;
+  {
+    float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int np0 = 0;
+    forces_step<APT, PATH>(g, b, rp, cnt, true, false, e0, w0, np0);
+    float q[1] = {e0};
+    double et[1];
+    group_sum<1>(g, q, et);
+    E_cold = 0.5 * et[0];
+  }
+  double* boxc = acc + ACC_BOX;  // FP64 box constants, read by warp 0 only
+  const double E_ref = (rp.ref_mode == MDEOS_REF_FIXED) ? n * bd.e_ref : E_cold;
+  const double E_tgt = n * bd.e + E_ref;
+  double Tk = temp_mode ? bd.e : 2.0 * (E_tgt - E_cold) / ndof;  // Eq. 9
+  if (g.tid == 0) {
+    boxc[0] = E_cold;
+    boxc[1] = E_ref;
+    boxc[2] = E_tgt;
+  }
+  int status = MDEOS_OK;
+  if (g.ctrl()[CTRL_OVERFLOW]) status = MDEOS_ENBR;
+  if (!(Tk > 0.0) || !isfinite(Tk)) status = MDEOS_EUNPHYS;
+
+  const int nseg = (bd.steps_equil > 0) ? rp.lift_iters : 0;
+  const int base = nseg > 0 ? bd.steps_equil / nseg : 0;
+  int seg = 0, seg_pos = 0;
+  int seg_len = (nseg == 1) ? bd.steps_equil : base;
+  int nsamp = max(1, (seg_len + 9) / 10);
+  const int total = bd.steps_equil + bd.steps_avg;
+  const int nb = rp.se_blocks;
+
+  if (status == MDEOS_OK) init_velocities<APT>(g, b, bd.seed, Tk, rp);
+  float lam = 1.0f;
+  float Tk_f = (float)Tk;
+  if (g.tid == 0) boxc[3] = Tk;
+  for (int step = 0; step < total && status == MDEOS_OK; ++step) {
+    const bool avg = step >= bd.steps_equil;
+    const int s_avg = step - bd.steps_equil;
+    const bool seg_end = !avg && (seg_pos == seg_len - 1);
+    const bool esamp = !avg && !temp_mode && (seg_pos >= seg_len - nsamp);
+    const bool need = kick_drift<APT>(g, b, rp, lam, disp);
+    if (PATH == PATH_NLIST) {
+      if (gbar_or(g.bar, g.nt, need)) {
+        wrap_own<APT>(g, b, disp);
+        build_nlist<APT>(g, b, cnt);
+        ++builds;
+      }
+    } else {
+      gbar(g.bar, g.nt);
+    }
+    {
+      const int st = g.ctrl()[CTRL_STATUS];  // written by warp 0 last step
+      if (st != 0 || g.ctrl()[CTRL_OVERFLOW] != 0) {
+        status = st != 0 ? st : MDEOS_ENBR;
+        break;
+      }
+    }
+    // forces at the new positions
+    float e_th = 0.f, w_th[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int np_th = 0;
+    forces_step<APT, PATH>(g, b, rp, cnt, avg || esamp, avg, e_th, w_th, np_th);
+    // second half kick, kinetic energy and kinetic stress
+    float ke = 0.f, kt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < APT; ++a) {
+      const int i = g.tid + a * g.nt;
+      if (i < n) {
+        const float4 fi = g.f()[i];
+        float4 vi = g.v()[i];
+        vi.x = fmaf(rp.hdtm, fi.x, vi.x);
+        vi.y = fmaf(rp.hdtm, fi.y, vi.y);
+        vi.z = fmaf(rp.hdtm, fi.z, vi.z);
+        g.v()[i] = vi;
+        ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+        if (avg) {
+          kt[0] += vi.x * vi.x;
+          kt[1] += vi.y * vi.y;
+          kt[2] += vi.z * vi.z;
+          kt[3] += vi.x * vi.y;
+          kt[4] += vi.x * vi.z;
+          kt[5] += vi.y * vi.z;
+        }
+      }
+    }
+    // per-warp partials: 0..5 stress (K + W), 6 E_pot, 7 E_kin
+    {
+      float* red = g.red() + g.warp() * kRedSlots;
+      const float s = warp_sum(0.5f * rp.mass_f * ke);
+      if (g.lane() == 0) red[7] = s;
+      if (avg || esamp) {
+        const float se = warp_sum(0.5f * e_th);
+        if (g.lane() == 0) red[6] = se;
+      }
+      if (avg) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float sk = warp_sum(rp.mass_f * kt[k] + 0.5f * w_th[k]);
+          if (g.lane() == 0) red[k] = sk;
+        }
+        int cand = 0;
+#pragma unroll
+        for (int a = 0; a < APT; ++a) {
+          const int i = g.tid + a * g.nt;
+          if (i < n) cand += (PATH == PATH_NLIST) ? cnt[a] : (PATH == PATH_ALLPAIRS ? n : 8 * n);
+        }
+        const float sp = warp_sum((float)np_th), sc = warp_sum((float)cand);
+        if (g.lane() == 0) {
+          red[8] = sp;
+          red[9] = sc;
+        }
+      }
+    }
+    gbar(g.bar, g.nt);
+    float ke_tot = 0.f;
+    for (int w = 0; w < g.nwarps; ++w) ke_tot += g.red()[w * kRedSlots + 7];
+    const float T_inst = 2.0f * ke_tot / ndof_f;
+    if (g.warp() == 0) {
+      const int lane = g.lane();
+      double q = 0.0;
+      const bool need_q = (lane == 7) || (lane == 6 && (avg || esamp)) || (lane < 6 && avg) ||
+                          ((lane == 8 || lane == 9) && avg);
+      if (need_q)
+        for (int w = 0; w < g.nwarps; ++w) q += (double)g.red()[w * kRedSlots + lane];
+      if (esamp && lane == 6) acc[ACC_RUN + 10] += q;
+      const double invV = 1.0 / V, inv_ndof = 1.0 / ndof;
+      if (avg) {
+        if (lane < 8) acc[ACC_RUN + lane] += (lane < 6) ? q * invV : q;
+        if (lane == 8 || lane == 9) acc[ACC_RUN + 3 + lane] += q;
+        const double s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
+        const double s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
+        const double e6 = __shfl_sync(0xffffffffu, q, 6);
+        if (lane == 0) {
+          const double Ps = (s0 + s1 + s2) * (invV / 3.0);
+          const double Ts = 2.0 * k7 * inv_ndof;
+          acc[ACC_RUN + 8] += Ps;
+          acc[ACC_RUN + 9] += Ts;
+          const int blk = (int)((long long)s_avg * nb / bd.steps_avg);
+          acc[ACC_BP + blk] += Ps;
+          acc[ACC_BT + blk] += Ts;
+          g.bcnt()[blk] += 1;
+          if (!isfinite(Ps) || !isfinite(Ts) || !isfinite(e6)) g.ctrl()[CTRL_STATUS] = MDEOS_EUNPHYS;
+        }
+      }
+      if (seg_end && lane == 6) {
+        const double Ebar = acc[ACC_RUN + 10] / nsamp;
+        const double Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) * inv_ndof;  // Eq. 10
+        g.bc()[0] = Tn;
+        acc[ACC_RUN + 10] = 0.0;
+      }
+    }
+    if (!(T_inst > 0.f) || !isfinite(T_inst)) {
+      status = MDEOS_EUNPHYS;
+      break;
+    }
+    lam = 1.0f;
+    if (seg_end) {
+      gbar(g.bar, g.nt);
+      const double Tn = g.bc()[0];
+      if (!(Tn > 0.0) || !isfinite(Tn)) {
+        status = MDEOS_EUNPHYS;
+        break;
+      }
+      if (g.tid == 0) boxc[3] = Tn;
+      Tk_f = (float)Tn;
+      lam = sqrtf(Tk_f / T_inst);
+      ++seg;
+      seg_pos = 0;
+      seg_len = (seg == nseg - 1) ? base + bd.steps_equil % nseg : base;
+      nsamp = max(1, (seg_len + 9) / 10);
+    } else if (!avg) {
+      if (rp.rescale_every_equil > 0 && (seg_pos + 1) % rp.rescale_every_equil == 0)
+        lam = sqrtf(Tk_f / T_inst);
+      ++seg_pos;
+    } else if (rp.rescale_every_avg > 0 && (s_avg + 1) % rp.rescale_every_avg == 0) {
+      lam = sqrtf(Tk_f / T_inst);
+    }
+  }
+  gbar(g.bar, g.nt);
+  if (status == MDEOS_OK && g.ctrl()[CTRL_STATUS] != 0) status = g.ctrl()[CTRL_STATUS];
+  // restriction: time averages and block standard errors
+  if (g.tid == 0) {
+    const double E_cold = boxc[0], E_ref = boxc[1], Tk = boxc[3];
+    const double m = bd.steps_avg;
+    mdeos_result r;
+    for (int k = 0; k < 6; ++k) r.sigma[k] = acc[ACC_RUN + k] / m;
+    r.P = acc[ACC_RUN + 8] / m;
+    r.T = acc[ACC_RUN + 9] / m;
+    r.epot = acc[ACC_RUN + 6] / m / n;
+    r.ekin = acc[ACC_RUN + 7] / m / n;
+    r.e_achieved = (acc[ACC_RUN + 7] / m + acc[ACC_RUN + 6] / m - E_ref) / n;
+    double mP = 0.0, mT = 0.0;
+    for (int k = 0; k < nb; ++k) {
+      const double c = g.bcnt()[k] > 0 ? (double)g.bcnt()[k] : 1.0;
+      acc[ACC_BP + k] /= c;
+      acc[ACC_BT + k] /= c;
+      mP += acc[ACC_BP + k];
+      mT += acc[ACC_BT + k];
+    }
+    mP /= nb;
+    mT /= nb;
+    double vP = 0.0, vT = 0.0;
+    for (int k = 0; k < nb; ++k) {
+      vP += (acc[ACC_BP + k] - mP) * (acc[ACC_BP + k] - mP);
+      vT += (acc[ACC_BT + k] - mT) * (acc[ACC_BT + k] - mT);
+    }
+    r.P_se = sqrt(vP / (nb - 1) / nb);
+    r.T_se = sqrt(vT / (nb - 1) / nb);
+    r.T_target = Tk;
+    r.e_cold = E_cold / n;
+    r.L = bd.L;
+    r.pairs_per_step = acc[ACC_RUN + 11] / m;
+    r.cand_per_step = acc[ACC_RUN + 12] / m;
+    r.element_id = bd.element_id;
+    r.natoms = n;
+    r.status = status;
+    r.nlist_builds = builds;
+    r.path = PATH;
+    if (status != MDEOS_OK) {
+      r.P = r.T = r.epot = r.ekin = r.e_achieved = r.P_se = r.T_se = 0.0;
+      for (int k = 0; k < 6; ++k) r.sigma[k] = 0.0;
+    }
+    *out = r;
+  }
+  gbar(g.bar, g.nt);
+}
+
+template <int APT>
+__device__ __forceinline__ void run_box_path(const Group& g, const BoxDesc& bd, const RunParams& rp,
+                                             mdeos_result* out) {
+  switch (bd.path) {
+    case PATH_NLIST: run_box<APT, PATH_NLIST>(g, bd, rp, out); break;
+    case PATH_ALLPAIRS_MI: run_box<APT, PATH_ALLPAIRS_MI>(g, bd, rp, out); break;
+    default: run_box<APT, PATH_ALLPAIRS>(g, bd, rp, out); break;
+  }
+}
+
+}  // namespace mdeos

@@ -1,0 +1,86 @@
+// Internal types shared by the host engine and the device kernels of the
+// batched atomistic EOS path.  Not part of the C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/mdeos.h"
+
+namespace mdeos {
+
+// Force paths (per box, chosen by the planner).
+enum Path : int {
+  PATH_ALLPAIRS = 0,    // every j broadcast from shared memory, minimum image (L >= 2 rc)
+  PATH_ALLPAIRS_MI = 1, // every j, the two nearest images per axis (rc <= L < 2 rc)
+  PATH_NLIST = 2        // Verlet list with skin, rebuilt from a shared-memory cell list
+};
+
+constexpr int kMaxBoxesPerItem = 8;   // named barriers 1..8 (0 is the CTA barrier)
+constexpr int kCtaThreads = 1024;
+constexpr int kMaxAtoms = 4096;       // 1024 threads x 4 atoms per thread
+constexpr int kMaxSeBlocks = 32;
+constexpr int kMaxCells = 1024;       // cell-list cells per box
+constexpr int kRedSlots = 10;         // reduction quantities per warp
+
+// Force-field and integrator constants (FP32 where the pair loop uses them).
+struct RunParams {
+  float eps4, eps24, sig6, rc2, ucut;
+  float rc;
+  float dt, hdtm;  // dt and dt / (2 m)
+  float mass_f;
+  double mass;
+  int lift_iters, rescale_every_equil, rescale_every_avg, se_blocks, ref_mode;
+};
+
+// One box as planned on the host.
+struct BoxDesc {
+  double rho, e, e_ref;
+  double L;                 // box side actually simulated (float-representable)
+  unsigned long long seed;
+  unsigned long long element_id;
+  int natoms, steps_equil, steps_avg;
+  unsigned flags;
+  int path;                 // Path
+  int maxnb;                // neighbour capacity per atom (PATH_NLIST)
+  int nc_cell;              // cells per axis for the list build (0: brute-force build)
+  int nc_lat;               // FCC cells per axis of the lifted lattice
+  float skin;
+  int out_index;            // slot in the result array
+};
+
+// A unit of the persistent kernel's work queue: up to 8 boxes of one size
+// class, each run by `warps_per_box` warps of the CTA.
+struct WorkItem {
+  int nbox;
+  int warps_per_box;
+  int apt;                  // atoms per thread (1..4)
+  int smem_stride;          // bytes of dynamic shared memory per box group
+  int ncell_cap;            // cells reserved per group
+  int nl_stride;            // uint16 entries of neighbour scratch per group
+  int box[kMaxBoxesPerItem];
+};
+
+constexpr int kAccDoubles = 2 * kMaxSeBlocks + 24;  // block sums of P and T, running sums, box constants
+
+// Shared-memory layout of one box group (host planner and device agree):
+//   positions, forces, velocities  float4[npad] each (48 B per atom slot)
+//   cell counts / starts           int[2 * ncell_cap + 2]
+//   per-warp partials              float[warps][kRedSlots]    (16-B aligned)
+//   FP64 broadcast slots           double[8]
+//   FP64 accumulators              double[kAccDoubles]
+//   block counts                   int[kMaxSeBlocks]
+//   control words                  int[16]
+__host__ __device__ inline int group_red_offset(int warps, int apt, int ncell_cap) {
+  int npad = warps * 32 * apt;
+  int b = npad * 48 + (2 * ncell_cap + 2) * 4;
+  return (b + 15) & ~15;
+}
+
+__host__ __device__ inline int group_smem_bytes(int warps, int apt, int ncell_cap) {
+  int b = group_red_offset(warps, apt, ncell_cap);
+  b += warps * kRedSlots * 4;
+  b += 8 * 8 + kAccDoubles * 8 + kMaxSeBlocks * 4 + 16 * 4;
+  return (b + 127) & ~127;
+}
+
+}  // namespace mdeos
