@@ -185,14 +185,20 @@ def ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     m.build()
-    boxes = w.config2(base_seed=20250807 + rank)
+    if args.boxes or args.md_steps:
+        half = (args.md_steps or 2000) // 2
+        boxes = w.config2(base_seed=20250807 + rank, nbox=args.boxes or 4096,
+                          steps_equil=half, steps_avg=half)
+    else:
+        boxes = w.config2(base_seed=20250807 + rank)
     reqs = gpu_requests(m, boxes)
     nbox = len(reqs)
     h = m.mdeos_create(m.mdeos_config_default(device=local))
     b = m.mdeos_batch_create(h, reqs)
     info = m.mdeos_batch_info(b)
     stream = torch.cuda.Stream()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    flush = None if args.no_flush else torch.empty(64 * 1024 * 1024, dtype=torch.float32,
+                                                   device="cuda")  # 256 MiB > L2
 
     def launch():
         m.mdeos_batch_launch(b, stream.cuda_stream)
@@ -203,6 +209,8 @@ def ours(args):
     res = m.mdeos_batch_results(b, nbox)
     assert (res["status"] == 0).all(), np.unique(res["status"], return_counts=True)
     total_steps = np.array([r["steps_equil"] + r["steps_avg"] for r in reqs], dtype=np.float64)
+    nl_mask = res["path"] == m.PATH_NLIST
+    rebuild_every = float(np.mean(total_steps[nl_mask] / np.maximum(res["nlist_builds"][nl_mask], 1)))
     pairs_per_launch = float((res["pairs_per_step"] * total_steps).sum())
     cand_per_launch = float((res["cand_per_step"] * total_steps).sum())
 
@@ -216,7 +224,8 @@ def ours(args):
     t0 = time.perf_counter()
     for k in range(args.steps):
         with torch.cuda.stream(stream):
-            flush.fill_(float(k))  # evict L2 between timed iterations (outside the events)
+            if flush is not None:
+                flush.fill_(float(k))  # evict L2 between timed iterations (outside the events)
             ev[k][0].record(stream)
             launch()
             ev[k][1].record(stream)
@@ -261,6 +270,7 @@ def ours(args):
         "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flop x {fmax:.0f} MHz (max SM clock)",
         "flops_basis": f"{FLOPS_PER_PAIR} flop x in-cutoff ordered pairs counted in this run",
         "pairs_per_launch": pairs_per_launch, "candidates_per_launch": cand_per_launch,
+        "verlet_rebuild_every_steps": rebuild_every,
     }
     if clk.get("sm_mhz"):
         roofline["frac_at_median_clock"] = achieved / (nsm * 256 * clk["sm_mhz"] * 1e6 / 1e12)
@@ -281,7 +291,9 @@ def ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded LJ boxes; no datasets or trained weights)",
-            "config": {"workload": WORKLOAD, "boxes_per_gpu": nbox,
+            "config": {"workload": WORKLOAD if not (args.boxes or args.md_steps) else
+                       f"reduced: {nbox} boxes x {args.md_steps or 2000} steps of " + WORKLOAD,
+                       "boxes_per_gpu": nbox,
                        "l2": "flushed between timed iterations (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (independent boxes)",
                        "plan": info},
@@ -305,6 +317,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush (profiling)")
+    ap.add_argument("--boxes", type=int, default=0, help="reduced box count (profiling)")
+    ap.add_argument("--md-steps", type=int, default=0, help="reduced MD steps per box")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

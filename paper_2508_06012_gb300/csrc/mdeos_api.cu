@@ -186,8 +186,11 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx) 
     while (nc > 3 && nc * nc * nc > kMaxCells) --nc;
     b.nc_cell = nc >= 3 ? nc : 0;
     p.ncell = nc >= 3 ? nc * nc * nc : 1;
+    // capacity from the liquid density at least: dilute boxes inside the
+    // liquid-vapour coexistence region form droplets of liquid density
     const double expect = 4.18879020478639 * rs * rs * rs * r.rho;
-    int mx = (int)std::ceil(1.35 * expect + 24.0);
+    const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(r.rho, 0.9);
+    int mx = (int)std::ceil(1.3 * expect_cap + 32.0);
     mx = std::min(mx, n - 1);
     b.maxnb = (mx + 3) & ~3;
     p.cost = steps * n * (expect * 1.0 + 8.0);

@@ -10,7 +10,7 @@ namespace mdeos {
 __global__ void __launch_bounds__(kCtaThreads, 1)
     eos_batch_kernel(const BoxDesc* __restrict__ boxes, const WorkItem* __restrict__ items,
                      int nitems, int* __restrict__ counter, mdeos_result* __restrict__ results,
-                     uint16_t* __restrict__ nl_scratch, long long nl_elems_per_cta, RunParams rp) {
+                     uint16_t* nl_scratch, long long nl_elems_per_cta, RunParams rp) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_item;
   uint16_t* nl_cta = nl_scratch + (long long)blockIdx.x * nl_elems_per_cta;

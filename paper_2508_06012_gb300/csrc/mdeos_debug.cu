@@ -107,6 +107,7 @@ __device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams
     int np = 0;
     compute_forces<APT, PATH, false, false, false>(g, b, rp, cnt, e0, w0, np);
   }
+  gbar(g.bar, g.nt);  // every force loop has read the positions before any atom moves
   for (int s = 0; s < steps; ++s) {
     const bool need = kick_drift<APT>(g, b, rp, 1.0f, disp);
     if (PATH == PATH_NLIST) {

@@ -81,8 +81,8 @@ __device__ __forceinline__ void philox4x32_10(uint32_t (&c)[4], uint32_t k0, uin
 
 // FP64 accumulator slots (group shared memory)
 enum { ACC_BP = 0, ACC_BT = kMaxSeBlocks, ACC_RUN = 2 * kMaxSeBlocks, ACC_BOX = 2 * kMaxSeBlocks + 16 };
-// running sums at ACC_RUN + k: 0..5 stress, 6 E_pot, 7 E_kin, 8 P, 9 T, 10 lifting E_pot sample,
-// 11 in-cutoff pairs, 12 candidates; box constants at ACC_BOX + 0..3
+// running sums at ACC_RUN + k: 0..5 stress / V, 6 E_pot, 7 E_kin, 8 in-cutoff pairs,
+// 9 candidates, 10 P, 11 T, 12 lifting E_pot sample; box constants at ACC_BOX + 0..3
 enum { CTRL_STATUS = 0, CTRL_OVERFLOW = 1 };
 
 struct Group {
@@ -195,8 +195,16 @@ __device__ __forceinline__ void lj_pair(float dx, float dy, float dz, bool ok, c
   npair += in ? 1 : 0;
 }
 
+// Round to the nearest integer (ties to even) on the FP32 adder: adding and
+// subtracting 1.5 * 2^23 leaves no fraction bits for |x| < 2^22.  Same result as
+// rintf, without the conversion pipe.
+__device__ __forceinline__ float round_nearest(float x) {
+  const float magic = 12582912.0f;
+  return __fsub_rn(__fadd_rn(x, magic), magic);
+}
+
 __device__ __forceinline__ float min_img(float d, float L, float invL) {
-  return fmaf(-L, rintf(d * invL), d);
+  return fmaf(-L, round_nearest(d * invL), d);
 }
 
 template <bool EN, bool VIR>
@@ -226,12 +234,14 @@ __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, 
       float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       int np = 0;
       if (PATH == PATH_NLIST) {
-        const uint2* __restrict__ p = reinterpret_cast<const uint2*>(g.nl) + i;
+        // The list is rewritten inside this kernel at every rebuild, so it must not
+        // go through the non-coherent read-only cache: L2-only loads.
+        const uint2* p = reinterpret_cast<const uint2*>(g.nl) + i;
         const int c = cnt[a];
         const int nfull = c >> 2;
 #pragma unroll 2
         for (int kb = 0; kb < nfull; ++kb) {
-          const uint2 q = p[(size_t)kb * g.npad];
+          const uint2 q = __ldcg(p + (size_t)kb * g.npad);
           nl_pair<EN, VIR>(xs, (int)(q.x & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
           nl_pair<EN, VIR>(xs, (int)(q.x >> 16), xi, b, rp, fx, fy, fz, e, w, np);
           nl_pair<EN, VIR>(xs, (int)(q.y & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
@@ -239,7 +249,7 @@ __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, 
         }
         const int rem = c & 3;
         if (rem) {
-          const uint2 q = p[(size_t)nfull * g.npad];
+          const uint2 q = __ldcg(p + (size_t)nfull * g.npad);
           nl_pair<EN, VIR>(xs, (int)(q.x & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
           if (rem > 1) nl_pair<EN, VIR>(xs, (int)(q.x >> 16), xi, b, rp, fx, fy, fz, e, w, np);
           if (rem > 2) nl_pair<EN, VIR>(xs, (int)(q.y & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
@@ -583,7 +593,6 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   const BoxCtx b = make_ctx(bd, rp);
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
-  const float ndof_f = (float)ndof;
   const double V = bd.L * bd.L * bd.L;
   const bool temp_mode = (bd.flags & MDEOS_REQ_TEMPERATURE) != 0;
   float disp[APT];
@@ -637,6 +646,9 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   const int nb = rp.se_blocks;
 
   if (status == MDEOS_OK) init_velocities<APT>(g, b, bd.seed, Tk, rp);
+  const float invV_f = (float)(1.0 / V), inv3V_f = (float)(1.0 / (3.0 * V));
+  const float inv_ndof_f = (float)(1.0 / ndof);
+  const int lead = (g.bar - 1) & 3 & (g.nwarps - 1);  // spreads group leaders over SMSPs
   float lam = 1.0f;
   float Tk_f = (float)Tk;
   if (g.tid == 0) boxc[3] = Tk;
@@ -720,39 +732,42 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
     gbar(g.bar, g.nt);
     float ke_tot = 0.f;
     for (int w = 0; w < g.nwarps; ++w) ke_tot += g.red()[w * kRedSlots + 7];
-    const float T_inst = 2.0f * ke_tot / ndof_f;
-    if (g.warp() == 0) {
+    const float T_inst = 2.0f * ke_tot * inv_ndof_f;
+    if (g.warp() == lead) {
+      // Per-step sums of the warp partials stay FP32 (<= 32 terms); each lane then
+      // adds one quantity into its FP64 time accumulator, so a step costs one
+      // convert and one FP64 add per warp instead of one per quantity.
       const int lane = g.lane();
-      double q = 0.0;
-      const bool need_q = (lane == 7) || (lane == 6 && (avg || esamp)) || (lane < 6 && avg) ||
-                          ((lane == 8 || lane == 9) && avg);
-      if (need_q)
-        for (int w = 0; w < g.nwarps; ++w) q += (double)g.red()[w * kRedSlots + lane];
-      if (esamp && lane == 6) acc[ACC_RUN + 10] += q;
-      const double invV = 1.0 / V, inv_ndof = 1.0 / ndof;
+      float q = 0.f;
+      if (lane < kRedSlots)
+        for (int w = 0; w < g.nwarps; ++w) q += g.red()[w * kRedSlots + lane];
+      const float s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
+      const float s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
+      const float e6 = __shfl_sync(0xffffffffu, q, 6);
+      const float Ps = (s0 + s1 + s2) * inv3V_f;   // Eq. 11, mean normal stress
+      const float Ts = 2.0f * k7 * inv_ndof_f;
+      int slot = -1;
+      float val = 0.f;
       if (avg) {
-        if (lane < 8) acc[ACC_RUN + lane] += (lane < 6) ? q * invV : q;
-        if (lane == 8 || lane == 9) acc[ACC_RUN + 3 + lane] += q;
-        const double s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
-        const double s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
-        const double e6 = __shfl_sync(0xffffffffu, q, 6);
-        if (lane == 0) {
-          const double Ps = (s0 + s1 + s2) * (invV / 3.0);
-          const double Ts = 2.0 * k7 * inv_ndof;
-          acc[ACC_RUN + 8] += Ps;
-          acc[ACC_RUN + 9] += Ts;
-          const int blk = (int)((long long)s_avg * nb / bd.steps_avg);
-          acc[ACC_BP + blk] += Ps;
-          acc[ACC_BT + blk] += Ts;
-          g.bcnt()[blk] += 1;
-          if (!isfinite(Ps) || !isfinite(Ts) || !isfinite(e6)) g.ctrl()[CTRL_STATUS] = MDEOS_EUNPHYS;
-        }
+        const int blk = (s_avg * nb) / bd.steps_avg;
+        if (lane < 6) { slot = ACC_RUN + lane; val = q * invV_f; }
+        else if (lane < 10) { slot = ACC_RUN + lane; val = q; }
+        else if (lane == 10) { slot = ACC_RUN + 10; val = Ps; }
+        else if (lane == 11) { slot = ACC_RUN + 11; val = Ts; }
+        else if (lane == 12) { slot = ACC_BP + blk; val = Ps; g.bcnt()[blk] += 1; }
+        else if (lane == 13) { slot = ACC_BT + blk; val = Ts; }
+        if (lane == 10 && (!isfinite(Ps) || !isfinite(Ts) || !isfinite(e6)))
+          g.ctrl()[CTRL_STATUS] = MDEOS_EUNPHYS;
+      } else if (esamp && lane == 6) {
+        slot = ACC_RUN + 12;
+        val = q;
       }
+      if (slot >= 0) acc[slot] += (double)val;
       if (seg_end && lane == 6) {
-        const double Ebar = acc[ACC_RUN + 10] / nsamp;
-        const double Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) * inv_ndof;  // Eq. 10
+        const double Ebar = acc[ACC_RUN + 12] / nsamp;
+        const double Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) / ndof;  // Eq. 10
         g.bc()[0] = Tn;
-        acc[ACC_RUN + 10] = 0.0;
+        acc[ACC_RUN + 12] = 0.0;
       }
     }
     if (!(T_inst > 0.f) || !isfinite(T_inst)) {
@@ -790,8 +805,8 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
     const double m = bd.steps_avg;
     mdeos_result r;
     for (int k = 0; k < 6; ++k) r.sigma[k] = acc[ACC_RUN + k] / m;
-    r.P = acc[ACC_RUN + 8] / m;
-    r.T = acc[ACC_RUN + 9] / m;
+    r.P = acc[ACC_RUN + 10] / m;
+    r.T = acc[ACC_RUN + 11] / m;
     r.epot = acc[ACC_RUN + 6] / m / n;
     r.ekin = acc[ACC_RUN + 7] / m / n;
     r.e_achieved = (acc[ACC_RUN + 7] / m + acc[ACC_RUN + 6] / m - E_ref) / n;
@@ -815,8 +830,8 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
     r.T_target = Tk;
     r.e_cold = E_cold / n;
     r.L = bd.L;
-    r.pairs_per_step = acc[ACC_RUN + 11] / m;
-    r.cand_per_step = acc[ACC_RUN + 12] / m;
+    r.pairs_per_step = acc[ACC_RUN + 8] / m;
+    r.cand_per_step = acc[ACC_RUN + 9] / m;
     r.element_id = bd.element_id;
     r.natoms = n;
     r.status = status;
