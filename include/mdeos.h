@@ -171,6 +171,34 @@ mdeos_status mdeos_batch_info(const mdeos_batch* b, int32_t* n_items, int32_t* n
 mdeos_status mdeos_stats(const mdeos_handle* h, size_t* last_h2d_bytes, size_t* last_d2h_bytes,
                          long long* kernel_launches, size_t* device_bytes);
 
+/* ---- evaluation without device allocation -----------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they need an EOS answer (a material-model
+ * callback inside a hydrocode's time step, where cudaMalloc would synchronise
+ * the device; code whose device memory is owned by a pool; host threads that
+ * must not block).  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Its work table, queue counter and Verlet lists live in a static
+ * device array of MDEOS_NOALLOC_SCRATCH_BYTES that every GPU loading this
+ * library holds until exit.
+ *
+ * cfg:       host, copied; cfg->device must be the calling thread's current device.
+ * reqs:      host array of n requests, copied before return.
+ * d_results: device array of n mdeos_result, caller-owned; written in request
+ *            order when the work on `stream` completes (requests rejected by
+ *            the planner get their status there too).
+ * stream:    cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The first call on a device looks up the static array's device address and
+ * sets the kernel's shared-memory limit; make that first call before any
+ * stream capture.  Every call reuses the same array (it keeps the previous
+ * call's contents; the call clears what must start at zero): calls whose work
+ * overlaps on the GPU race, so serialise them (one stream, or events).  A batch
+ * whose work table plus one CTA's Verlet lists exceed the array is rejected
+ * with MDEOS_EINVAL; smaller scratch per CTA runs on fewer CTAs.
+ * Errors: MDEOS_EINVAL, MDEOS_ECUDA. */
+#define MDEOS_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)
+mdeos_status mdeos_submit_noalloc(const mdeos_config* cfg, const mdeos_request* reqs, int32_t n,
+                                  mdeos_result* d_results, void* stream);
+
 /* ---- single-box kernels exposed for parity tests ----------------------
  * These run one box through the same device code as the batch path. */
 

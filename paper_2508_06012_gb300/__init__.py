@@ -27,7 +27,7 @@ EXPORTED = [
     "mdeos_last_error", "mdeos_batch_create", "mdeos_batch_launch",
     "mdeos_batch_device_results", "mdeos_batch_results", "mdeos_batch_destroy",
     "mdeos_batch_info", "mdeos_stats", "mdeos_debug_lift", "mdeos_debug_forces",
-    "mdeos_debug_md",
+    "mdeos_debug_md", "mdeos_submit_noalloc",
 ]
 
 
@@ -123,6 +123,7 @@ def lib():
         L.mdeos_debug_forces.argtypes = [P(mdeos_config), vp, i32, d, i32, d, vp, vp, vp, vp]
         L.mdeos_debug_md.argtypes = [P(mdeos_config), vp, vp, i32, d, i32, d, i32, i32, d, vp,
                                      vp, vp]
+        L.mdeos_submit_noalloc.argtypes = [P(mdeos_config), vp, i32, vp, vp]
         for name in EXPORTED:
             fn = getattr(L, name)
             if name not in ("mdeos_config_default", "mdeos_last_error",
@@ -229,6 +230,17 @@ def mdeos_stats(h) -> dict:
     _check(lib().mdeos_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                              ctypes.byref(d)))
     return {"h2d": a.value, "d2h": b.value, "launches": c.value, "device_bytes": d.value}
+
+
+def mdeos_submit_noalloc(reqs, d_results_ptr: int, cfg: mdeos_config | None = None,
+                         stream: int | None = None) -> None:
+    """Queue a batch without any device allocation by the library; results land in
+    the caller's device array at d_results_ptr (n records) when the stream reaches it."""
+    arr = as_requests(reqs)
+    cfg = cfg or mdeos_config_default()
+    _check(lib().mdeos_submit_noalloc(ctypes.byref(cfg), arr.ctypes.data_as(ctypes.c_void_p),
+                                      len(arr), ctypes.c_void_p(d_results_ptr),
+                                      ctypes.c_void_p(stream or 0)))
 
 
 def _dptr(t) -> ctypes.c_void_p:

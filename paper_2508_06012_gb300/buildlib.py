@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdeos.so")
-SOURCES = ["mdeos_batch.cu", "mdeos_debug.cu", "mdeos_api.cu"]
+SOURCES = ["mdeos_batch.cu", "mdeos_debug.cu", "mdeos_noalloc.cu", "mdeos_api.cu"]
 HEADERS = ["mdeos_device.cuh", "mdeos_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -287,6 +287,40 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
   return MDEOS_OK;
 }
 
+namespace mdeos {
+mdeos_status set_error(mdeos_status st, const std::string& msg) { return fail(st, msg); }
+
+// Planning for the no-allocation entry point (mdeos_noalloc.cu): validation,
+// packing and the host copy of the initial results, all in host memory.
+mdeos_status plan_for_noalloc(const mdeos_request* reqs, int n, const mdeos_config& c, int nsm,
+                              int smem_max, std::vector<BoxDesc>& boxes,
+                              std::vector<WorkItem>& items, std::vector<mdeos_result>& init,
+                              int& grid, int& smem, long long& nl_per_cta, RunParams& rp);
+}  // namespace mdeos
+
+static void planning_result(mdeos_result& r, int status, const mdeos_request& q);
+
+mdeos_status mdeos::plan_for_noalloc(const mdeos_request* reqs, int n, const mdeos_config& c,
+                                     int nsm, int smem_max, std::vector<BoxDesc>& boxes,
+                                     std::vector<WorkItem>& items,
+                                     std::vector<mdeos_result>& init, int& grid, int& smem,
+                                     long long& nl_per_cta, RunParams& rp) {
+  mdeos_status st = check_config(&c);
+  if (st != MDEOS_OK) return st;
+  Plan plan;
+  st = make_plan(reqs, n, c, nsm, smem_max, plan);
+  if (st != MDEOS_OK) return st;
+  boxes = plan.boxes;
+  items = plan.items;
+  init.resize(n);
+  for (int i = 0; i < n; ++i) planning_result(init[i], plan.status[i], reqs[i]);
+  grid = plan.grid;
+  smem = plan.smem;
+  nl_per_cta = plan.nl_per_cta;
+  rp = make_run_params(&c);
+  return MDEOS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // handle
 
