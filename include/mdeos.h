@@ -223,10 +223,14 @@ mdeos_status mdeos_debug_forces(const mdeos_config* cfg, const float* x4, int32_
  * for `steps` steps, rescaling velocities to T_target every rescale_every
  * steps (0 = NVE).  Per-step E_pot and E_kin go to device double[steps]
  * arrays epot/ekin (either may be NULL).  Positions are returned wrapped
- * into [0, L). */
+ * into [0, L).  If cycles != NULL (device int64[11]) it receives the SM
+ * cycles spent in drift, list builds, forces and kick + reductions, the number
+ * of list builds, and the list build's phases (count, scan, scatter, cell sort,
+ * permute, search). */
 mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float* v4, int32_t n, double L,
                             int32_t steps, double T_target, int32_t rescale_every, int32_t path,
-                            double skin, double* epot, double* ekin, void* stream);
+                            double skin, double* epot, double* ekin, long long* cycles,
+                            void* stream);
 
 #ifdef __cplusplus
 }

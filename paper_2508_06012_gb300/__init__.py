@@ -122,7 +122,7 @@ def lib():
                                        P(d), vp]
         L.mdeos_debug_forces.argtypes = [P(mdeos_config), vp, i32, d, i32, d, vp, vp, vp, vp]
         L.mdeos_debug_md.argtypes = [P(mdeos_config), vp, vp, i32, d, i32, d, i32, i32, d, vp,
-                                     vp, vp]
+                                     vp, vp, vp]
         L.mdeos_submit_noalloc.argtypes = [P(mdeos_config), vp, i32, vp, vp]
         for name in EXPORTED:
             fn = getattr(L, name)
@@ -281,8 +281,9 @@ def mdeos_debug_forces(x4, L: float, path: int, skin: float = 0.3,
 
 def mdeos_debug_md(x4, v4, L: float, steps: int, path: int, skin: float = 0.3,
                    T_target: float = 0.0, rescale_every: int = 0,
-                   cfg: mdeos_config | None = None, stream=None):
-    """Device velocity-Verlet on one box, in place; returns (epot[steps], ekin[steps])."""
+                   cfg: mdeos_config | None = None, stream=None, cycles=None):
+    """Device velocity-Verlet on one box, in place; returns (epot[steps], ekin[steps]).
+    `cycles`, if given, is a cuda int64 tensor of 11 receiving per-phase SM cycles."""
     import torch
     cfg = cfg or mdeos_config_default()
     n = x4.shape[0]
@@ -290,6 +291,7 @@ def mdeos_debug_md(x4, v4, L: float, steps: int, path: int, skin: float = 0.3,
     ek = torch.zeros(max(steps, 1), dtype=torch.float64, device=x4.device)
     _check(lib().mdeos_debug_md(ctypes.byref(cfg), _dptr(x4), _dptr(v4), n, L, steps, T_target,
                                 rescale_every, path, skin, _dptr(ep), _dptr(ek),
+                                _dptr(cycles) if cycles is not None else ctypes.c_void_p(0),
                                 _stream_ptr(stream)))
     return ep[:steps], ek[:steps]
 

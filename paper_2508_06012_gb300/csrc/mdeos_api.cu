@@ -31,7 +31,8 @@ cudaError_t launch_debug_forces(const BoxDesc& bd, const RunParams& rp, int apt,
                                 long long* pairs, uint16_t* nl, cudaStream_t st);
 cudaError_t launch_debug_md(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
                             int smem, float4* x4, float4* v4, int steps, double T, int every,
-                            double* ep, double* ek, uint16_t* nl, cudaStream_t st);
+                            double* ep, double* ek, long long* cyc, uint16_t* nl,
+                            cudaStream_t st);
 }  // namespace mdeos
 
 using namespace mdeos;
@@ -192,7 +193,7 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx) 
     const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(r.rho, 0.9);
     int mx = (int)std::ceil(1.3 * expect_cap + 32.0);
     mx = std::min(mx, n - 1);
-    b.maxnb = (mx + 3) & ~3;
+    b.maxnb = (mx + 7) & ~7;  // whole 8-entry list words
     p.cost = steps * n * (expect * 1.0 + 8.0);
   } else {
     b.skin = 0.f;
@@ -256,7 +257,7 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
     std::memset(&wi, 0, sizeof(wi));
     wi.warps_per_box = warps;
     wi.apt = apt;
-    int ncell_cap = 1, maxnb = 4;
+    int ncell_cap = 1, maxnb = 8;
     double cost = 0.0;
     int nb = 0;
     while (k < bp.size() && bp[k].warps == warps && bp[k].apt == apt && nb < per_cta) {
@@ -274,7 +275,7 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
     wi.nbox = nb;
     wi.ncell_cap = ncell_cap;
     wi.smem_stride = group_smem_bytes(warps, apt, ncell_cap);
-    wi.nl_stride = ((maxnb + 3) & ~3) * npad;
+    wi.nl_stride = ((maxnb + 7) & ~7) * npad;
     plan.smem = std::max(plan.smem, nb * wi.smem_stride);
     plan.nl_per_cta = std::max(plan.nl_per_cta, (long long)nb * wi.nl_stride);
     items.push_back({wi, cost});
@@ -769,7 +770,7 @@ static mdeos_status debug_setup(const mdeos_config* cfg, int n, double L, int pa
     while (nc > 3 && nc * nc * nc > kMaxCells) --nc;
     bd.nc_cell = nc >= 3 ? nc : 0;
     ncell = nc >= 3 ? nc * nc * nc : 1;
-    bd.maxnb = std::max(4, ((n - 1) + 3) & ~3);  // room for every atom: no overflow in tests
+    bd.maxnb = std::max(8, ((n - 1) + 7) & ~7);  // room for every atom: no overflow in tests
     nl_bytes = (size_t)bd.maxnb * kCtaThreads * apt * sizeof(uint16_t);
   }
   smem = group_smem_bytes(32, apt, ncell);
@@ -821,7 +822,8 @@ extern "C" mdeos_status mdeos_debug_forces(const mdeos_config* cfg, const float*
 extern "C" mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float* v4, int32_t n,
                                        double L, int32_t steps, double T_target,
                                        int32_t rescale_every, int32_t path, double skin,
-                                       double* epot, double* ekin, void* stream) {
+                                       double* epot, double* ekin, long long* cycles,
+                                       void* stream) {
   if (!x4 || !v4 || steps < 0 || rescale_every < 0) return fail(MDEOS_EINVAL, "bad arguments");
   BoxDesc bd;
   RunParams rp;
@@ -833,7 +835,7 @@ extern "C" mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float
   uint16_t* nl = nullptr;
   if (nlb) CK(cudaMallocAsync(&nl, nlb, s));
   cudaError_t e = launch_debug_md(bd, rp, apt, ncell, smem, (float4*)x4, (float4*)v4, steps,
-                                  T_target, rescale_every, epot, ekin, nl, s);
+                                  T_target, rescale_every, epot, ekin, cycles, nl, s);
   if (nl) cudaFreeAsync(nl, s);
   if (e != cudaSuccess) return cuda_fail(e, "debug_md launch");
   CK(cudaStreamSynchronize(s));

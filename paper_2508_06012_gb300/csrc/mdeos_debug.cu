@@ -8,20 +8,18 @@ template <int APT>
 __device__ void debug_lift_body(const Group& g, const BoxDesc& bd, const RunParams& rp, double T,
                                 float4* x4, float4* v4, double* e_out) {
   const BoxCtx b = make_ctx(bd, rp);
-  int cnt[APT];
-  for (int a = 0; a < APT; ++a) cnt[a] = 0;
   if (g.tid < 16) g.ctrl()[g.tid] = 0;
   lattice_own<APT>(g, bd);
   gbar(g.bar, g.nt);
   float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int np = 0;
   if (bd.path == PATH_NLIST) {
-    build_nlist<APT>(g, b, cnt);
-    compute_forces<APT, PATH_NLIST, true, false, false>(g, b, rp, cnt, e0, w0, np);
+    build_nlist<APT>(g, b);
+    compute_forces<APT, PATH_NLIST, true, false, false>(g, b, rp, e0, w0, np);
   } else if (bd.path == PATH_ALLPAIRS_MI) {
-    compute_forces<APT, PATH_ALLPAIRS_MI, true, false, false>(g, b, rp, cnt, e0, w0, np);
+    compute_forces<APT, PATH_ALLPAIRS_MI, true, false, false>(g, b, rp, e0, w0, np);
   } else {
-    compute_forces<APT, PATH_ALLPAIRS, true, false, false>(g, b, rp, cnt, e0, w0, np);
+    compute_forces<APT, PATH_ALLPAIRS, true, false, false>(g, b, rp, e0, w0, np);
   }
   double et[1];
   float q[1] = {e0};
@@ -30,8 +28,10 @@ __device__ void debug_lift_body(const Group& g, const BoxDesc& bd, const RunPara
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
     if (i < b.n) {
-      x4[i] = g.x()[i];
-      v4[i] = g.v()[i];
+      const float4 xi = g.x()[i];
+      const int id = __float_as_int(xi.w);
+      x4[id] = make_float4(xi.x, xi.y, xi.z, 0.f);
+      v4[id] = g.v()[i];
     }
   }
   if (g.tid == 0) e_out[0] = 0.5 * et[0];
@@ -41,31 +41,37 @@ template <int APT, int PATH>
 __device__ void debug_forces_body(const Group& g, const BoxDesc& bd, const RunParams& rp,
                                   const float4* x4, float4* f4, double* ew, long long* pairs) {
   const BoxCtx b = make_ctx(bd, rp);
-  int cnt[APT];
   for (int a = 0; a < APT; ++a) {
-    cnt[a] = 0;
     const int i = g.tid + a * g.nt;
-    if (i < b.n) g.x()[i] = x4[i];
+    if (i < b.n) {
+      const float4 xi = x4[i];
+      g.x()[i] = make_float4(xi.x, xi.y, xi.z, __int_as_float(i));
+      g.v()[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
   if (g.tid < 16) g.ctrl()[g.tid] = 0;
   gbar(g.bar, g.nt);
   if (PATH == PATH_NLIST) {
-    // the list is built from wrapped positions; forces use the originals
-    float disp[APT];
-    wrap_own<APT>(g, b, disp);
-    build_nlist<APT>(g, b, cnt);
+    // the list is built from wrapped positions (and may re-order the atoms);
+    // forces use the positions as given
+    wrap_own<APT>(g, b);
+    build_nlist<APT>(g, b);
     for (int a = 0; a < APT; ++a) {
       const int i = g.tid + a * g.nt;
-      if (i < b.n) g.x()[i] = x4[i];
+      if (i < b.n) {
+        const float4 xo = g.x()[i];
+        const float4 xi = x4[__float_as_int(xo.w)];
+        g.x()[i] = make_float4(xi.x, xi.y, xi.z, xo.w);
+      }
     }
     gbar(g.bar, g.nt);
   }
   float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int np = 0;
-  compute_forces<APT, PATH, true, true, true>(g, b, rp, cnt, e, w, np);
+  compute_forces<APT, PATH, true, true, true>(g, b, rp, e, w, np);
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
-    if (i < b.n) f4[i] = g.f()[i];
+    if (i < b.n) f4[__float_as_int(g.x()[i].w)] = g.f()[i];
   }
   float q[8] = {0.5f * e,    0.5f * w[0], 0.5f * w[1], 0.5f * w[2],
                 0.5f * w[3], 0.5f * w[4], 0.5f * w[5], (float)np};
@@ -81,46 +87,54 @@ __device__ void debug_forces_body(const Group& g, const BoxDesc& bd, const RunPa
 template <int APT, int PATH>
 __device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams& rp, float4* x4,
                               float4* v4, int steps, double T_target, int rescale_every,
-                              double* epot, double* ekin) {
+                              double* epot, double* ekin, long long* cyc) {
+  // cyc (optional): SM cycles seen by thread 0 in [drift, list build, forces,
+  // kick + reductions] summed over the steps, the number of list builds, and
+  // the build's phases [count, scan, scatter, cell sort, permute, search]
+  long long c_drift = 0, c_build = 0, c_force = 0, c_red = 0, nbuild = 0;
+  long long bph[6] = {0, 0, 0, 0, 0, 0};
   const BoxCtx b = make_ctx(bd, rp);
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
-  int cnt[APT];
-  float disp[APT];
   for (int a = 0; a < APT; ++a) {
-    cnt[a] = 0;
-    disp[a] = 0.f;
     const int i = g.tid + a * g.nt;
     if (i < n) {
-      g.x()[i] = x4[i];
-      g.v()[i] = v4[i];
+      const float4 xi = x4[i], vi = v4[i];
+      g.x()[i] = make_float4(xi.x, xi.y, xi.z, __int_as_float(i));
+      g.v()[i] = make_float4(vi.x, vi.y, vi.z, 0.f);
     }
   }
   if (g.tid < 16) g.ctrl()[g.tid] = 0;
   gbar(g.bar, g.nt);
   if (PATH == PATH_NLIST) {
-    wrap_own<APT>(g, b, disp);
-    build_nlist<APT>(g, b, cnt);
+    wrap_own<APT>(g, b);
+    build_nlist<APT>(g, b);
   }
   {
     float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int np = 0;
-    compute_forces<APT, PATH, false, false, false>(g, b, rp, cnt, e0, w0, np);
+    compute_forces<APT, PATH, false, false, false>(g, b, rp, e0, w0, np);
   }
   gbar(g.bar, g.nt);  // every force loop has read the positions before any atom moves
   for (int s = 0; s < steps; ++s) {
-    const bool need = kick_drift<APT>(g, b, rp, 1.0f, disp);
+    const long long t0 = clock64();
+    const bool need = kick_drift<APT>(g, b, rp, 1.0f);
+    bool rebuilt = false;
     if (PATH == PATH_NLIST) {
-      if (gbar_or(g.bar, g.nt, need)) {
-        wrap_own<APT>(g, b, disp);
-        build_nlist<APT>(g, b, cnt);
-      }
+      rebuilt = gbar_or(g.bar, g.nt, need);
     } else {
       gbar(g.bar, g.nt);
     }
+    const long long t1 = clock64();
+    if (rebuilt) {
+      wrap_own<APT>(g, b);
+      build_nlist<APT>(g, b, cyc ? bph : nullptr);
+    }
+    const long long t2 = clock64();
     float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int np = 0;
-    compute_forces<APT, PATH, true, false, false>(g, b, rp, cnt, e, w, np);
+    compute_forces<APT, PATH, true, false, false>(g, b, rp, e, w, np);
+    const long long t3 = clock64();
     float ke = 0.f;
     for (int a = 0; a < APT; ++a) {
       const int i = g.tid + a * g.nt;
@@ -140,6 +154,12 @@ __device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams
     if (g.tid == 0) {
       if (epot) epot[s] = tot[0];
       if (ekin) ekin[s] = tot[1];
+      const long long t4 = clock64();
+      c_drift += t1 - t0;
+      c_build += t2 - t1;
+      c_force += t3 - t2;
+      c_red += t4 - t3;
+      nbuild += rebuilt ? 1 : 0;
     }
     if (rescale_every > 0 && (s + 1) % rescale_every == 0) {
       const float lam = (float)sqrt(T_target / (2.0 * tot[1] / ndof));
@@ -155,13 +175,23 @@ __device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams
       }
     }
   }
-  wrap_own<APT>(g, b, disp);
+  wrap_own<APT>(g, b);
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
     if (i < n) {
-      x4[i] = g.x()[i];
-      v4[i] = g.v()[i];
+      const float4 xi = g.x()[i], vi = g.v()[i];
+      const int id = __float_as_int(xi.w);
+      x4[id] = make_float4(xi.x, xi.y, xi.z, 0.f);
+      v4[id] = make_float4(vi.x, vi.y, vi.z, 0.f);
     }
+  }
+  if (cyc && g.tid == 0) {
+    cyc[0] = c_drift;
+    cyc[1] = c_build;
+    cyc[2] = c_force;
+    cyc[3] = c_red;
+    cyc[4] = nbuild;
+    for (int k = 0; k < 6; ++k) cyc[5 + k] = bph[k];
   }
 }
 
@@ -203,27 +233,31 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
 
 template <int APT>
 __device__ void debug_md_path(const Group& g, const BoxDesc& bd, const RunParams& rp, float4* x4,
-                              float4* v4, int steps, double T, int every, double* ep, double* ek) {
+                              float4* v4, int steps, double T, int every, double* ep, double* ek,
+                              long long* cyc) {
   switch (bd.path) {
     case PATH_NLIST:
-      debug_md_body<APT, PATH_NLIST>(g, bd, rp, x4, v4, steps, T, every, ep, ek);
+      debug_md_body<APT, PATH_NLIST>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc);
       break;
     case PATH_ALLPAIRS_MI:
-      debug_md_body<APT, PATH_ALLPAIRS_MI>(g, bd, rp, x4, v4, steps, T, every, ep, ek);
+      debug_md_body<APT, PATH_ALLPAIRS_MI>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc);
       break;
-    default: debug_md_body<APT, PATH_ALLPAIRS>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
+    default:
+      debug_md_body<APT, PATH_ALLPAIRS>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc);
+      break;
   }
 }
 
 __global__ void __launch_bounds__(kCtaThreads, 1)
     debug_md_kernel(BoxDesc bd, RunParams rp, int apt, int ncell_cap, float4* x4, float4* v4,
-                    int steps, double T, int every, double* ep, double* ek, uint16_t* nl) {
+                    int steps, double T, int every, double* ep, double* ek, long long* cyc,
+                    uint16_t* nl) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Group g = make_group(smem, threadIdx.x, 32, apt, ncell_cap, 1, nl);
   switch (apt) {
-    case 1: debug_md_path<1>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
-    case 2: debug_md_path<2>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
-    default: debug_md_path<4>(g, bd, rp, x4, v4, steps, T, every, ep, ek); break;
+    case 1: debug_md_path<1>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc); break;
+    case 2: debug_md_path<2>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc); break;
+    default: debug_md_path<4>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc); break;
   }
 }
 
@@ -252,9 +286,10 @@ cudaError_t launch_debug_forces(const BoxDesc& bd, const RunParams& rp, int apt,
 
 cudaError_t launch_debug_md(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
                             int smem, float4* x4, float4* v4, int steps, double T, int every,
-                            double* ep, double* ek, uint16_t* nl, cudaStream_t st) {
+                            double* ep, double* ek, long long* cyc, uint16_t* nl,
+                            cudaStream_t st) {
   debug_md_kernel<<<1, kCtaThreads, smem, st>>>(bd, rp, apt, ncell_cap, x4, v4, steps, T, every,
-                                                ep, ek, nl);
+                                                ep, ek, cyc, nl);
   return cudaGetLastError();
 }
 

@@ -87,7 +87,7 @@ enum { CTRL_STATUS = 0, CTRL_OVERFLOW = 1 };
 
 struct Group {
   unsigned char* base;
-  uint16_t* nl;  // neighbour scratch: word (kb, i) at ((kb * npad + i) * 4) uint16 units
+  uint16_t* nl;  // neighbour scratch: word (kb, i) at ((kb * npad + i) * 8) uint16 units
   int tid, nt, bar, npad, nwarps, off_red;
   __device__ __forceinline__ int warp() const { return tid >> 5; }
   __device__ __forceinline__ int lane() const { return tid & 31; }
@@ -166,21 +166,36 @@ __device__ inline BoxCtx make_ctx(const BoxDesc& bd, const RunParams& rp) {
 //   f_ij = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2 * r_ij
 // `ok` masks the term (the atom itself, padding).
 
+// pair constants, passed by value into the force pass
+struct LJ {
+  float rc2, eps4, eps24, sig6, ucut;
+};
+
+__device__ __forceinline__ LJ make_lj(const RunParams& rp) {
+  LJ c;
+  c.rc2 = rp.rc2;
+  c.eps4 = rp.eps4;
+  c.eps24 = rp.eps24;
+  c.sig6 = rp.sig6;
+  c.ucut = rp.ucut;
+  return c;
+}
+
 template <bool EN, bool VIR>
-__device__ __forceinline__ void lj_pair(float dx, float dy, float dz, bool ok, const RunParams& rp,
+__device__ __forceinline__ void lj_pair(float dx, float dy, float dz, bool ok, const LJ& c,
                                         float& fx, float& fy, float& fz, float& e, float (&w)[6],
                                         int& npair) {
   float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  bool in = ok && (r2 < rp.rc2);
+  bool in = ok && (r2 < c.rc2);
   float ir2 = rcp_approx(r2);
-  float s6 = rp.sig6 * ir2 * ir2 * ir2;
-  float fr = rp.eps24 * s6 * fmaf(2.0f, s6, -1.0f) * ir2;
+  float s6 = c.sig6 * ir2 * ir2 * ir2;
+  float fr = c.eps24 * s6 * fmaf(2.0f, s6, -1.0f) * ir2;
   fr = in ? fr : 0.0f;
   fx = fmaf(fr, dx, fx);
   fy = fmaf(fr, dy, fy);
   fz = fmaf(fr, dz, fz);
   if (EN) {
-    float u = fmaf(rp.eps4 * s6, s6 - 1.0f, -rp.ucut);
+    float u = fmaf(c.eps4 * s6, s6 - 1.0f, -c.ucut);
     e += in ? u : 0.0f;
   }
   if (VIR) {
@@ -195,6 +210,16 @@ __device__ __forceinline__ void lj_pair(float dx, float dy, float dz, bool ok, c
   npair += in ? 1 : 0;
 }
 
+// 16-byte shared-memory load from a 32-bit shared address (the force pass is not
+// inlined, so its pointers would otherwise be generic)
+__device__ __forceinline__ float4 ld_shared4(uint32_t a) {
+  float4 v;
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "r"(a));
+  return v;
+}
+
 // Round to the nearest integer (ties to even) on the FP32 adder: adding and
 // subtracting 1.5 * 2^23 leaves no fraction bits for |x| < 2^22.  Same result as
 // rintf, without the conversion pipe.
@@ -207,109 +232,173 @@ __device__ __forceinline__ float min_img(float d, float L, float invL) {
   return fmaf(-L, round_nearest(d * invL), d);
 }
 
+// Verlet-list pair: minimum image across the periodic box; `ok` masks padding
 template <bool EN, bool VIR>
-__device__ __forceinline__ void nl_pair(const float4* __restrict__ xs, int j, const float4& xi,
-                                        const BoxCtx& b, const RunParams& rp, float& fx, float& fy,
-                                        float& fz, float& e, float (&w)[6], int& np) {
-  const float4 xj = xs[j];
-  float dx = min_img(xi.x - xj.x, b.L, b.invL);
-  float dy = min_img(xi.y - xj.y, b.L, b.invL);
-  float dz = min_img(xi.z - xj.z, b.L, b.invL);
-  lj_pair<EN, VIR>(dx, dy, dz, true, rp, fx, fy, fz, e, w, np);
+__device__ __forceinline__ void nl_pair_bd(uint32_t xs_a, int j, bool ok, const float4& xi,
+                                           float L, float invL, const LJ& c, float& fx, float& fy,
+                                           float& fz, float& e, float (&w)[6], int& np) {
+  const float4 xj = ld_shared4(xs_a + 16u * (uint32_t)j);
+  const float dx = min_img(xi.x - xj.x, L, invL);
+  const float dy = min_img(xi.y - xj.y, L, invL);
+  const float dz = min_img(xi.z - xj.z, L, invL);
+  lj_pair<EN, VIR>(dx, dy, dz, ok, c, fx, fy, fz, e, w, np);
 }
 
-// Forces on the thread's own atoms (written to g.f()), with optional energy,
-// virial and pair-count partials over ordered pairs (the caller halves E, W).
+// per-thread partial sums of one force pass
+struct FSums {
+  float e, w0, w1, w2, w3, w4, w5;
+  int np;
+};
+
+// Forces on the thread's own slots tid, tid + nt, ... (written to fs), with
+// optional energy, virial and pair-count partials over ordered pairs (the caller
+// halves E and W).  Not inlined and fed only scalars: it runs with the whole
+// register budget for the pair loop while the caller's step state is saved once
+// per call, and positions are read with explicit shared-memory loads.
 template <int APT, int PATH, bool EN, bool VIR, bool CNT>
-__device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, const RunParams& rp,
-                                               const int (&cnt)[APT], float& e_acc,
-                                               float (&w_acc)[6], int& pair_acc) {
-  const float4* __restrict__ xs = g.x();
-#pragma unroll
+__device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16_t* nl, int tid,
+                                         int nt, int npad, int n, int maxnb, float L, float invL,
+                                         LJ c) {
+  // energy, virial and pair count accumulate over all of the thread's atoms
+  float e = 0.f;
+  float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int np = 0;
+#pragma unroll 1
   for (int a = 0; a < APT; ++a) {
-    const int i = g.tid + a * g.nt;
-    if (i < b.n) {
-      const float4 xi = xs[i];
-      float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-      float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      int np = 0;
+    const int i = tid + a * nt;
+    if (i < n) {
+      const float4 xi = ld_shared4(xs_a + 16u * (uint32_t)i);
+      const float cw = fs[i].w;  // packed list lengths (Verlet path), kept across steps
+      float fx = 0.f, fy = 0.f, fz = 0.f;
       if (PATH == PATH_NLIST) {
-        // The list is rewritten inside this kernel at every rebuild, so it must not
-        // go through the non-coherent read-only cache: L2-only loads.
-        const uint2* p = reinterpret_cast<const uint2*>(g.nl) + i;
-        const int c = cnt[a];
-        const int nfull = c >> 2;
-#pragma unroll 2
-        for (int kb = 0; kb < nfull; ++kb) {
-          const uint2 q = __ldcg(p + (size_t)kb * g.npad);
-          nl_pair<EN, VIR>(xs, (int)(q.x & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
-          nl_pair<EN, VIR>(xs, (int)(q.x >> 16), xi, b, rp, fx, fy, fz, e, w, np);
-          nl_pair<EN, VIR>(xs, (int)(q.y & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
-          nl_pair<EN, VIR>(xs, (int)(q.y >> 16), xi, b, rp, fx, fy, fz, e, w, np);
-        }
-        const int rem = c & 3;
-        if (rem) {
-          const uint2 q = __ldcg(p + (size_t)nfull * g.npad);
-          nl_pair<EN, VIR>(xs, (int)(q.x & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
-          if (rem > 1) nl_pair<EN, VIR>(xs, (int)(q.x >> 16), xi, b, rp, fx, fy, fz, e, w, np);
-          if (rem > 2) nl_pair<EN, VIR>(xs, (int)(q.y & 0xffffu), xi, b, rp, fx, fy, fz, e, w, np);
+        // Row of slot i: eight uint16 entries per 16-byte word, word (k/8) of slot
+        // i at (k/8) * npad + i, so a warp's word loads are contiguous.  The list
+        // is rewritten inside this kernel at every rebuild, so it is read with
+        // L2-only loads (never the read-only cache); the next word is fetched while
+        // the current one is processed.  One list with the minimum image on every
+        // entry keeps the lanes of a warp in step (splitting off pairs that need
+        // no image made lanes near a face run a second loop the others idle in).
+        const uint4* p = reinterpret_cast<const uint4*>(nl) + i;
+        const int cn = __float_as_int(cw);
+        const int nw = (cn + 7) >> 3;  // words, the last one partial
+        uint4 q = nw > 0 ? __ldcg(p) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 1
+        for (int kb = 0; kb < nw; ++kb) {
+          const uint4 cur = q;
+          if (kb + 1 < nw) q = __ldcg(p + (size_t)(kb + 1) * npad);
+          const int left = cn - (kb << 3);
+          if (left >= 8) {
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.x & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.x >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.y & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.y >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.z & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.z >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.w & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.w >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
+          } else {
+            // last word: entries beyond the count are stale, the atom itself
+            // stands in for them and is masked out
+#pragma unroll
+            for (int u = 0; u < 7; ++u) {
+              const unsigned wd = u < 2 ? cur.x : (u < 4 ? cur.y : (u < 6 ? cur.z : cur.w));
+              const int jj = (int)((wd >> (16 * (u & 1))) & 0xffffu);
+              const bool ok = u < left;
+              nl_pair_bd<EN, VIR>(xs_a, ok ? jj : i, ok, xi, L, invL, c, fx, fy, fz, e, w, np);
+            }
+          }
         }
       } else if (PATH == PATH_ALLPAIRS) {
-        for (int j = 0; j < b.n; ++j) {
-          const float4 xj = xs[j];
-          float dx = min_img(xi.x - xj.x, b.L, b.invL);
-          float dy = min_img(xi.y - xj.y, b.L, b.invL);
-          float dz = min_img(xi.z - xj.z, b.L, b.invL);
-          lj_pair<EN, VIR>(dx, dy, dz, j != i, rp, fx, fy, fz, e, w, np);
+        for (int j = 0; j < n; ++j) {
+          const float4 xj = ld_shared4(xs_a + 16u * (uint32_t)j);
+          const float dx = min_img(xi.x - xj.x, L, invL);
+          const float dy = min_img(xi.y - xj.y, L, invL);
+          const float dz = min_img(xi.z - xj.z, L, invL);
+          lj_pair<EN, VIR>(dx, dy, dz, j != i, c, fx, fy, fz, e, w, np);
         }
       } else {  // PATH_ALLPAIRS_MI: rc <= L < 2 rc, the two nearest images per axis
-        for (int j = 0; j < b.n; ++j) {
-          const float4 xj = xs[j];
-          float d0x = min_img(xi.x - xj.x, b.L, b.invL);
-          float d0y = min_img(xi.y - xj.y, b.L, b.invL);
-          float d0z = min_img(xi.z - xj.z, b.L, b.invL);
-          float d1x = d0x - copysignf(b.L, d0x);
-          float d1y = d0y - copysignf(b.L, d0y);
-          float d1z = d0z - copysignf(b.L, d0z);
+        for (int j = 0; j < n; ++j) {
+          const float4 xj = ld_shared4(xs_a + 16u * (uint32_t)j);
+          const float d0x = min_img(xi.x - xj.x, L, invL);
+          const float d0y = min_img(xi.y - xj.y, L, invL);
+          const float d0z = min_img(xi.z - xj.z, L, invL);
+          const float d1x = d0x - copysignf(L, d0x);
+          const float d1y = d0y - copysignf(L, d0y);
+          const float d1z = d0z - copysignf(L, d0z);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            float dx = (c & 1) ? d1x : d0x;
-            float dy = (c & 2) ? d1y : d0y;
-            float dz = (c & 4) ? d1z : d0z;
-            bool ok = (j != i) || (c != 0);
-            lj_pair<EN, VIR>(dx, dy, dz, ok, rp, fx, fy, fz, e, w, np);
+          for (int k = 0; k < 8; ++k) {
+            const float dx = (k & 1) ? d1x : d0x;
+            const float dy = (k & 2) ? d1y : d0y;
+            const float dz = (k & 4) ? d1z : d0z;
+            lj_pair<EN, VIR>(dx, dy, dz, (j != i) || (k != 0), c, fx, fy, fz, e, w, np);
           }
         }
       }
-      g.f()[i] = make_float4(fx, fy, fz, 0.f);
-      if (EN) e_acc += e;
-      if (VIR) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) w_acc[k] += w[k];
-      }
-      if (CNT) pair_acc += np;
+      fs[i] = make_float4(fx, fy, fz, cw);
     }
   }
+  FSums out = {EN ? e : 0.f, w[0], w[1], w[2], w[3], w[4], w[5], CNT ? np : 0};
+  return out;
+}
+
+template <int APT, int PATH, bool EN, bool VIR, bool CNT>
+__device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, const RunParams& rp,
+                                               float& e_acc, float (&w_acc)[6], int& pair_acc) {
+  const uint32_t xs_a = (uint32_t)__cvta_generic_to_shared(g.x());
+  const FSums r = force_pass<APT, PATH, EN, VIR, CNT>(xs_a, g.f(), g.nl, g.tid, g.nt, g.npad, b.n,
+                                                      b.maxnb, b.L, b.invL, make_lj(rp));
+  if (EN) e_acc += r.e;
+  if (VIR) {
+    w_acc[0] += r.w0;
+    w_acc[1] += r.w1;
+    w_acc[2] += r.w2;
+    w_acc[3] += r.w3;
+    w_acc[4] += r.w4;
+    w_acc[5] += r.w5;
+  }
+  if (CNT) pair_acc += r.np;
 }
 
 // ---------------------------------------------------------------------------
-// Verlet list build from positions wrapped into [0, L).  With >= 3 cells of
-// side >= rc + skin per axis a shared-memory cell list (counting sort; each
-// cell ordered by atom index, so the list order is deterministic) feeds the
-// search; smaller boxes scan every atom.  Thread t writes only the rows of
-// the atoms it owns, which only it reads back.
+// Verlet list build from positions wrapped into [0, L).
+//
+// Cell path (>= 3 cells of side >= rc + skin per axis): a shared-memory counting
+// sort re-orders the box into cell order -- positions (original atom id carried
+// in x.w) and velocities are permuted in place, and ownership follows the slot --
+// so the 32 lanes of a warp hold neighbouring atoms and scan the same cells, and
+// later force-loop gathers touch nearby shared-memory words.  Inside a cell atoms
+// keep their previous relative order (sorted by previous slot), so the order, the
+// list and every result are deterministic.  The per-cell image shift replaces a
+// per-candidate minimum image in the search.
+// Small boxes (fewer than 3 cells per axis) scan every atom without re-ordering.
+// The list length of slot s is kept in f[s].w (as int bits).
 __device__ __forceinline__ void nl_store(uint16_t* row, int k, int npad, int j) {
-  row[(size_t)(k >> 2) * npad * 4 + (k & 3)] = (uint16_t)j;
+  row[(size_t)(k >> 3) * npad * 8 + (k & 7)] = (uint16_t)j;
+}
+
+__device__ __forceinline__ int cell_of(const float4& x, float cinv, int nc) {
+  const int cx = min((int)(x.x * cinv), nc - 1);
+  const int cy = min((int)(x.y * cinv), nc - 1);
+  const int cz = min((int)(x.z * cinv), nc - 1);
+  return (cz * nc + cy) * nc + cx;
 }
 
 template <int APT>
-__device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
+__device__ void build_nlist(const Group& g, const BoxCtx& b, long long* prof = nullptr) {
   const int n = b.n;
+  long long tp = prof ? clock64() : 0;
+#define MDEOS_PHASE(k)                          \
+  if (prof && g.tid == 0) {                     \
+    const long long tn = clock64();             \
+    prof[k] += tn - tp;                         \
+    tp = tn;                                    \
+  }
   float4* xs = g.x();
-  float4* srt = g.f();  // cell-sorted copy (the forces are dead during a rebuild)
+  float4* vs = g.v();
+  float4* srt = g.f();  // sorted copy of the positions (forces are dead during a rebuild)
   if (b.nc >= 3) {
     const int nc = b.nc, ncell = nc * nc * nc;
-    int* ccount = g.cell();            // counts, then insertion cursors
+    int* ccount = g.cell();              // counts, then insertion cursors
     int* cstart = g.cell() + ncell + 1;  // [ncell + 1]
     for (int c = g.tid; c < ncell; c += g.nt) ccount[c] = 0;
     gbar(g.bar, g.nt);
@@ -319,29 +408,25 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
       const int i = g.tid + a * g.nt;
       mycell[a] = 0;
       if (i < n) {
-        const float4 xi = xs[i];
-        const int cx = min((int)(xi.x * b.cinv), nc - 1);
-        const int cy = min((int)(xi.y * b.cinv), nc - 1);
-        const int cz = min((int)(xi.z * b.cinv), nc - 1);
-        const int c = (cz * nc + cy) * nc + cx;
-        mycell[a] = c;
-        atomicAdd(&ccount[c], 1);
+        mycell[a] = cell_of(xs[i], b.cinv, nc);
+        atomicAdd(&ccount[mycell[a]], 1);
       }
     }
     gbar(g.bar, g.nt);
+    MDEOS_PHASE(0)
     if (g.warp() == 0) {
       const int lane = g.lane();
       const int per = (ncell + 31) / 32;
       const int lo = lane * per, hi = min(lo + per, ncell);
-      int s = 0;
-      for (int c = lo; c < hi; ++c) s += ccount[c];
-      int incl = s;
+      int sum = 0;
+      for (int c = lo; c < hi; ++c) sum += ccount[c];
+      int incl = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
       }
-      int run = incl - s;
+      int run = incl - sum;
       for (int c = lo; c < hi; ++c) {
         const int k = ccount[c];
         cstart[c] = run;
@@ -351,22 +436,26 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
       if (lane == 31) cstart[ncell] = incl;
     }
     gbar(g.bar, g.nt);
+    MDEOS_PHASE(1)
+    // scatter (position, previous slot << 16 | atom id) into the sorted copy
 #pragma unroll
     for (int a = 0; a < APT; ++a) {
       const int i = g.tid + a * g.nt;
       if (i < n) {
         const int slot = atomicAdd(&ccount[mycell[a]], 1);
         const float4 xi = xs[i];
-        srt[slot] = make_float4(xi.x, xi.y, xi.z, __int_as_float(i));
+        srt[slot] = make_float4(xi.x, xi.y, xi.z,
+                                __int_as_float((i << 16) | (__float_as_int(xi.w) & 0xffff)));
       }
     }
     gbar(g.bar, g.nt);
-    for (int c = g.tid; c < ncell; c += g.nt) {  // order each cell by atom index
+    MDEOS_PHASE(2)
+    for (int c = g.tid; c < ncell; c += g.nt) {  // restore the previous order inside each cell
       const int s0 = cstart[c], s1 = cstart[c + 1];
-      for (int s = s0 + 1; s < s1; ++s) {
-        const float4 key = srt[s];
+      for (int q = s0 + 1; q < s1; ++q) {
+        const float4 key = srt[q];
         const int kk = __float_as_int(key.w);
-        int t = s - 1;
+        int t = q - 1;
         while (t >= s0 && __float_as_int(srt[t].w) > kk) {
           srt[t + 1] = srt[t];
           --t;
@@ -375,32 +464,60 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
       }
     }
     gbar(g.bar, g.nt);
+    MDEOS_PHASE(3)
+    // permute velocities in place: read every old slot first, then write the new ones
+    float4 vnew[APT];
 #pragma unroll
     for (int a = 0; a < APT; ++a) {
-      const int i = g.tid + a * g.nt;
-      if (i < n) {
-        const float4 xi = xs[i];
-        const int c = mycell[a];
+      const int sl = g.tid + a * g.nt;
+      if (sl < n) vnew[a] = vs[__float_as_int(srt[sl].w) >> 16];
+    }
+    gbar(g.bar, g.nt);
+#pragma unroll
+    for (int a = 0; a < APT; ++a) {
+      const int sl = g.tid + a * g.nt;
+      if (sl < n) {
+        const float4 q = srt[sl];
+        vs[sl] = make_float4(vnew[a].x, vnew[a].y, vnew[a].z, 0.f);
+        xs[sl] = make_float4(q.x, q.y, q.z, __int_as_float(__float_as_int(q.w) & 0xffff));
+      }
+    }
+    gbar(g.bar, g.nt);
+    MDEOS_PHASE(4)
+    // Search: each slot scans the 27 neighbour cells of its home cell; the image
+    // shift of a wrapped neighbour cell is applied to the home atom once per cell.
+    const float rcs2 = b.rcs2;
+#pragma unroll
+    for (int a = 0; a < APT; ++a) {
+      const int sl = g.tid + a * g.nt;
+      if (sl < n) {
+        const float4 xi = xs[sl];
+        const int c = cell_of(xi, b.cinv, nc);
         const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-        uint16_t* row = g.nl + (size_t)i * 4;
+        uint16_t* row = g.nl + (size_t)sl * 8;
         int k = 0;
         for (int dz = -1; dz <= 1; ++dz) {
-          const int qz = (cz + dz + nc) % nc;
+          int qz = cz + dz;
+          const float shz = qz < 0 ? -b.L : (qz >= nc ? b.L : 0.f);
+          qz = qz < 0 ? qz + nc : (qz >= nc ? qz - nc : qz);
           for (int dy = -1; dy <= 1; ++dy) {
-            const int qy = (cy + dy + nc) % nc;
+            int qy = cy + dy;
+            const float shy = qy < 0 ? -b.L : (qy >= nc ? b.L : 0.f);
+            qy = qy < 0 ? qy + nc : (qy >= nc ? qy - nc : qy);
             for (int dx = -1; dx <= 1; ++dx) {
-              const int qx = (cx + dx + nc) % nc;
+              int qx = cx + dx;
+              const float shx = qx < 0 ? -b.L : (qx >= nc ? b.L : 0.f);
+              qx = qx < 0 ? qx + nc : (qx >= nc ? qx - nc : qx);
+              // neighbour image sits at x_j + shift: d = (x_i - shift) - x_j
+              const float ax = xi.x - shx, ay = xi.y - shy, az = xi.z - shz;
               const int q = (qz * nc + qy) * nc + qx;
-              const int s1 = cstart[q + 1];
-              for (int s = cstart[q]; s < s1; ++s) {
-                const float4 xo = srt[s];
-                const int j = __float_as_int(xo.w);
-                const float ddx = min_img(xi.x - xo.x, b.L, b.invL);
-                const float ddy = min_img(xi.y - xo.y, b.L, b.invL);
-                const float ddz = min_img(xi.z - xo.z, b.L, b.invL);
+              const int t1 = cstart[q + 1];
+              for (int t = cstart[q]; t < t1; ++t) {
+                const float4 xo = xs[t];
+                const float ddx = ax - xo.x, ddy = ay - xo.y, ddz = az - xo.z;
                 const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                if (j != i && r2 < b.rcs2) {
-                  if (k < b.maxnb) nl_store(row, k, g.npad, j);
+                if (t != sl && r2 < rcs2) {
+                  if (k < b.maxnb) nl_store(row, k, g.npad, t);
                   ++k;
                 }
               }
@@ -411,10 +528,11 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
           atomicOr(&g.ctrl()[CTRL_OVERFLOW], 1);
           k = b.maxnb;
         }
-        cnt[a] = k;
+        srt[sl] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
       }
     }
-    gbar(g.bar, g.nt);  // the sorted copy aliases the force array
+    gbar(g.bar, g.nt);
+    MDEOS_PHASE(5)
   } else {
     gbar(g.bar, g.nt);  // positions just wrapped by their owners
 #pragma unroll
@@ -422,7 +540,7 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
       const int i = g.tid + a * g.nt;
       if (i < n) {
         const float4 xi = xs[i];
-        uint16_t* row = g.nl + (size_t)i * 4;
+        uint16_t* row = g.nl + (size_t)i * 8;
         int k = 0;
         for (int j = 0; j < n; ++j) {
           const float4 xo = xs[j];
@@ -439,21 +557,23 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, int (&cnt)[APT]) {
           atomicOr(&g.ctrl()[CTRL_OVERFLOW], 1);
           k = b.maxnb;
         }
-        cnt[a] = k;
+        srt[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
       }
     }
     gbar(g.bar, g.nt);
+    MDEOS_PHASE(5)
   }
+#undef MDEOS_PHASE
 }
 
-// wrap own positions into [0, L) and reset their displacement bounds
+// wrap own positions into [0, L) and reset their displacement bounds (v.w)
 template <int APT>
-__device__ __forceinline__ void wrap_own(const Group& g, const BoxCtx& b, float (&disp)[APT]) {
+__device__ __forceinline__ void wrap_own(const Group& g, const BoxCtx& b) {
 #pragma unroll
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
-    disp[a] = 0.f;
     if (i < b.n) {
+      g.v()[i].w = 0.f;
       float4 xi = g.x()[i];
       xi.x -= b.L * floorf(xi.x * b.invL);
       xi.y -= b.L * floorf(xi.y * b.invL);
@@ -482,7 +602,7 @@ __device__ void lattice_own(const Group& g, const BoxDesc& bd) {
       const double by = (bb == 1 || bb == 3) ? 0.5 : 0.0;
       const double bz = (bb == 2 || bb == 3) ? 0.5 : 0.0;
       g.x()[i] = make_float4((float)(a * (cx + bx)), (float)(a * (cy + by)), (float)(a * (cz + bz)),
-                             0.f);
+                             __int_as_float(i));  // original atom id travels with the atom
     }
   }
 }
@@ -503,7 +623,8 @@ __device__ void init_velocities(const Group& g, const BoxCtx& b, unsigned long l
     const int i = g.tid + a * g.nt;
     v[a] = make_float3(0.f, 0.f, 0.f);
     if (i < b.n) {
-      uint32_t c[4] = {(uint32_t)i, 0u, 0u, 0u};
+      const uint32_t id = (uint32_t)__float_as_int(g.x()[i].w);
+      uint32_t c[4] = {id, 0u, 0u, 0u};
       philox4x32_10(c, k0, k1);
       // uniforms in the open interval (0, 1); Box-Muller in FP64 (once per atom)
       const double u0 = ((double)c[0] + 0.5) * two_m32, u1 = ((double)c[1] + 0.5) * two_m32;
@@ -546,21 +667,20 @@ __device__ void init_velocities(const Group& g, const BoxCtx& b, unsigned long l
 // the three force variants the step loop uses
 template <int APT, int PATH>
 __device__ __forceinline__ void forces_step(const Group& g, const BoxCtx& b, const RunParams& rp,
-                                            const int (&cnt)[APT], bool en, bool vir, float& e,
-                                            float (&w)[6], int& np) {
+                                            bool en, bool vir, float& e, float (&w)[6], int& np) {
   if (vir)
-    compute_forces<APT, PATH, true, true, true>(g, b, rp, cnt, e, w, np);
+    compute_forces<APT, PATH, true, true, true>(g, b, rp, e, w, np);
   else if (en)
-    compute_forces<APT, PATH, true, false, false>(g, b, rp, cnt, e, w, np);
+    compute_forces<APT, PATH, true, false, false>(g, b, rp, e, w, np);
   else
-    compute_forces<APT, PATH, false, false, false>(g, b, rp, cnt, e, w, np);
+    compute_forces<APT, PATH, false, false, false>(g, b, rp, e, w, np);
 }
 
 // first half kick with the pending thermostat factor, then drift; returns
 // whether any own atom's displacement bound passed half the skin
 template <int APT>
 __device__ __forceinline__ bool kick_drift(const Group& g, const BoxCtx& b, const RunParams& rp,
-                                           float lam, float (&disp)[APT]) {
+                                           float lam) {
   bool need = false;
 #pragma unroll
   for (int a = 0; a < APT; ++a) {
@@ -571,14 +691,15 @@ __device__ __forceinline__ bool kick_drift(const Group& g, const BoxCtx& b, cons
       vi.x = fmaf(lam, vi.x, rp.hdtm * fi.x);
       vi.y = fmaf(lam, vi.y, rp.hdtm * fi.y);
       vi.z = fmaf(lam, vi.z, rp.hdtm * fi.z);
+      // v.w: bound on the displacement since the last list build
+      vi.w = fmaf(rp.dt, sqrtf(vi.x * vi.x + vi.y * vi.y + vi.z * vi.z), vi.w);
       g.v()[i] = vi;
       float4 xi = g.x()[i];
       xi.x = fmaf(rp.dt, vi.x, xi.x);
       xi.y = fmaf(rp.dt, vi.y, xi.y);
       xi.z = fmaf(rp.dt, vi.z, xi.z);
       g.x()[i] = xi;
-      disp[a] += rp.dt * sqrtf(vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
-      need = need || (disp[a] > b.half_skin);
+      need = need || (vi.w > b.half_skin);
     }
   }
   return need;
@@ -595,13 +716,6 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   const double ndof = 3.0 * n - 3.0;
   const double V = bd.L * bd.L * bd.L;
   const bool temp_mode = (bd.flags & MDEOS_REQ_TEMPERATURE) != 0;
-  float disp[APT];
-  int cnt[APT];
-#pragma unroll
-  for (int a = 0; a < APT; ++a) {
-    disp[a] = 0.f;
-    cnt[a] = 0;
-  }
   double* acc = g.acc();
   if (g.tid < 16) g.ctrl()[g.tid] = 0;
   for (int k = g.tid; k < kAccDoubles; k += g.nt) acc[k] = 0.0;
@@ -609,8 +723,12 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   lattice_own<APT>(g, bd);
   gbar(g.bar, g.nt);
   int builds = 0;
+  for (int a = 0; a < APT; ++a) {  // zero velocities (displacement bounds) before any build
+    const int i = g.tid + a * g.nt;
+    if (i < n) g.v()[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   if (PATH == PATH_NLIST) {
-    build_nlist<APT>(g, b, cnt);
+    build_nlist<APT>(g, b);
     ++builds;
   }
   // E_cold: potential energy of the lifted lattice at rest (Sec. III)
@@ -618,7 +736,7 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   {
     float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int np0 = 0;
-    forces_step<APT, PATH>(g, b, rp, cnt, true, false, e0, w0, np0);
+    forces_step<APT, PATH>(g, b, rp, true, false, e0, w0, np0);
     float q[1] = {e0};
     double et[1];
     group_sum<1>(g, q, et);
@@ -657,11 +775,11 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
     const int s_avg = step - bd.steps_equil;
     const bool seg_end = !avg && (seg_pos == seg_len - 1);
     const bool esamp = !avg && !temp_mode && (seg_pos >= seg_len - nsamp);
-    const bool need = kick_drift<APT>(g, b, rp, lam, disp);
+    const bool need = kick_drift<APT>(g, b, rp, lam);
     if (PATH == PATH_NLIST) {
       if (gbar_or(g.bar, g.nt, need)) {
-        wrap_own<APT>(g, b, disp);
-        build_nlist<APT>(g, b, cnt);
+        wrap_own<APT>(g, b);
+        build_nlist<APT>(g, b);
         ++builds;
       }
     } else {
@@ -677,7 +795,7 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
     // forces at the new positions
     float e_th = 0.f, w_th[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int np_th = 0;
-    forces_step<APT, PATH>(g, b, rp, cnt, avg || esamp, avg, e_th, w_th, np_th);
+    forces_step<APT, PATH>(g, b, rp, avg || esamp, avg, e_th, w_th, np_th);
     // second half kick, kinetic energy and kinetic stress
     float ke = 0.f, kt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -720,7 +838,11 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
 #pragma unroll
         for (int a = 0; a < APT; ++a) {
           const int i = g.tid + a * g.nt;
-          if (i < n) cand += (PATH == PATH_NLIST) ? cnt[a] : (PATH == PATH_ALLPAIRS ? n : 8 * n);
+          if (i < n) {
+            const int cw = __float_as_int(g.f()[i].w);
+            cand += (PATH == PATH_NLIST) ? cw
+                                         : (PATH == PATH_ALLPAIRS ? n : 8 * n);
+          }
         }
         const float sp = warp_sum((float)np_th), sc = warp_sum((float)cand);
         if (g.lane() == 0) {
