@@ -34,6 +34,7 @@ class Params(ctypes.Structure):
         ("lift_iters", ctypes.c_int), ("rescale_every_equil", ctypes.c_int),
         ("rescale_every_avg", ctypes.c_int), ("se_blocks", ctypes.c_int),
         ("energy_ref_mode", ctypes.c_int), ("force_mode", ctypes.c_int),
+        ("warm_lift_iters", ctypes.c_int),
     ]
 
 
@@ -95,6 +96,11 @@ def lib():
         _lib.orc_eos_batch.argtypes = [p, i, ctypes.POINTER(Params), p, i]
         _lib.orc_eos_batch.restype = i
         _lib.orc_max_threads.restype = i
+        _lib.orc_eos_eval_state.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(Params),
+                                            p, p, d, p, p, ctypes.POINTER(Result)]
+        _lib.orc_eos_eval_state.restype = i
+        _lib.orc_eos_batch_state.argtypes = [p, i, ctypes.POINTER(Params), p, p, p, p, p, p, i]
+        _lib.orc_eos_batch_state.restype = i
     return _lib
 
 
@@ -104,9 +110,10 @@ def _ptr(a: np.ndarray):
 
 def make_params(eps=1.0, sigma=1.0, mass=1.0, rc=2.5, dt=0.005, lift_iters=2,
                 rescale_every_equil=0, rescale_every_avg=10, se_blocks=10,
-                energy_ref_mode=REF_ECOLD, force_mode=FORCE_ALLPAIRS) -> Params:
+                energy_ref_mode=REF_ECOLD, force_mode=FORCE_ALLPAIRS,
+                warm_lift_iters=1) -> Params:
     return Params(eps, sigma, mass, rc, dt, lift_iters, rescale_every_equil,
-                  rescale_every_avg, se_blocks, energy_ref_mode, force_mode)
+                  rescale_every_avg, se_blocks, energy_ref_mode, force_mode, warm_lift_iters)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -200,6 +207,66 @@ def eos_batch(reqs: list[dict], params: Params | None = None, nthreads: int = 0)
     lib().orc_eos_batch(ctypes.cast(arr, ctypes.c_void_p), n, ctypes.byref(params),
                         ctypes.cast(out, ctypes.c_void_p), nthreads)
     return [_result_dict(out[k]) for k in range(n)]
+
+
+def _req_array(reqs):
+    arr = (Request * len(reqs))()
+    for k, r in enumerate(reqs):
+        arr[k] = Request(r["rho"], r["e"], r.get("e_ref", 0.0), r["natoms"], r["steps_equil"],
+                         r["steps_avg"], r.get("flags", 0), r.get("seed", 0))
+    return arr
+
+
+def eos_eval_state(req: dict, params: Params | None = None, x_in=None, v_in=None, L_in=0.0):
+    """One evaluation with an optional warm start from (x_in, v_in, L_in).
+
+    Returns (result dict, x_out (n,3), v_out (n,3)); x_out/v_out is the final
+    state (None if the evaluation failed)."""
+    params = params or make_params()
+    n = req["natoms"]
+    rq = _req_array([req])
+    out = Result()
+    xo = np.zeros((n, 3))
+    vo = np.zeros((n, 3))
+    if x_in is not None:
+        xi = np.ascontiguousarray(x_in, dtype=np.float64).reshape(n, 3)
+        vi = np.ascontiguousarray(v_in, dtype=np.float64).reshape(n, 3)
+        px, pv = _ptr(xi), _ptr(vi)
+    else:
+        px = pv = None
+        L_in = 0.0
+    lib().orc_eos_eval_state(rq, ctypes.byref(params), px, pv, float(L_in), _ptr(xo), _ptr(vo),
+                             ctypes.byref(out))
+    d = _result_dict(out)
+    if d["status"] != OK:
+        return d, None, None
+    return d, xo, vo
+
+
+def eos_batch_state(reqs: list[dict], params: Params | None = None, x_in=None, v_in=None,
+                    L_in=None, nthreads: int = 0):
+    """Batch of equal-size requests with per-request warm starts.
+
+    x_in, v_in: (nreq, natoms, 3) or None; L_in: (nreq,) with <= 0 meaning cold.
+    Returns (list of result dicts, x_out, v_out) with the final states."""
+    params = params or make_params()
+    nr = len(reqs)
+    n = reqs[0]["natoms"]
+    assert all(r["natoms"] == n for r in reqs)
+    rq = _req_array(reqs)
+    out = (Result * nr)()
+    xo = np.zeros((nr, n, 3))
+    vo = np.zeros((nr, n, 3))
+    if x_in is not None:
+        xi = np.ascontiguousarray(x_in, dtype=np.float64).reshape(nr, n, 3)
+        vi = np.ascontiguousarray(v_in, dtype=np.float64).reshape(nr, n, 3)
+        li = np.ascontiguousarray(L_in, dtype=np.float64).reshape(nr)
+        px, pv, pl = _ptr(xi), _ptr(vi), _ptr(li)
+    else:
+        px = pv = pl = None
+    lib().orc_eos_batch_state(ctypes.cast(rq, ctypes.c_void_p), nr, ctypes.byref(params), px, pv,
+                              pl, _ptr(xo), _ptr(vo), ctypes.cast(out, ctypes.c_void_p), nthreads)
+    return [_result_dict(out[k]) for k in range(nr)], xo, vo
 
 
 def max_threads() -> int:

@@ -307,12 +307,22 @@ int orc_md_steps(int n, double* x, double* v, double* f, double L, const orc_par
 /* ------------------------------------------------------------------ */
 static int is_fin(double a) { return isfinite(a) ? 1 : 0; }
 
-int orc_eos_eval(const orc_request* rq, const orc_params* p, orc_result* out) {
+/* Lifting -> MD -> restriction.  Cold start (x_in == NULL): the FCC lattice of
+ * Eq. 6-7 with Maxwell velocities at the Eq. 9 temperature and lift_iters
+ * Eq. 10 segments.  Warm start (x_in != NULL, the previous final state of the
+ * same element, box side L_in): positions scaled affinely by L / L_in, the
+ * velocities kept, their mean removed and rescaled to the Eq. 10 temperature
+ * of the scaled configuration, then warm_lift_iters Eq. 10 segments.  The
+ * final state (positions in [0, L)) is written to x_out / v_out if given. */
+static int eos_core(const orc_request* rq, const orc_params* p, const double* x_in,
+                    const double* v_in, double L_in, double* x_out, double* v_out,
+                    orc_result* out) {
   memset(out, 0, sizeof(*out));
   int n = rq->natoms;
-  int nseg = p->lift_iters;
+  const int warm = x_in != NULL && v_in != NULL && L_in > 0.0;
+  int nseg = warm ? p->warm_lift_iters : p->lift_iters;
   if (n < 2 || !(rq->rho > 0.0) || rq->steps_avg < 1 || p->se_blocks < 2 ||
-      p->se_blocks > rq->steps_avg || p->lift_iters < 0 || rq->steps_equil < 0 ||
+      p->se_blocks > rq->steps_avg || nseg < 0 || rq->steps_equil < 0 ||
       (rq->steps_equil > 0 && rq->steps_equil < nseg) ||
       (rq->steps_equil > 0 && nseg == 0)) {
     out->status = ORC_EINVAL;
@@ -343,8 +353,32 @@ int orc_eos_eval(const orc_request* rq, const orc_params* p, orc_result* out) {
   /* Eq. 9 (or the given T) */
   double Tk = temp_mode ? rq->e : 2.0 * (E_tgt - E_cold) / ndof;
   int status = ORC_OK;
-  if (!(Tk > 0.0) || !is_fin(Tk)) status = ORC_EUNPHYS;
-  if (status == ORC_OK) orc_init_velocities(n, rq->seed, Tk, p->mass, v);
+  if (!warm && (!(Tk > 0.0) || !is_fin(Tk))) status = ORC_EUNPHYS;
+  if (warm) {
+    /* warm start: affine scaling of the previous state, Eq. 10 temperature
+     * of the scaled configuration */
+    const double s = L / L_in;
+    double vm[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) {
+        double xi = x_in[3 * i + a] * s;
+        xi -= L * floor(xi / L);
+        if (xi >= L) xi -= L;
+        x[3 * i + a] = xi;
+        v[3 * i + a] = v_in[3 * i + a];
+        vm[a] += v_in[3 * i + a];
+      }
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) v[3 * i + a] -= vm[a] / n;
+    double E0 = orc_lj_forces(n, x, L, p, p->force_mode, f, W);
+    Tk = temp_mode ? rq->e : 2.0 * (E_tgt - E0) / ndof; /* Eq. 10 */
+    if (!(Tk > 0.0) || !is_fin(Tk) || !is_fin(E0))
+      status = ORC_EUNPHYS;
+    else
+      rescale_to(n, v, p->mass, Tk);
+  } else if (status == ORC_OK) {
+    orc_init_velocities(n, rq->seed, Tk, p->mass, v);
+  }
 
   /* Equilibration: lift_iters NVE segments; after each, E_pot is sampled and
    * the temperature updated with Eq. 10, then velocities are rescaled to it.
@@ -421,8 +455,39 @@ int orc_eos_eval(const orc_request* rq, const orc_params* p, orc_result* out) {
     free(bP); free(bT); free(bn);
   }
   out->status = status;
+  if (status == ORC_OK && x_out && v_out) {
+    memcpy(x_out, x, sizeof(double) * 3 * n);
+    memcpy(v_out, v, sizeof(double) * 3 * n);
+  }
   free(x); free(v); free(f);
   return status;
+}
+
+int orc_eos_eval(const orc_request* rq, const orc_params* p, orc_result* out) {
+  return eos_core(rq, p, NULL, NULL, 0.0, NULL, NULL, out);
+}
+
+int orc_eos_eval_state(const orc_request* rq, const orc_params* p, const double* x_in,
+                       const double* v_in, double L_in, double* x_out, double* v_out,
+                       orc_result* out) {
+  return eos_core(rq, p, x_in, v_in, L_in, x_out, v_out, out);
+}
+
+int orc_eos_batch_state(const orc_request* rq, int n, const orc_params* p, const double* x_in,
+                        const double* v_in, const double* L_in, double* x_out, double* v_out,
+                        orc_result* out, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int i = 0; i < n; ++i) {
+    const long long o = 3LL * rq[0].natoms * i;
+    const int w = L_in != NULL && L_in[i] > 0.0;
+    eos_core(&rq[i], p, w ? x_in + o : NULL, w ? v_in + o : NULL, w ? L_in[i] : 0.0,
+             x_out ? x_out + o : NULL, v_out ? v_out + o : NULL, &out[i]);
+  }
+  (void)nthreads;
+  return ORC_OK;
 }
 
 int orc_max_threads(void) {

@@ -38,6 +38,7 @@ typedef struct {
   int se_blocks;           /* block count for the standard error */
   int energy_ref_mode;     /* ORC_REF_ECOLD (paper) or ORC_REF_FIXED */
   int force_mode;          /* ORC_FORCE_ALLPAIRS or ORC_FORCE_CELL */
+  int warm_lift_iters;     /* Eq. 10 segments after a warm start */
 } orc_params;
 
 typedef struct {
@@ -90,6 +91,21 @@ double orc_kinetic(int n, const double* v, double mass);
 
 /* Full lifting -> MD -> restriction for one request (Sec. III, Eq. 6-11). */
 int orc_eos_eval(const orc_request* rq, const orc_params* p, orc_result* out);
+
+/* Same with a warm start from a previous state (x_in, v_in: 3n doubles each,
+ * box side L_in; NULL = cold) and the final state written to x_out, v_out
+ * (NULL = not kept).  Warm reading: positions scaled by L / L_in, velocities
+ * kept with their mean removed, one Eq. 10 temperature from the scaled
+ * configuration, then warm_lift_iters Eq. 10 segments before averaging. */
+int orc_eos_eval_state(const orc_request* rq, const orc_params* p, const double* x_in,
+                       const double* v_in, double L_in, double* x_out, double* v_out,
+                       orc_result* out);
+
+/* Batch form of orc_eos_eval_state; every request has rq[0].natoms atoms,
+ * state arrays hold 3 * natoms doubles per request; L_in[i] <= 0 = cold. */
+int orc_eos_batch_state(const orc_request* rq, int n, const orc_params* p, const double* x_in,
+                        const double* v_in, const double* L_in, double* x_out, double* v_out,
+                        orc_result* out, int nthreads);
 
 /* Same for a batch, OpenMP over requests (nthreads <= 0: all cores). */
 int orc_eos_batch(const orc_request* rq, int n, const orc_params* p, orc_result* out,
