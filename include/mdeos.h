@@ -54,7 +54,9 @@ enum {
 
 /* mdeos_request.flags */
 enum {
-  MDEOS_REQ_TEMPERATURE = 1u /* request.e holds a temperature; lifting holds it fixed */
+  MDEOS_REQ_TEMPERATURE = 1u, /* request.e holds a temperature; lifting holds it fixed */
+  MDEOS_REQ_COLD = 2u         /* lift from the lattice even if the element has a stored
+                                 state (the final state is still stored) */
 };
 
 /* Library configuration.  Fill with mdeos_config_default, then override. */
@@ -71,6 +73,17 @@ typedef struct {
   double skin;                 /* Verlet-list skin; <= 0 lets the autotuner choose */
   size_t hbm_budget_bytes;     /* cap on library device memory; 0 = no cap */
   void* cuda_stream;           /* cudaStream_t to run on; NULL = library-owned stream */
+  /* Warm start (element_id != 0, mdeos_submit only): the handle keeps each
+   * element's final MD state and lifts its next request from it -- positions
+   * scaled affinely to the new box side, velocities kept (mean removed) and
+   * rescaled to the Eq. 10 temperature of the scaled configuration, then
+   * warm_lift_iters Eq. 10 segments instead of lift_iters.  The store holds
+   * warm_slots elements of up to warm_atoms atoms (32 B per atom of device
+   * memory, allocated by mdeos_create, counted in hbm_budget_bytes); 0 = off. */
+  int32_t warm_lift_iters;     /* Eq. 10 segments after a warm start; default 1 */
+  int32_t warm_slots;          /* elements kept; 0 = no warm store */
+  int32_t warm_atoms;          /* atoms per stored element (>= natoms of its requests) */
+  int32_t reserved0;
 } mdeos_config;
 
 /* One EOS query.  Layout is part of the ABI. */
@@ -104,6 +117,8 @@ typedef struct {
   int32_t status;      /* mdeos_status of this box */
   int32_t nlist_builds;/* neighbour-list rebuilds (diagnostic) */
   int32_t path;        /* force path used: 0 all-pairs, 1 all-pairs multi-image, 2 Verlet list */
+  int32_t warm;        /* 1 if lifted from the element's stored state, else 0 */
+  int32_t reserved0;
 } mdeos_result;
 
 typedef struct mdeos_handle mdeos_handle;
@@ -198,6 +213,103 @@ mdeos_status mdeos_stats(const mdeos_handle* h, size_t* last_h2d_bytes, size_t* 
 #define MDEOS_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)
 mdeos_status mdeos_submit_noalloc(const mdeos_config* cfg, const mdeos_request* reqs, int32_t n,
                                   mdeos_result* d_results, void* stream);
+
+/* ---- warm-start store -------------------------------------------------
+ * Slot rules: an element_id first seen takes the next free slot (none free:
+ * evaluated cold, not stored); a slot is rewritten by every successful
+ * evaluation of its element and invalidated by a failed one.  When one
+ * mdeos_submit holds an element_id more than once, its first request uses and
+ * updates the slot and the others run cold without storing.  mdeos_batch_* and
+ * mdeos_submit_noalloc never use the store.  natoms must not exceed warm_atoms
+ * (larger requests run cold, not stored). */
+
+/* Copy the stored state of element_id to host x4/v4 (float4[natoms] each:
+ * positions in [0, L) with w = atom id as float bits, velocities with w = 0)
+ * and its box side to *L.  Waits for the handle's outstanding work.
+ * Errors: MDEOS_EINVAL (no valid stored state of that size). */
+mdeos_status mdeos_warm_export(mdeos_handle* h, uint64_t element_id, int32_t natoms, float* x4,
+                               float* v4, double* L);
+
+/* Store a state for element_id (host float4[natoms] positions in a box of side L
+ * and velocities; w components ignored), so its next request warm-starts from it.
+ * Errors: MDEOS_EINVAL (no store, natoms > warm_atoms, L <= 0), MDEOS_ENOMEM (no
+ * free slot). */
+mdeos_status mdeos_warm_import(mdeos_handle* h, uint64_t element_id, int32_t natoms,
+                               const float* x4, const float* v4, double L);
+
+/* Forget every stored state (slots are reused). */
+mdeos_status mdeos_warm_reset(mdeos_handle* h);
+
+/* ---- 1D Lagrangian hydro caller (Sec. II, Eq. 2-5) ----------------------
+ * Planar Lagrangian hydrodynamics on a staggered grid (node x, u; zone mass,
+ * rho, e) whose closure P(rho, e) is an ideal gas, the Mie-Grueneisen form of
+ * Eq. 1 (linear Us-up Hugoniot as reference curve), or the atomistic EOS of
+ * this library, called once per zone and step as one batch (Sec. III, last
+ * paragraph).  One step, all in FP64 on the device:
+ *   closure P, c^2;  q = rho (q_quad du^2 - q_lin c du) for du = u_{z+1} - u_z < 0;
+ *   dt = cfl min dx / (c + 2 q_quad max(-du, 0)), at most dt_grow * previous dt;
+ *   u += dt F / M with F_i = (P+q)_{i-1} - (P+q)_i (0 outside a free end; u = 0
+ *   at a wall);  x += dt (u_old + u_new) / 2;
+ *   e -= dt (P+q) (uh_{z+1} - uh_z) / m (compatible form: total energy is
+ *   conserved to round-off);  rho = m / (x_{z+1} - x_z).
+ * The MD closure uses c^2 = sound_gamma * max(P / rho, T) (the paper gives no
+ * sound speed for it). */
+enum { MDEOS_CLOSURE_IDEAL_GAS = 0, MDEOS_CLOSURE_MIE_GRUNEISEN = 1, MDEOS_CLOSURE_MD = 2 };
+enum { MDEOS_BC_WALL = 0, MDEOS_BC_FREE = 1 };
+
+typedef struct {
+  int32_t nzones;
+  int32_t closure;             /* MDEOS_CLOSURE_* */
+  int32_t bc_left, bc_right;   /* MDEOS_BC_* */
+  double q_quad, q_lin;        /* artificial viscosity constants; default 2, 0.5 */
+  double cfl, dt_grow;         /* default 0.5, 1.1 */
+  double dt_fixed;             /* > 0: this time step instead of the CFL one */
+  double gamma;                /* ideal gas */
+  double mg_rho0, mg_c, mg_s, mg_gamma; /* Mie-Grueneisen: rho0, C, s, Gamma */
+  /* MD closure: requests of natoms atoms; the first call of each zone uses the
+   * *_first step counts (a cold lift), later calls steps_equil / steps_avg and a
+   * warm start when the handle has a warm store with >= nzones free slots. */
+  int32_t natoms, steps_equil, steps_avg, steps_equil_first, steps_avg_first;
+  int32_t first_temperature;   /* 1: the first call lifts at temperature e0[z] and
+                                  sets e to the achieved energy (MDEOS_REQ_TEMPERATURE) */
+  double e_ref;                /* energy zero per atom (MDEOS_REF_FIXED handles) */
+  double sound_gamma;          /* default 3 */
+  uint64_t seed;               /* zone z, call k: Philox key seed + (k << 32) + z */
+  uint64_t element_base;       /* zone z is element element_base + z + 1 */
+} mdeos_hydro_config;
+
+typedef struct mdeos_hydro mdeos_hydro;
+
+/* Defaults: wall ends, q_quad 2, q_lin 0.5, cfl 0.5, dt_grow 1.1, gamma 5/3,
+ * sound_gamma 3; the rest 0. */
+void mdeos_hydro_config_default(mdeos_hydro_config* cfg);
+
+/* Create a hydro problem on handle h's device and stream (h stays owned by the
+ * caller and must outlive the problem).  x, u: host double[nzones + 1] node
+ * positions (strictly increasing) and velocities; rho, e0: host double[nzones]
+ * zone densities and specific energies (temperatures with first_temperature).
+ * Copied.  Errors: MDEOS_EINVAL, MDEOS_ENOMEM, MDEOS_ECUDA. */
+mdeos_status mdeos_hydro_create(mdeos_handle* h, const mdeos_hydro_config* cfg, const double* x,
+                                const double* u, const double* rho, const double* e0,
+                                mdeos_hydro** out);
+
+/* Advance nsteps steps (synchronous).  Analytic closures run all steps in one
+ * launch; the MD closure runs one EOS batch and one hydro launch per step.
+ * Errors: MDEOS_EUNPHYS (tangled mesh, non-finite state, or an EOS box that
+ * failed; the state is left at the last good step), MDEOS_ECUDA. */
+mdeos_status mdeos_hydro_step(mdeos_hydro* hy, int32_t nsteps);
+
+/* Copy the state to host arrays (any may be NULL): x, u double[nzones + 1];
+ * rho, e, P, q, c2 double[nzones] (P, q, c2 of the last step);
+ * clock double[3] = (time, last dt, steps taken). */
+mdeos_status mdeos_hydro_state(mdeos_hydro* hy, double* x, double* u, double* rho, double* e,
+                               double* P, double* q, double* c2, double* clock);
+
+/* Results of the last MD-closure batch (host mdeos_result[nzones]).
+ * Errors: MDEOS_EINVAL if the closure is not MD or no step ran. */
+mdeos_status mdeos_hydro_eos_results(mdeos_hydro* hy, mdeos_result* out);
+
+mdeos_status mdeos_hydro_destroy(mdeos_hydro* hy);
 
 /* ---- single-box kernels exposed for parity tests ----------------------
  * These run one box through the same device code as the batch path. */

@@ -19,15 +19,19 @@ MDEOS_OK, MDEOS_PENDING = 0, 1
 MDEOS_EINVAL, MDEOS_ENOMEM, MDEOS_EUNPHYS, MDEOS_EBOX = -1, -2, -3, -4
 MDEOS_ETIMEDOUT, MDEOS_ECUDA, MDEOS_ECANCELLED, MDEOS_ENBR = -5, -6, -7, -8
 MDEOS_REF_ECOLD, MDEOS_REF_FIXED = 0, 1
-MDEOS_REQ_TEMPERATURE = 1
+MDEOS_REQ_TEMPERATURE, MDEOS_REQ_COLD = 1, 2
 PATH_ALLPAIRS, PATH_ALLPAIRS_MI, PATH_NLIST = 0, 1, 2
+CLOSURE_IDEAL_GAS, CLOSURE_MIE_GRUNEISEN, CLOSURE_MD = 0, 1, 2
+BC_WALL, BC_FREE = 0, 1
 
 EXPORTED = [
     "mdeos_config_default", "mdeos_create", "mdeos_submit", "mdeos_poll", "mdeos_destroy",
     "mdeos_last_error", "mdeos_batch_create", "mdeos_batch_launch",
     "mdeos_batch_device_results", "mdeos_batch_results", "mdeos_batch_destroy",
     "mdeos_batch_info", "mdeos_stats", "mdeos_debug_lift", "mdeos_debug_forces",
-    "mdeos_debug_md", "mdeos_submit_noalloc",
+    "mdeos_debug_md", "mdeos_submit_noalloc", "mdeos_warm_export", "mdeos_warm_import",
+    "mdeos_warm_reset", "mdeos_hydro_config_default", "mdeos_hydro_create", "mdeos_hydro_step",
+    "mdeos_hydro_state", "mdeos_hydro_eos_results", "mdeos_hydro_destroy",
 ]
 
 
@@ -39,6 +43,8 @@ class mdeos_config(ctypes.Structure):
         ("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("mass", ctypes.c_double),
         ("rc", ctypes.c_double), ("dt", ctypes.c_double), ("skin", ctypes.c_double),
         ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
+        ("warm_lift_iters", ctypes.c_int32), ("warm_slots", ctypes.c_int32),
+        ("warm_atoms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -60,6 +66,23 @@ class mdeos_result(ctypes.Structure):
         ("cand_per_step", ctypes.c_double), ("element_id", ctypes.c_uint64),
         ("natoms", ctypes.c_int32), ("status", ctypes.c_int32),
         ("nlist_builds", ctypes.c_int32), ("path", ctypes.c_int32),
+        ("warm", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+    ]
+
+
+class mdeos_hydro_config(ctypes.Structure):
+    _fields_ = [
+        ("nzones", ctypes.c_int32), ("closure", ctypes.c_int32),
+        ("bc_left", ctypes.c_int32), ("bc_right", ctypes.c_int32),
+        ("q_quad", ctypes.c_double), ("q_lin", ctypes.c_double),
+        ("cfl", ctypes.c_double), ("dt_grow", ctypes.c_double), ("dt_fixed", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("mg_rho0", ctypes.c_double), ("mg_c", ctypes.c_double),
+        ("mg_s", ctypes.c_double), ("mg_gamma", ctypes.c_double),
+        ("natoms", ctypes.c_int32), ("steps_equil", ctypes.c_int32),
+        ("steps_avg", ctypes.c_int32), ("steps_equil_first", ctypes.c_int32),
+        ("steps_avg_first", ctypes.c_int32), ("first_temperature", ctypes.c_int32),
+        ("e_ref", ctypes.c_double), ("sound_gamma", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("element_base", ctypes.c_uint64),
     ]
 
 
@@ -68,7 +91,7 @@ RESULT_DTYPE = np.dtype([
     ("e_achieved", "f8"), ("P_se", "f8"), ("T_se", "f8"), ("T_target", "f8"),
     ("e_cold", "f8"), ("L", "f8"), ("pairs_per_step", "f8"), ("cand_per_step", "f8"),
     ("element_id", "u8"), ("natoms", "i4"), ("status", "i4"), ("nlist_builds", "i4"),
-    ("path", "i4"),
+    ("path", "i4"), ("warm", "i4"), ("reserved0", "i4"),
 ])
 REQUEST_DTYPE = np.dtype([
     ("rho", "f8"), ("e", "f8"), ("e_ref", "f8"), ("natoms", "i4"), ("steps_equil", "i4"),
@@ -124,10 +147,21 @@ def lib():
         L.mdeos_debug_md.argtypes = [P(mdeos_config), vp, vp, i32, d, i32, d, i32, i32, d, vp,
                                      vp, vp, vp]
         L.mdeos_submit_noalloc.argtypes = [P(mdeos_config), vp, i32, vp, vp]
+        u64 = ctypes.c_uint64
+        L.mdeos_warm_export.argtypes = [vp, u64, i32, vp, vp, P(d)]
+        L.mdeos_warm_import.argtypes = [vp, u64, i32, vp, vp, d]
+        L.mdeos_warm_reset.argtypes = [vp]
+        L.mdeos_hydro_config_default.argtypes = [P(mdeos_hydro_config)]
+        L.mdeos_hydro_config_default.restype = None
+        L.mdeos_hydro_create.argtypes = [vp, P(mdeos_hydro_config), vp, vp, vp, vp, P(vp)]
+        L.mdeos_hydro_step.argtypes = [vp, i32]
+        L.mdeos_hydro_state.argtypes = [vp] + [vp] * 8
+        L.mdeos_hydro_eos_results.argtypes = [vp, vp]
+        L.mdeos_hydro_destroy.argtypes = [vp]
         for name in EXPORTED:
             fn = getattr(L, name)
             if name not in ("mdeos_config_default", "mdeos_last_error",
-                            "mdeos_batch_device_results"):
+                            "mdeos_batch_device_results", "mdeos_hydro_config_default"):
                 fn.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -294,6 +328,88 @@ def mdeos_debug_md(x4, v4, L: float, steps: int, path: int, skin: float = 0.3,
                                 _dptr(cycles) if cycles is not None else ctypes.c_void_p(0),
                                 _stream_ptr(stream)))
     return ep[:steps], ek[:steps]
+
+
+def mdeos_warm_export(h, element_id: int, natoms: int):
+    """Stored final state of an element: (x4, v4 float32 [n,4] host arrays, L)."""
+    x4 = np.zeros((natoms, 4), dtype=np.float32)
+    v4 = np.zeros((natoms, 4), dtype=np.float32)
+    L = ctypes.c_double()
+    _check(lib().mdeos_warm_export(h, element_id, natoms, x4.ctypes.data_as(ctypes.c_void_p),
+                                   v4.ctypes.data_as(ctypes.c_void_p), ctypes.byref(L)))
+    return x4, v4, L.value
+
+
+def mdeos_warm_import(h, element_id: int, x, v, L: float) -> None:
+    """Store a state (positions x and velocities v, [n,3] or [n,4]) for an element."""
+    n = len(x)
+    x4 = np.zeros((n, 4), dtype=np.float32)
+    v4 = np.zeros((n, 4), dtype=np.float32)
+    x4[:, :3] = np.asarray(x)[:, :3]
+    v4[:, :3] = np.asarray(v)[:, :3]
+    _check(lib().mdeos_warm_import(h, element_id, n, x4.ctypes.data_as(ctypes.c_void_p),
+                                   v4.ctypes.data_as(ctypes.c_void_p), float(L)))
+
+
+def mdeos_warm_reset(h) -> None:
+    _check(lib().mdeos_warm_reset(h))
+
+
+def mdeos_hydro_config_default(**over) -> mdeos_hydro_config:
+    c = mdeos_hydro_config()
+    lib().mdeos_hydro_config_default(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+def _f8(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != (n,):
+        raise ValueError(f"expected {n} values, got shape {a.shape}")
+    return a
+
+
+class Hydro:
+    """1D Lagrangian hydro on the GPU (mdeos_hydro_*); the handle must outlive it."""
+
+    def __init__(self, h, cfg: mdeos_hydro_config, x, u, rho, e0):
+        nz = cfg.nzones
+        self.nz = nz
+        self.cfg = cfg
+        self._keep = [_f8(x, nz + 1), _f8(u, nz + 1), _f8(rho, nz), _f8(e0, nz)]
+        self.hy = ctypes.c_void_p()
+        vp = [a.ctypes.data_as(ctypes.c_void_p) for a in self._keep]
+        _check(lib().mdeos_hydro_create(h, ctypes.byref(cfg), *vp, ctypes.byref(self.hy)))
+
+    def step(self, nsteps: int = 1) -> None:
+        _check(lib().mdeos_hydro_step(self.hy, nsteps))
+
+    def state(self) -> dict:
+        nz = self.nz
+        out = {k: np.zeros(nz + 1) for k in ("x", "u")}
+        out.update({k: np.zeros(nz) for k in ("rho", "e", "P", "q", "c2")})
+        clock = np.zeros(3)
+        ptrs = [out[k].ctypes.data_as(ctypes.c_void_p) for k in ("x", "u", "rho", "e", "P", "q", "c2")]
+        _check(lib().mdeos_hydro_state(self.hy, *ptrs, clock.ctypes.data_as(ctypes.c_void_p)))
+        out["t"], out["dt"], out["steps"] = clock[0], clock[1], int(clock[2])
+        return out
+
+    def eos_results(self) -> np.ndarray:
+        out = np.zeros(self.nz, dtype=RESULT_DTYPE)
+        _check(lib().mdeos_hydro_eos_results(self.hy, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def close(self):
+        if self.hy:
+            lib().mdeos_hydro_destroy(self.hy)
+            self.hy = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def e_from_temperature(T, natoms):

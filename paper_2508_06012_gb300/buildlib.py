@@ -12,7 +12,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdeos.so")
-SOURCES = ["mdeos_batch.cu", "mdeos_debug.cu", "mdeos_noalloc.cu", "mdeos_api.cu"]
+SOURCES = ["mdeos_batch.cu", "mdeos_debug.cu", "mdeos_noalloc.cu", "mdeos_api.cu",
+           "mdeos_hydro.cu"]
+# per-file flags: the hydro update is FP64 in a fixed operation order, without
+# contracted multiply-adds on the device or the host
+EXTRA = {"mdeos_hydro.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]}
 HEADERS = ["mdeos_device.cuh", "mdeos_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -45,7 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + deps_common):
-            cmd = [nvcc] + common + (["-Xptxas", "-v"] if verbose else []) + ["-c", s, "-o", o]
+            cmd = [nvcc] + common + EXTRA.get(src, []) + (["-Xptxas", "-v"] if verbose else []) \
+                + ["-c", s, "-o", o]
             jobs.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

@@ -13,6 +13,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "mdeos_internal.h"
@@ -80,6 +81,9 @@ extern "C" void mdeos_config_default(mdeos_config* c) {
   c->skin = 0.0;
   c->hbm_budget_bytes = 0;
   c->cuda_stream = nullptr;
+  c->warm_lift_iters = 1;
+  c->warm_slots = 0;
+  c->warm_atoms = 0;
 }
 
 static mdeos_status check_config(const mdeos_config* c) {
@@ -94,6 +98,11 @@ static mdeos_status check_config(const mdeos_config* c) {
   if (c->energy_ref_mode != MDEOS_REF_ECOLD && c->energy_ref_mode != MDEOS_REF_FIXED)
     return fail(MDEOS_EINVAL, "energy_ref_mode must be REF_ECOLD or REF_FIXED");
   if (c->skin > 2.0 * c->rc) return fail(MDEOS_EINVAL, "skin larger than 2 rc");
+  if (c->warm_lift_iters < 1 || c->warm_lift_iters > 64)
+    return fail(MDEOS_EINVAL, "warm_lift_iters out of range 1..64");
+  if (c->warm_slots < 0 || c->warm_atoms < 0 || c->warm_atoms > kMaxAtoms ||
+      (c->warm_slots > 0 && c->warm_atoms < 2))
+    return fail(MDEOS_EINVAL, "warm_slots / warm_atoms out of range");
   return MDEOS_OK;
 }
 
@@ -115,6 +124,7 @@ static RunParams make_run_params(const mdeos_config* c) {
   rp.rescale_every_avg = c->rescale_every_avg;
   rp.se_blocks = c->se_blocks;
   rp.ref_mode = c->energy_ref_mode;
+  rp.warm_lift_iters = c->warm_lift_iters;
   return rp;
 }
 
@@ -154,7 +164,7 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx) 
                   std::isfinite(r.e) && std::isfinite(r.e_ref) && r.steps_avg >= c.se_blocks &&
                   r.steps_equil >= 0 && (long long)r.steps_equil + r.steps_avg < (1LL << 30) &&
                   (r.steps_equil == 0 || (c.lift_iters >= 1 && r.steps_equil >= c.lift_iters)) &&
-                  (r.flags & ~(uint32_t)MDEOS_REQ_TEMPERATURE) == 0;
+                  (r.flags & ~(uint32_t)(MDEOS_REQ_TEMPERATURE | MDEOS_REQ_COLD)) == 0;
   if (!ok) {
     p.status = MDEOS_EINVAL;
     return p;
@@ -330,6 +340,11 @@ struct PinnedBlock {
   size_t size = 0;
 };
 
+struct PinnedBlockPtr {
+  void* p = nullptr;
+  size_t size = 0;
+};
+
 struct TicketState {
   int n = 0;
   cudaEvent_t done = nullptr;
@@ -342,8 +357,24 @@ struct TicketState {
   size_t bytes = 0;
 };
 
+struct WarmSlot {
+  int slot = 0;
+  int natoms = 0;   // atoms of the state last planned into the slot
+  double L = 0.0;   // its box side
+};
+
 struct mdeos_handle {
   mdeos_config cfg;
+  // warm-start store: slot k holds x float4[warm_atoms] then v float4[warm_atoms]
+  float4* d_warm = nullptr;
+  int* d_warm_flag = nullptr;
+  size_t warm_bytes = 0;
+  std::unordered_map<uint64_t, WarmSlot> warm_map;
+  int warm_next = 0;
+  // reusable device work table of eval_into_device
+  void* d_eval = nullptr;
+  size_t eval_bytes = 0;
+  PinnedBlockPtr eval_pinned;
   RunParams rp;
   int device = 0, nsm = 0, smem_max = 0;
   cudaStream_t stream = nullptr;
@@ -444,6 +475,24 @@ extern "C" mdeos_status mdeos_create(const mdeos_config* cfg, mdeos_handle** out
     delete h;
     return cuda_fail(e, "kernel attributes (is this an sm_103 GPU?)");
   }
+  if (cfg->warm_slots > 0) {
+    const size_t slot_bytes = (size_t)2 * cfg->warm_atoms * sizeof(float4);
+    h->warm_bytes = (size_t)cfg->warm_slots * slot_bytes + (size_t)cfg->warm_slots * sizeof(int);
+    if (cfg->hbm_budget_bytes && h->warm_bytes > cfg->hbm_budget_bytes) {
+      delete h;
+      return fail(MDEOS_ENOMEM, "warm-start store exceeds the HBM budget");
+    }
+    e = cudaMalloc(&h->d_warm, (size_t)cfg->warm_slots * slot_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_warm_flag, (size_t)cfg->warm_slots * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_warm_flag, 0, (size_t)cfg->warm_slots * sizeof(int));
+    if (e != cudaSuccess) {
+      if (h->d_warm) cudaFree(h->d_warm);
+      if (h->d_warm_flag) cudaFree(h->d_warm_flag);
+      delete h;
+      return cuda_fail(e, "warm-start store allocation");
+    }
+    h->used_bytes += h->warm_bytes;
+  }
   if (cfg->cuda_stream) {
     h->stream = (cudaStream_t)cfg->cuda_stream;
   } else {
@@ -475,6 +524,10 @@ extern "C" mdeos_status mdeos_destroy(mdeos_handle* h) {
   cudaStreamSynchronize(h->stream);
   for (auto& b : h->pinned_free) cudaFreeHost(b.p);
   if (h->d_nl) cudaFree(h->d_nl);
+  if (h->d_warm) cudaFree(h->d_warm);
+  if (h->d_warm_flag) cudaFree(h->d_warm_flag);
+  if (h->d_eval) cudaFree(h->d_eval);
+  if (h->eval_pinned.p) cudaFreeHost(h->eval_pinned.p);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return MDEOS_OK;
@@ -489,6 +542,35 @@ static void planning_result(mdeos_result& r, int status, const mdeos_request& q)
   r.path = -1;
 }
 
+// Attach warm-start slots to the planned boxes (slot rules in mdeos.h).
+static void assign_warm(mdeos_handle* h, Plan& plan, const mdeos_request* reqs) {
+  if (!h->d_warm) return;
+  const int cap = h->cfg.warm_atoms;
+  std::unordered_set<uint64_t> seen;
+  for (BoxDesc& bd : plan.boxes) {
+    const mdeos_request& r = reqs[bd.out_index];
+    if (r.element_id == 0 || r.natoms > cap) continue;
+    if (!seen.insert(r.element_id).second) continue;  // repeated element: cold, not stored
+    auto it = h->warm_map.find(r.element_id);
+    if (it == h->warm_map.end()) {
+      if (h->warm_next >= h->cfg.warm_slots) continue;  // store full: cold, not stored
+      WarmSlot ws;
+      ws.slot = h->warm_next++;
+      it = h->warm_map.emplace(r.element_id, ws).first;
+    }
+    WarmSlot& ws = it->second;
+    const bool try_warm = ws.natoms == r.natoms && ws.L > 0.0 &&
+                          (r.flags & MDEOS_REQ_COLD) == 0 &&
+                          (r.steps_equil == 0 || r.steps_equil >= h->cfg.warm_lift_iters);
+    bd.warm_state = h->d_warm + (size_t)ws.slot * 2 * cap;
+    bd.warm_flag = h->d_warm_flag + ws.slot;
+    bd.warm_cap = cap;
+    bd.L_old = try_warm ? ws.L : 0.0;
+    ws.natoms = r.natoms;
+    ws.L = bd.L;
+  }
+}
+
 extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs, int32_t n,
                                      uint64_t* ticket) {
   if (!h || !reqs || !ticket || n < 1) return fail(MDEOS_EINVAL, "bad submit arguments");
@@ -497,6 +579,7 @@ extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs,
   Plan plan;
   mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan);
   if (st != MDEOS_OK) return st;
+  assign_warm(h, plan, reqs);
   TicketState t;
   t.n = n;
   t.status = plan.status;
@@ -723,6 +806,157 @@ extern "C" mdeos_status mdeos_batch_destroy(mdeos_batch* b) {
   delete b;
   return MDEOS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// warm-start store
+
+extern "C" mdeos_status mdeos_warm_export(mdeos_handle* h, uint64_t element_id, int32_t natoms,
+                                          float* x4, float* v4, double* L) {
+  if (!h || !x4 || !v4 || !L || natoms < 2) return fail(MDEOS_EINVAL, "bad warm_export arguments");
+  std::lock_guard<std::mutex> lock(h->mu);
+  auto it = h->warm_map.find(element_id);
+  if (!h->d_warm || it == h->warm_map.end() || it->second.natoms != natoms)
+    return fail(MDEOS_EINVAL, "no stored state of this element and size");
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  const WarmSlot& ws = it->second;
+  int flag = 0;
+  CK(cudaMemcpy(&flag, h->d_warm_flag + ws.slot, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag != 1) return fail(MDEOS_EINVAL, "the element's last evaluation failed");
+  const float4* base = h->d_warm + (size_t)ws.slot * 2 * h->cfg.warm_atoms;
+  CK(cudaMemcpy(x4, base, (size_t)natoms * sizeof(float4), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(v4, base + h->cfg.warm_atoms, (size_t)natoms * sizeof(float4),
+                cudaMemcpyDeviceToHost));
+  *L = ws.L;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_warm_import(mdeos_handle* h, uint64_t element_id, int32_t natoms,
+                                          const float* x4, const float* v4, double L) {
+  if (!h || !x4 || !v4 || natoms < 2 || !(L > 0) || element_id == 0)
+    return fail(MDEOS_EINVAL, "bad warm_import arguments");
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (!h->d_warm || natoms > h->cfg.warm_atoms)
+    return fail(MDEOS_EINVAL, "no warm store, or natoms above warm_atoms");
+  auto it = h->warm_map.find(element_id);
+  if (it == h->warm_map.end()) {
+    if (h->warm_next >= h->cfg.warm_slots) return fail(MDEOS_ENOMEM, "warm store full");
+    WarmSlot ws;
+    ws.slot = h->warm_next++;
+    it = h->warm_map.emplace(element_id, ws).first;
+  }
+  WarmSlot& ws = it->second;
+  std::vector<float4> hx((size_t)natoms), hv((size_t)natoms);
+  for (int i = 0; i < natoms; ++i) {
+    int id = i;
+    float w;
+    std::memcpy(&w, &id, sizeof(float));
+    hx[i] = make_float4(x4[4 * i], x4[4 * i + 1], x4[4 * i + 2], w);
+    hv[i] = make_float4(v4[4 * i], v4[4 * i + 1], v4[4 * i + 2], 0.f);
+  }
+  CK(cudaSetDevice(h->device));
+  float4* base = h->d_warm + (size_t)ws.slot * 2 * h->cfg.warm_atoms;
+  const int one = 1;
+  CK(cudaMemcpyAsync(base, hx.data(), (size_t)natoms * sizeof(float4), cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaMemcpyAsync(base + h->cfg.warm_atoms, hv.data(), (size_t)natoms * sizeof(float4),
+                     cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_warm_flag + ws.slot, &one, sizeof(int), cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  ws.natoms = natoms;
+  ws.L = L;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_warm_reset(mdeos_handle* h) {
+  if (!h) return fail(MDEOS_EINVAL, "handle is NULL");
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (!h->d_warm) return MDEOS_OK;
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemsetAsync(h->d_warm_flag, 0, (size_t)h->cfg.warm_slots * sizeof(int), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->warm_map.clear();
+  h->warm_next = 0;
+  return MDEOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation into a caller's device array (used by the hydro driver)
+
+namespace mdeos {
+
+cudaStream_t handle_stream(const mdeos_handle* h) { return h->stream; }
+int handle_device(const mdeos_handle* h) { return h->device; }
+const mdeos_config& handle_config(const mdeos_handle* h) { return h->cfg; }
+
+// Plans n requests (warm store included), uploads the work table and launches
+// the persistent batch kernel on the handle's stream; d_results (device, n
+// records) receives every result, planning rejections included, when the
+// stream reaches it.  Synchronises the stream first: the work table buffers are
+// reused from call to call.
+mdeos_status eval_into_device(mdeos_handle* h, const mdeos_request* reqs, int n,
+                              mdeos_result* d_results) {
+  if (!h || !reqs || !d_results || n < 1) return fail(MDEOS_EINVAL, "bad eval arguments");
+  std::lock_guard<std::mutex> lock(h->mu);
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  Plan plan;
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan);
+  if (st != MDEOS_OK) return st;
+  assign_warm(h, plan, reqs);
+  const size_t nb = plan.boxes.size(), ni = plan.items.size();
+  const size_t off_items = (nb * sizeof(BoxDesc) + 255) & ~size_t(255);
+  const size_t in_bytes = off_items + ni * sizeof(WorkItem);
+  const size_t off_cnt = (in_bytes + 255) & ~size_t(255);
+  const size_t dev_bytes = off_cnt + 256;
+  bool rejected = false;
+  for (int i = 0; i < n; ++i) rejected = rejected || plan.status[i] != MDEOS_OK;
+  const size_t host_bytes = std::max(in_bytes, rejected ? (size_t)n * sizeof(mdeos_result) : 0);
+  if (dev_bytes > h->eval_bytes) {
+    if (h->cfg.hbm_budget_bytes && h->used_bytes + dev_bytes - h->eval_bytes > h->cfg.hbm_budget_bytes)
+      return fail(MDEOS_ENOMEM, "batch exceeds the HBM budget");
+    if (h->d_eval) CK(cudaFree(h->d_eval));
+    h->used_bytes -= h->eval_bytes;
+    h->d_eval = nullptr;
+    h->eval_bytes = 0;
+    CK(cudaMalloc(&h->d_eval, dev_bytes));
+    h->eval_bytes = dev_bytes;
+    h->used_bytes += dev_bytes;
+  }
+  if (host_bytes > h->eval_pinned.size) {
+    if (h->eval_pinned.p) CK(cudaFreeHost(h->eval_pinned.p));
+    h->eval_pinned.p = nullptr;
+    h->eval_pinned.size = 0;
+    CK(cudaMallocHost(&h->eval_pinned.p, host_bytes));
+    h->eval_pinned.size = host_bytes;
+  }
+  char* d = (char*)h->d_eval;
+  if (rejected) {
+    mdeos_result* init = (mdeos_result*)h->eval_pinned.p;
+    for (int i = 0; i < n; ++i) planning_result(init[i], plan.status[i], reqs[i]);
+    CK(cudaMemcpyAsync(d_results, init, (size_t)n * sizeof(mdeos_result), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // the staging buffer is reused below
+  }
+  if (nb == 0) return MDEOS_OK;
+  std::memcpy(h->eval_pinned.p, plan.boxes.data(), nb * sizeof(BoxDesc));
+  std::memcpy((char*)h->eval_pinned.p + off_items, plan.items.data(), ni * sizeof(WorkItem));
+  const size_t scratch = (size_t)plan.grid * plan.nl_per_cta * sizeof(uint16_t);
+  if ((st = ensure_scratch(h, scratch)) != MDEOS_OK) return st;
+  CK(cudaMemcpyAsync(d, h->eval_pinned.p, in_bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream));
+  cudaError_t e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni,
+                                   (int*)(d + off_cnt), d_results, h->d_nl, plan.nl_per_cta, h->rp,
+                                   plan.grid, plan.smem, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "eos_batch_kernel launch");
+  h->launches += 1;
+  return MDEOS_OK;
+}
+
+void count_launch(mdeos_handle* h, long long k) { h->launches += k; }
+
+}  // namespace mdeos
 
 // ---------------------------------------------------------------------------
 // single-box parity entry points

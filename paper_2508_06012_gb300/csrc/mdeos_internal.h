@@ -1,6 +1,8 @@
 // Internal types shared by the host engine and the device kernels of the
 // batched atomistic EOS path.  Not part of the C ABI.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -30,6 +32,7 @@ struct RunParams {
   float mass_f;
   double mass;
   int lift_iters, rescale_every_equil, rescale_every_avg, se_blocks, ref_mode;
+  int warm_lift_iters;
 };
 
 // One box as planned on the host.
@@ -46,6 +49,13 @@ struct BoxDesc {
   int nc_lat;               // FCC cells per axis of the lifted lattice
   float skin;
   int out_index;            // slot in the result array
+  // warm-start slot (nullptr: none): x float4[warm_cap] then v float4[warm_cap];
+  // its flag is 1 while the slot holds a valid state of this element
+  float4* warm_state;
+  int* warm_flag;
+  double L_old;             // box side of the stored state; > 0: try a warm start
+  int warm_cap;
+  int warm_pad;
 };
 
 // A unit of the persistent kernel's work queue: up to 8 boxes of one size
