@@ -30,6 +30,12 @@ cudaError_t launch_debug_lift(const BoxDesc& bd, const RunParams& rp, double T, 
 cudaError_t launch_debug_forces(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
                                 int smem, const float4* x4, float4* f4, double* ew,
                                 long long* pairs, uint16_t* nl, cudaStream_t st);
+cudaError_t launch_debug_big_forces(const BoxDesc& bd, const RunParams& rp, unsigned char* scratch,
+                                    const float4* x4, float4* f4, double* ew, long long* pairs,
+                                    cudaStream_t st);
+cudaError_t launch_debug_big_md(const BoxDesc& bd, const RunParams& rp, unsigned char* scratch,
+                                float4* x4, float4* v4, int steps, double T, int every, double* ep,
+                                double* ek, long long* cyc, cudaStream_t st);
 cudaError_t launch_debug_md(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
                             int smem, float4* x4, float4* v4, int steps, double T, int every,
                             double* ep, double* ek, long long* cyc, uint16_t* nl,
@@ -135,6 +141,7 @@ struct BoxPlan {
   BoxDesc bd;
   int warps = 4, apt = 1;
   int ncell = 1;
+  bool big = false;  // above the shared-memory limit: global-memory state, one CTA
   double cost = 0.0;
   int status = MDEOS_OK;
 };
@@ -145,7 +152,7 @@ static int round_apt(int a) { return a <= 1 ? 1 : (a <= 2 ? 2 : 4); }
 // minimum image) simulate the same box.
 static double box_side(int n, double rho) { return (double)(float)std::cbrt((double)n / rho); }
 
-static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx) {
+static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, bool allow_big) {
   BoxPlan p;
   BoxDesc& b = p.bd;
   std::memset(&b, 0, sizeof(b));
@@ -160,7 +167,8 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx) 
   b.flags = r.flags;
   b.out_index = idx;
   const int n = r.natoms;
-  const bool ok = n >= 2 && n <= kMaxAtoms && std::isfinite(r.rho) && r.rho > 0 &&
+  const bool ok = n >= 2 && n <= (allow_big ? kMaxAtomsBig : kMaxAtoms) && std::isfinite(r.rho) &&
+                  r.rho > 0 &&
                   std::isfinite(r.e) && std::isfinite(r.e_ref) && r.steps_avg >= c.se_blocks &&
                   r.steps_equil >= 0 && (long long)r.steps_equil + r.steps_avg < (1LL << 30) &&
                   (r.steps_equil == 0 || (c.lift_iters >= 1 && r.steps_equil >= c.lift_iters)) &&
@@ -182,6 +190,35 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx) 
   // path choice (autotuner defaults; a measured table can override per class)
   double skin = c.skin > 0 ? c.skin : 0.3;
   const double smax = 0.5 * L - c.rc;
+  if (n > kMaxAtoms) {
+    // above the shared-memory limit: Verlet list, state in global memory
+    if (smax < 0.15) {
+      p.status = MDEOS_EBOX;
+      return p;
+    }
+    skin = std::min(skin, smax);
+    const double rs = c.rc + skin;
+    int nc = (int)std::floor(L / rs);
+    while (nc > 3 && nc * nc * nc > kMaxCellsBig) --nc;
+    if (nc < 3) {
+      p.status = MDEOS_EBOX;
+      return p;
+    }
+    b.path = PATH_NLIST;
+    b.skin = (float)skin;
+    b.nc_cell = nc;
+    const double expect = 4.18879020478639 * rs * rs * rs * r.rho;
+    const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(r.rho, 0.9);
+    int mx = (int)std::ceil(1.3 * expect_cap + 32.0);
+    mx = std::min(mx, n - 1);
+    b.maxnb = (mx + 7) & ~7;
+    p.big = true;
+    p.ncell = nc * nc * nc;
+    p.warps = 32;
+    p.apt = 0;
+    p.cost = steps * n * (expect * 1.15 + 8.0);
+    return p;
+  }
   if (L < 2.0 * c.rc) {
     b.path = PATH_ALLPAIRS_MI;
   } else if (n <= 128 || smax < 0.15) {
@@ -232,14 +269,14 @@ struct Plan {
 };
 
 static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_config& c, int nsm,
-                              int smem_max, Plan& plan) {
+                              int smem_max, Plan& plan, bool allow_big = true) {
   plan.boxes.clear();
   plan.items.clear();
   plan.status.assign(n, MDEOS_OK);
   std::vector<BoxPlan> bp;
   bp.reserve(n);
   for (int i = 0; i < n; ++i) {
-    BoxPlan p = plan_box(reqs[i], c, i);
+    BoxPlan p = plan_box(reqs[i], c, i, allow_big);
     plan.status[i] = p.status;
     if (p.status == MDEOS_OK) bp.push_back(p);
   }
@@ -259,6 +296,25 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
   plan.nl_per_cta = 0;
   size_t k = 0;
   while (k < bp.size()) {
+    if (bp[k].big) {  // one box per item, scratch in global memory
+      WorkItem wi;
+      std::memset(&wi, 0, sizeof(wi));
+      wi.nbox = 1;
+      wi.warps_per_box = 32;
+      wi.apt = 0;
+      wi.big = 1;
+      wi.ncell_cap = bp[k].ncell;
+      wi.smem_stride = kBigSharedBytes;
+      const size_t bytes = big_scratch_bytes(bp[k].bd.natoms, bp[k].ncell, bp[k].bd.maxnb);
+      wi.nl_stride = (int)(((bytes + 15) & ~(size_t)15) / 2);
+      wi.box[0] = (int)plan.boxes.size();
+      plan.boxes.push_back(bp[k].bd);
+      plan.smem = std::max(plan.smem, kBigSharedBytes);
+      plan.nl_per_cta = std::max(plan.nl_per_cta, (long long)wi.nl_stride);
+      items.push_back({wi, bp[k].cost});
+      ++k;
+      continue;
+    }
     const int warps = bp[k].warps, apt = bp[k].apt;
     const int npad = warps * 32 * apt;
     const int per_cta = std::min(kCtaThreads / (warps * 32), kMaxBoxesPerItem);
@@ -319,7 +375,7 @@ mdeos_status mdeos::plan_for_noalloc(const mdeos_request* reqs, int n, const mde
   mdeos_status st = check_config(&c);
   if (st != MDEOS_OK) return st;
   Plan plan;
-  st = make_plan(reqs, n, c, nsm, smem_max, plan);
+  st = make_plan(reqs, n, c, nsm, smem_max, plan, /*allow_big=*/false);
   if (st != MDEOS_OK) return st;
   boxes = plan.boxes;
   items = plan.items;
@@ -1012,6 +1068,38 @@ static mdeos_status debug_setup(const mdeos_config* cfg, int n, double L, int pa
   return MDEOS_OK;
 }
 
+// Boxes above the shared-memory limit: Verlet path with state in global memory.
+// The list capacity is twice the liquid-density estimate (tests hand in arbitrary
+// configurations; an overflow is reported as a NaN energy).
+static mdeos_status debug_big_setup(const mdeos_config* cfg, int n, double L, int path,
+                                    double skin, BoxDesc& bd, RunParams& rp, size_t& scratch) {
+  mdeos_status st = check_config(cfg);
+  if (st != MDEOS_OK) return st;
+  if (n <= kMaxAtoms || n > kMaxAtomsBig) return fail(MDEOS_EINVAL, "n out of range");
+  if (path != PATH_NLIST) return fail(MDEOS_EINVAL, "boxes above 4096 atoms use the Verlet path");
+  if (!(skin >= 0) || L < 2 * (cfg->rc + skin))
+    return fail(MDEOS_EBOX, "Verlet list needs L >= 2 (rc + skin)");
+  const double rs = cfg->rc + skin;
+  int nc = (int)std::floor(L / rs);
+  while (nc > 3 && nc * nc * nc > kMaxCellsBig) --nc;
+  if (nc < 3) return fail(MDEOS_EBOX, "fewer than 3 cells per axis");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return fail(MDEOS_ECUDA, "no CUDA device available");
+  rp = make_run_params(cfg);
+  std::memset(&bd, 0, sizeof(bd));
+  bd.natoms = n;
+  bd.L = L;
+  bd.path = PATH_NLIST;
+  bd.skin = (float)skin;
+  bd.nc_cell = nc;
+  const double rho = n / (L * L * L);
+  int mx = (int)std::ceil(2.0 * 4.18879020478639 * rs * rs * rs * std::max(rho, 0.9) + 64.0);
+  bd.maxnb = (std::min(mx, n - 1) + 7) & ~7;
+  scratch = big_scratch_bytes(n, nc * nc * nc, bd.maxnb);
+  return MDEOS_OK;
+}
+
 extern "C" mdeos_status mdeos_debug_lift(const mdeos_config* cfg, int32_t n, double rho, double T,
                                          uint64_t seed, float* x4, float* v4, double* e_out,
                                          double* L_out, void* stream) {
@@ -1038,6 +1126,20 @@ extern "C" mdeos_status mdeos_debug_forces(const mdeos_config* cfg, const float*
   if (!x4 || !f4 || !ew) return fail(MDEOS_EINVAL, "bad arguments");
   BoxDesc bd;
   RunParams rp;
+  if (n > kMaxAtoms) {
+    size_t sb = 0;
+    mdeos_status st = debug_big_setup(cfg, n, L, path, skin, bd, rp, sb);
+    if (st != MDEOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, sb, s));
+    cudaError_t e = launch_debug_big_forces(bd, rp, scratch, (const float4*)x4, (float4*)f4, ew,
+                                            pairs, s);
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "debug_big_forces launch");
+    CK(cudaStreamSynchronize(s));
+    return MDEOS_OK;
+  }
   int apt, ncell, smem;
   size_t nlb;
   mdeos_status st = debug_setup(cfg, n, L, path, skin, bd, rp, apt, ncell, smem, nlb);
@@ -1061,6 +1163,20 @@ extern "C" mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float
   if (!x4 || !v4 || steps < 0 || rescale_every < 0) return fail(MDEOS_EINVAL, "bad arguments");
   BoxDesc bd;
   RunParams rp;
+  if (n > kMaxAtoms) {
+    size_t sb = 0;
+    mdeos_status st = debug_big_setup(cfg, n, L, path, skin, bd, rp, sb);
+    if (st != MDEOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, sb, s));
+    cudaError_t e = launch_debug_big_md(bd, rp, scratch, (float4*)x4, (float4*)v4, steps, T_target,
+                                        rescale_every, epot, ekin, cycles, s);
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "debug_big_md launch");
+    CK(cudaStreamSynchronize(s));
+    return MDEOS_OK;
+  }
   int apt, ncell, smem;
   size_t nlb;
   mdeos_status st = debug_setup(cfg, n, L, path, skin, bd, rp, apt, ncell, smem, nlb);

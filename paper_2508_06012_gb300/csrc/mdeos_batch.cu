@@ -3,7 +3,7 @@
 // ordered by decreasing cost, and runs every box of the item concurrently in
 // its own warp group (arXiv 2508.06012, Sec. III: one independent MD run per
 // element and call).
-#include "mdeos_device.cuh"
+#include "mdeos_big.cuh"
 
 namespace mdeos {
 
@@ -21,6 +21,12 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     __syncthreads();
     if (it >= nitems) break;
     const WorkItem wi = items[it];
+    if (wi.big) {  // one box above the shared-memory limit, the whole CTA
+      const BoxDesc& bd = boxes[wi.box[0]];
+      run_big(reinterpret_cast<unsigned char*>(nl_cta), reinterpret_cast<BigShared*>(smem), bd, rp,
+              results + bd.out_index);
+      continue;
+    }
     const int ntb = wi.warps_per_box * 32;
     const int grp = threadIdx.x / ntb;
     if (grp < wi.nbox) {

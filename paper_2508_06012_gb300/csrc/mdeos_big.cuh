@@ -1,0 +1,597 @@
+// Boxes above the shared-memory limit (4097..32768 atoms): the same lifting ->
+// MD -> restriction as run_box (Sec. III, Eq. 6-11), run by one whole CTA with
+// the box state in global memory.
+//
+// Layout of a box's per-CTA scratch (16-byte aligned, `cap` = n rounded up to 32):
+//   x, v, x2, v2, f   float4[cap] each (x.w = atom id, v.w = displacement bound,
+//                     f.w = list length; x2/v2 receive the cell-ordered copy at a
+//                     rebuild, then the two buffers swap roles)
+//   cell counts, cell starts   int[ncell + 1] each
+//   Verlet list       uint16 indices, 8 per 16-byte word, word kb of slot s at
+//                     (kb * cap + s) * 16 bytes
+// A rebuild sorts the atoms into cell order, so the 1024 atoms a CTA works on at
+// once are spatial neighbours and their gathers stay in L1 (~100 KB of positions
+// around a slab of cells).  FP64 appears only in the per-step leader-warp
+// accumulation and the once-per-box lifting arithmetic, as in run_box.
+#pragma once
+
+#include "mdeos_device.cuh"
+
+namespace mdeos {
+
+// shared memory of a big-box CTA
+struct BigShared {
+  float red[32 * kRedSlots];
+  double bc[8];
+  double acc[kAccDoubles];
+  int bcnt[kMaxSeBlocks];
+  int ctrl[16];
+  int scan[32];
+};
+
+static_assert(sizeof(BigShared) <= kBigSharedBytes, "big-box shared memory");
+
+struct BigMem {
+  float4 *x, *v, *x2, *v2, *f;
+  int *cnt, *start;
+  uint4* nl;
+  int cap;
+};
+
+__device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
+  BigMem m;
+  m.cap = big_cap(n);
+  float4* q = reinterpret_cast<float4*>(p);
+  m.x = q;
+  m.v = q + m.cap;
+  m.x2 = q + 2 * m.cap;
+  m.v2 = q + 3 * m.cap;
+  m.f = q + 4 * m.cap;
+  unsigned char* c = p + (size_t)80 * m.cap;
+  m.cnt = reinterpret_cast<int*>(c);
+  m.start = m.cnt + ncell + 1;
+  m.nl = reinterpret_cast<uint4*>(c + big_cells_bytes(ncell));
+  return m;
+}
+
+// Sum NQ per-thread FP32 values over the CTA; FP32 warp sums, FP64 across warps.
+template <int NQ>
+__device__ void block_sum(BigShared* sh, const float (&q)[NQ], double (&out)[NQ]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const float s = warp_sum(q[k]);
+    if (lane == 0) sh->red[warp * kRedSlots + k] = s;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < NQ) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += (double)sh->red[w * kRedSlots + lane];
+    sh->bc[lane] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) out[k] = sh->bc[k];
+}
+
+// Lifted FCC lattice (Eq. 6-7), same site order as lattice_own; velocities zero.
+__device__ inline void big_lattice(const BigMem& m, const BoxDesc& bd) {
+  const int nc = bd.nc_lat;
+  const double a = bd.L / nc;
+  for (int i = threadIdx.x; i < bd.natoms; i += blockDim.x) {
+    const int c = i >> 2, bb = i & 3;
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    const double bx = (bb == 1 || bb == 2) ? 0.5 : 0.0;
+    const double by = (bb == 1 || bb == 3) ? 0.5 : 0.0;
+    const double bz = (bb == 2 || bb == 3) ? 0.5 : 0.0;
+    m.x[i] = make_float4((float)(a * (cx + bx)), (float)(a * (cy + by)), (float)(a * (cz + bz)),
+                         __int_as_float(i));
+    m.v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__device__ inline void big_wrap(const BigMem& m, int n, float L, float invL) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float4 xi = m.x[i];
+    xi.x -= L * floorf(xi.x * invL);
+    xi.y -= L * floorf(xi.y * invL);
+    xi.z -= L * floorf(xi.z * invL);
+    xi.x = fmaxf((xi.x >= L) ? xi.x - L : xi.x, 0.f);
+    xi.y = fmaxf((xi.y >= L) ? xi.y - L : xi.y, 0.f);
+    xi.z = fmaxf((xi.z >= L) ? xi.z - L : xi.z, 0.f);
+    m.x[i] = xi;
+    m.v[i].w = 0.f;
+  }
+}
+
+// Verlet list from wrapped positions: counting sort into cell order (inside a
+// cell by previous slot: deterministic), permutation of x and v into the second
+// buffers (then swapped), 27-cell search with one image shift per cell.
+static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float L, float cinv, float rs2,
+                          int maxnb) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ncell = nc * nc * nc;
+  for (int c = tid; c < ncell; c += nt) m.cnt[c] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    const int c = cell_of(m.x[i], cinv, nc);
+    m.f[i].x = __int_as_float(c);
+    atomicAdd(&m.cnt[c], 1);
+  }
+  __syncthreads();
+  {  // exclusive scan of the counts into starts; counts become insertion cursors
+    const int per = (ncell + nt - 1) / nt;
+    const int lo = min(tid * per, ncell), hi = min(lo + per, ncell);
+    int s = 0;
+    for (int c = lo; c < hi; ++c) s += m.cnt[c];
+    const int lane = tid & 31, warp = tid >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh->scan[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int v = lane < (nt >> 5) ? sh->scan[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      sh->scan[lane] = v;
+    }
+    __syncthreads();
+    int off = (warp > 0 ? sh->scan[warp - 1] : 0) + incl - s;
+    for (int c = lo; c < hi; ++c) {
+      const int k = m.cnt[c];
+      m.start[c] = off;
+      off += k;
+      m.cnt[c] = 0;
+    }
+    if (tid == 0) m.start[ncell] = n;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    const int c = __float_as_int(m.f[i].x);
+    const int s = m.start[c] + atomicAdd(&m.cnt[c], 1);
+    reinterpret_cast<float*>(m.x2 + s)[3] = __int_as_float(i);
+  }
+  __syncthreads();
+  for (int c = tid; c < ncell; c += nt) {  // insertion sort of the previous slots
+    const int lo = m.start[c], hi = m.start[c + 1];
+    for (int a = lo + 1; a < hi; ++a) {
+      const float key = m.x2[a].w;
+      const int kk = __float_as_int(key);
+      int b = a - 1;
+      while (b >= lo && __float_as_int(m.x2[b].w) > kk) {
+        reinterpret_cast<float*>(m.x2 + b + 1)[3] = m.x2[b].w;
+        --b;
+      }
+      reinterpret_cast<float*>(m.x2 + b + 1)[3] = key;
+    }
+  }
+  __syncthreads();
+  for (int s = tid; s < n; s += nt) {
+    const int i = __float_as_int(m.x2[s].w);
+    m.x2[s] = m.x[i];
+    const float4 vi = m.v[i];
+    m.v2[s] = make_float4(vi.x, vi.y, vi.z, 0.f);
+  }
+  __syncthreads();
+  {
+    float4* t = m.x;
+    m.x = m.x2;
+    m.x2 = t;
+    t = m.v;
+    m.v = m.v2;
+    m.v2 = t;
+  }
+  uint16_t* row = reinterpret_cast<uint16_t*>(m.nl);
+  const size_t wstride = (size_t)m.cap * 8;  // uint16 entries between words of one slot
+  for (int s = tid; s < n; s += nt) {
+    const float4 xi = m.x[s];
+    const int cx = min((int)(xi.x * cinv), nc - 1);
+    const int cy = min((int)(xi.y * cinv), nc - 1);
+    const int cz = min((int)(xi.z * cinv), nc - 1);
+    int k = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      int zz = cz + dz;
+      float sz = 0.f;
+      if (zz < 0) { zz += nc; sz = -L; } else if (zz >= nc) { zz -= nc; sz = L; }
+      for (int dy = -1; dy <= 1; ++dy) {
+        int yy = cy + dy;
+        float sy = 0.f;
+        if (yy < 0) { yy += nc; sy = -L; } else if (yy >= nc) { yy -= nc; sy = L; }
+        for (int dx = -1; dx <= 1; ++dx) {
+          int xx = cx + dx;
+          float sx = 0.f;
+          if (xx < 0) { xx += nc; sx = -L; } else if (xx >= nc) { xx -= nc; sx = L; }
+          const int c = (zz * nc + yy) * nc + xx;
+          const int j1 = m.start[c + 1];
+          for (int j = m.start[c]; j < j1; ++j) {
+            const float4 xj = m.x[j];
+            const float ddx = xi.x - (xj.x + sx), ddy = xi.y - (xj.y + sy), ddz = xi.z - (xj.z + sz);
+            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            if (j != s && r2 < rs2) {
+              if (k < maxnb) row[(size_t)(k >> 3) * wstride + (size_t)s * 8 + (k & 7)] = (uint16_t)j;
+              ++k;
+            }
+          }
+        }
+      }
+    }
+    if (k > maxnb) atomicOr(&sh->ctrl[CTRL_OVERFLOW], 1);
+    m.f[s].w = __int_as_float(min(k, maxnb));
+  }
+  __syncthreads();
+}
+
+// Forces on every atom (strided over the CTA) from the Verlet list, minimum image
+// on every entry; partial sums over the thread's atoms.  Out of line and fed
+// scalars, like force_pass.  Positions are read with ordinary (L1-cached) loads:
+// they were written by this CTA before the last barrier.
+template <bool EN, bool VIR, bool CNT>
+__device__ __noinline__ FSums big_force_pass(const float4* x, float4* f, const uint4* nl, int cap,
+                                             int n, float L, float invL, LJ c) {
+  float e = 0.f;
+  float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int np = 0;
+#pragma unroll 1
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const float4 xi = x[s];
+    const float cw = f[s].w;
+    const int cn = __float_as_int(cw);
+    const int nw = (cn + 7) >> 3;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    const uint4* p = nl + s;
+    uint4 q = nw > 0 ? __ldcg(p) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 1
+    for (int kb = 0; kb < nw; ++kb) {
+      const uint4 cur = q;
+      if (kb + 1 < nw) q = __ldcg(p + (size_t)(kb + 1) * cap);
+      const int left = cn - (kb << 3);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const unsigned wd = u < 2 ? cur.x : (u < 4 ? cur.y : (u < 6 ? cur.z : cur.w));
+        const int jj = (int)((wd >> (16 * (u & 1))) & 0xffffu);
+        const bool ok = u < left;
+        const float4 xj = x[ok ? jj : s];
+        const float dx = min_img(xi.x - xj.x, L, invL);
+        const float dy = min_img(xi.y - xj.y, L, invL);
+        const float dz = min_img(xi.z - xj.z, L, invL);
+        lj_pair<EN, VIR>(dx, dy, dz, ok, c, fx, fy, fz, e, w, np);
+      }
+    }
+    f[s] = make_float4(fx, fy, fz, cw);
+  }
+  FSums out = {EN ? e : 0.f, w[0], w[1], w[2], w[3], w[4], w[5], CNT ? np : 0};
+  return out;
+}
+
+struct BigCtx {
+  int n, nc, maxnb;
+  float L, invL, half_skin, rs2, cinv;
+};
+
+__device__ inline BigCtx make_big_ctx(const BoxDesc& bd, const RunParams& rp) {
+  BigCtx b;
+  b.n = bd.natoms;
+  b.nc = bd.nc_cell;
+  b.maxnb = bd.maxnb;
+  b.L = (float)bd.L;
+  b.invL = (float)(1.0 / bd.L);
+  b.half_skin = 0.5f * bd.skin;
+  const float rs = rp.rc + bd.skin;
+  b.rs2 = rs * rs;
+  b.cinv = (float)(bd.nc_cell / bd.L);
+  return b;
+}
+
+__device__ __forceinline__ FSums big_forces(const BigMem& m, const BigCtx& b, const LJ& c, bool en,
+                                            bool vir) {
+  if (vir) return big_force_pass<true, true, true>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+  if (en) return big_force_pass<true, false, false>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+  return big_force_pass<false, false, false>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+}
+
+// Maxwell velocities at T (Eq. 9): Philox keyed by the seed, counter = atom id,
+// FP64 Box-Muller, mean removed, exact rescale to T; same arithmetic as
+// init_velocities with the intermediate values kept in v instead of registers.
+static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, int n, unsigned long long seed,
+                                    double T, const RunParams& rp) {
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffull), k1 = (uint32_t)(seed >> 32);
+  const double sd = sqrt(T / rp.mass);
+  const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
+  float p[3] = {0.f, 0.f, 0.f};
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const uint32_t id = (uint32_t)__float_as_int(m.x[s].w);
+    uint32_t c[4] = {id, 0u, 0u, 0u};
+    philox4x32_10(c, k0, k1);
+    const double u0 = ((double)c[0] + 0.5) * two_m32, u1 = ((double)c[1] + 0.5) * two_m32;
+    const double u2 = ((double)c[2] + 0.5) * two_m32, u3 = ((double)c[3] + 0.5) * two_m32;
+    const double r01 = sqrt(-2.0 * log(u0)), r23 = sqrt(-2.0 * log(u2));
+    double s1, c1, s3, c3;
+    sincospi(2.0 * u1, &s1, &c1);
+    sincospi(2.0 * u3, &s3, &c3);
+    const float vx = (float)(sd * r01 * c1), vy = (float)(sd * r01 * s1), vz = (float)(sd * r23 * c3);
+    m.v[s] = make_float4(vx, vy, vz, 0.f);
+    p[0] += vx;
+    p[1] += vy;
+    p[2] += vz;
+  }
+  double ptot[3];
+  block_sum<3>(sh, p, ptot);
+  const float mx = (float)(ptot[0] / n), my = (float)(ptot[1] / n), mz = (float)(ptot[2] / n);
+  float ke[1] = {0.f};
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    float4 vi = m.v[s];
+    vi.x -= mx;
+    vi.y -= my;
+    vi.z -= mz;
+    m.v[s] = vi;
+    ke[0] += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+  }
+  double ketot[1];
+  block_sum<1>(sh, ke, ketot);
+  const double Tinst = rp.mass * ketot[0] / (3.0 * n - 3.0);
+  const float lam = (float)sqrt(T / Tinst);
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const float4 vi = m.v[s];
+    m.v[s] = make_float4(lam * vi.x, lam * vi.y, lam * vi.z, 0.f);
+  }
+  __syncthreads();
+}
+
+// first half kick with the pending thermostat factor, drift, displacement bound
+__device__ __forceinline__ bool big_kick_drift(const BigMem& m, const BigCtx& b,
+                                               const RunParams& rp, float lam) {
+  bool need = false;
+  for (int s = threadIdx.x; s < b.n; s += blockDim.x) {
+    const float4 fi = m.f[s];
+    float4 vi = m.v[s];
+    vi.x = fmaf(lam, vi.x, rp.hdtm * fi.x);
+    vi.y = fmaf(lam, vi.y, rp.hdtm * fi.y);
+    vi.z = fmaf(lam, vi.z, rp.hdtm * fi.z);
+    vi.w = fmaf(rp.dt, sqrtf(vi.x * vi.x + vi.y * vi.y + vi.z * vi.z), vi.w);
+    m.v[s] = vi;
+    float4 xi = m.x[s];
+    xi.x = fmaf(rp.dt, vi.x, xi.x);
+    xi.y = fmaf(rp.dt, vi.y, xi.y);
+    xi.z = fmaf(rp.dt, vi.z, xi.z);
+    m.x[s] = xi;
+    need = need || (vi.w > b.half_skin);
+  }
+  return need;
+}
+
+// One big box, start to finish (same schedule and accumulation as run_box).
+static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* sh, const BoxDesc& bd,
+                                     const RunParams& rp, mdeos_result* out) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = nt >> 5;
+  const BigCtx b = make_big_ctx(bd, rp);
+  const LJ lj = make_lj(rp);
+  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  const int n = b.n;
+  const double ndof = 3.0 * n - 3.0;
+  const double V = bd.L * bd.L * bd.L;
+  const bool temp_mode = (bd.flags & MDEOS_REQ_TEMPERATURE) != 0;
+  double* acc = sh->acc;
+  if (tid < 16) sh->ctrl[tid] = 0;
+  for (int k = tid; k < kAccDoubles; k += nt) acc[k] = 0.0;
+  for (int k = tid; k < kMaxSeBlocks; k += nt) sh->bcnt[k] = 0;
+  big_lattice(m, bd);
+  __syncthreads();
+  big_build(m, sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+  int builds = 1;
+  double E_cold;
+  {
+    const FSums r = big_forces(m, b, lj, true, false);
+    float q[1] = {r.e};
+    double et[1];
+    block_sum<1>(sh, q, et);
+    E_cold = 0.5 * et[0];
+  }
+  double* boxc = acc + ACC_BOX;
+  const double E_ref = (rp.ref_mode == MDEOS_REF_FIXED) ? n * bd.e_ref : E_cold;
+  const double E_tgt = n * bd.e + E_ref;
+  double Tk = temp_mode ? bd.e : 2.0 * (E_tgt - E_cold) / ndof;  // Eq. 9
+  int status = MDEOS_OK;
+  if (!(Tk > 0.0) || !isfinite(Tk)) status = MDEOS_EUNPHYS;
+  if (sh->ctrl[CTRL_OVERFLOW]) status = MDEOS_ENBR;
+  if (tid == 0) {
+    boxc[0] = E_cold;
+    boxc[1] = E_ref;
+    boxc[2] = E_tgt;
+    boxc[3] = Tk;
+  }
+  const int nseg = (bd.steps_equil > 0) ? rp.lift_iters : 0;
+  const int base = nseg > 0 ? bd.steps_equil / nseg : 0;
+  int seg = 0, seg_pos = 0;
+  int seg_len = (nseg == 1) ? bd.steps_equil : base;
+  int nsamp = max(1, (seg_len + 9) / 10);
+  const int total = bd.steps_equil + bd.steps_avg;
+  const int nb = rp.se_blocks;
+  if (status == MDEOS_OK) big_init_velocities(m, sh, n, bd.seed, Tk, rp);
+  const float invV_f = (float)(1.0 / V), inv3V_f = (float)(1.0 / (3.0 * V));
+  const float inv_ndof_f = (float)(1.0 / ndof);
+  float lam = 1.0f;
+  float Tk_f = (float)Tk;
+  for (int step = 0; step < total && status == MDEOS_OK; ++step) {
+    const bool avg = step >= bd.steps_equil;
+    const int s_avg = step - bd.steps_equil;
+    const bool seg_end = !avg && (seg_pos == seg_len - 1);
+    const bool esamp = !avg && !temp_mode && (seg_pos >= seg_len - nsamp);
+    const bool need = big_kick_drift(m, b, rp, lam);
+    if (__syncthreads_or(need)) {
+      big_wrap(m, n, b.L, b.invL);
+      __syncthreads();
+      big_build(m, sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+      ++builds;
+    }
+    {
+      const int st = sh->ctrl[CTRL_STATUS];
+      if (st != 0 || sh->ctrl[CTRL_OVERFLOW] != 0) {
+        status = st != 0 ? st : MDEOS_ENBR;
+        break;
+      }
+    }
+    const FSums r = big_forces(m, b, lj, avg || esamp, avg);
+    float ke = 0.f, kt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int cand = 0;
+    for (int s = tid; s < n; s += nt) {
+      const float4 fi = m.f[s];
+      float4 vi = m.v[s];
+      vi.x = fmaf(rp.hdtm, fi.x, vi.x);
+      vi.y = fmaf(rp.hdtm, fi.y, vi.y);
+      vi.z = fmaf(rp.hdtm, fi.z, vi.z);
+      m.v[s] = vi;
+      ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+      if (avg) {
+        kt[0] += vi.x * vi.x;
+        kt[1] += vi.y * vi.y;
+        kt[2] += vi.z * vi.z;
+        kt[3] += vi.x * vi.y;
+        kt[4] += vi.x * vi.z;
+        kt[5] += vi.y * vi.z;
+        cand += __float_as_int(fi.w);
+      }
+    }
+    {
+      float* red = sh->red + warp * kRedSlots;
+      const float s = warp_sum(0.5f * rp.mass_f * ke);
+      if (lane == 0) red[7] = s;
+      if (avg || esamp) {
+        const float se = warp_sum(0.5f * r.e);
+        if (lane == 0) red[6] = se;
+      }
+      if (avg) {
+        const float wv[6] = {r.w0, r.w1, r.w2, r.w3, r.w4, r.w5};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float sk = warp_sum(rp.mass_f * kt[k] + 0.5f * wv[k]);
+          if (lane == 0) red[k] = sk;
+        }
+        const float sp = warp_sum((float)r.np), sc = warp_sum((float)cand);
+        if (lane == 0) {
+          red[8] = sp;
+          red[9] = sc;
+        }
+      }
+    }
+    __syncthreads();
+    float ke_tot = 0.f;
+    for (int w = 0; w < nwarps; ++w) ke_tot += sh->red[w * kRedSlots + 7];
+    const float T_inst = 2.0f * ke_tot * inv_ndof_f;
+    if (warp == 0) {
+      float q = 0.f;
+      if (lane < kRedSlots)
+        for (int w = 0; w < nwarps; ++w) q += sh->red[w * kRedSlots + lane];
+      const float s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
+      const float s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
+      const float e6 = __shfl_sync(0xffffffffu, q, 6);
+      const float Ps = (s0 + s1 + s2) * inv3V_f;  // Eq. 11, mean normal stress
+      const float Ts = 2.0f * k7 * inv_ndof_f;
+      int slot = -1;
+      float val = 0.f;
+      if (avg) {
+        const int blk = (int)(((long long)s_avg * nb) / bd.steps_avg);
+        if (lane < 6) { slot = ACC_RUN + lane; val = q * invV_f; }
+        else if (lane < 10) { slot = ACC_RUN + lane; val = q; }
+        else if (lane == 10) { slot = ACC_RUN + 10; val = Ps; }
+        else if (lane == 11) { slot = ACC_RUN + 11; val = Ts; }
+        else if (lane == 12) { slot = ACC_BP + blk; val = Ps; sh->bcnt[blk] += 1; }
+        else if (lane == 13) { slot = ACC_BT + blk; val = Ts; }
+        if (lane == 10 && (!isfinite(Ps) || !isfinite(Ts) || !isfinite(e6)))
+          sh->ctrl[CTRL_STATUS] = MDEOS_EUNPHYS;
+      } else if (esamp && lane == 6) {
+        slot = ACC_RUN + 12;
+        val = q;
+      }
+      if (slot >= 0) acc[slot] += (double)val;
+      if (seg_end && lane == 6) {
+        const double Ebar = acc[ACC_RUN + 12] / nsamp;
+        const double Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) / ndof;  // Eq. 10
+        sh->bc[0] = Tn;
+        acc[ACC_RUN + 12] = 0.0;
+      }
+    }
+    if (!(T_inst > 0.f) || !isfinite(T_inst)) {
+      status = MDEOS_EUNPHYS;
+      break;
+    }
+    lam = 1.0f;
+    if (seg_end) {
+      __syncthreads();
+      const double Tn = sh->bc[0];
+      if (!(Tn > 0.0) || !isfinite(Tn)) {
+        status = MDEOS_EUNPHYS;
+        break;
+      }
+      if (tid == 0) boxc[3] = Tn;
+      Tk_f = (float)Tn;
+      lam = sqrtf(Tk_f / T_inst);
+      ++seg;
+      seg_pos = 0;
+      seg_len = (seg == nseg - 1) ? base + bd.steps_equil % nseg : base;
+      nsamp = max(1, (seg_len + 9) / 10);
+    } else if (!avg) {
+      if (rp.rescale_every_equil > 0 && (seg_pos + 1) % rp.rescale_every_equil == 0)
+        lam = sqrtf(Tk_f / T_inst);
+      ++seg_pos;
+    } else if (rp.rescale_every_avg > 0 && (s_avg + 1) % rp.rescale_every_avg == 0) {
+      lam = sqrtf(Tk_f / T_inst);
+    }
+  }
+  __syncthreads();
+  if (status == MDEOS_OK && sh->ctrl[CTRL_STATUS] != 0) status = sh->ctrl[CTRL_STATUS];
+  if (tid == 0) {
+    const double m_ = bd.steps_avg;
+    mdeos_result res;
+    for (int k = 0; k < 6; ++k) res.sigma[k] = acc[ACC_RUN + k] / m_;
+    res.P = acc[ACC_RUN + 10] / m_;
+    res.T = acc[ACC_RUN + 11] / m_;
+    res.epot = acc[ACC_RUN + 6] / m_ / n;
+    res.ekin = acc[ACC_RUN + 7] / m_ / n;
+    res.e_achieved = (acc[ACC_RUN + 7] / m_ + acc[ACC_RUN + 6] / m_ - boxc[1]) / n;
+    double mP = 0.0, mT = 0.0;
+    for (int k = 0; k < nb; ++k) {
+      const double c = sh->bcnt[k] > 0 ? (double)sh->bcnt[k] : 1.0;
+      acc[ACC_BP + k] /= c;
+      acc[ACC_BT + k] /= c;
+      mP += acc[ACC_BP + k];
+      mT += acc[ACC_BT + k];
+    }
+    mP /= nb;
+    mT /= nb;
+    double vP = 0.0, vT = 0.0;
+    for (int k = 0; k < nb; ++k) {
+      vP += (acc[ACC_BP + k] - mP) * (acc[ACC_BP + k] - mP);
+      vT += (acc[ACC_BT + k] - mT) * (acc[ACC_BT + k] - mT);
+    }
+    res.P_se = sqrt(vP / (nb - 1) / nb);
+    res.T_se = sqrt(vT / (nb - 1) / nb);
+    res.T_target = boxc[3];
+    res.e_cold = boxc[0] / n;
+    res.L = bd.L;
+    res.pairs_per_step = acc[ACC_RUN + 8] / m_;
+    res.cand_per_step = acc[ACC_RUN + 9] / m_;
+    res.element_id = bd.element_id;
+    res.natoms = n;
+    res.status = status;
+    res.nlist_builds = builds;
+    res.path = PATH_NLIST;
+    res.warm = 0;
+    res.reserved0 = 0;
+    if (status != MDEOS_OK) {
+      res.P = res.T = res.epot = res.ekin = res.e_achieved = res.P_se = res.T_se = 0.0;
+      for (int k = 0; k < 6; ++k) res.sigma[k] = 0.0;
+    }
+    *out = res;
+  }
+  __syncthreads();
+}
+
+}  // namespace mdeos

@@ -1,6 +1,6 @@
 // Single-box kernels for parity tests.  Each runs one box in one CTA (one
 // group of 32 warps) through the same device functions as the batch kernel.
-#include "mdeos_device.cuh"
+#include "mdeos_big.cuh"
 
 namespace mdeos {
 
@@ -259,6 +259,136 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     case 2: debug_md_path<2>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc); break;
     default: debug_md_path<4>(g, bd, rp, x4, v4, steps, T, every, ep, ek, cyc); break;
   }
+}
+
+// ---------------------------------------------------------------------------
+// boxes above the shared-memory limit (global-memory state, one CTA)
+
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    debug_big_forces_kernel(BoxDesc bd, RunParams rp, unsigned char* scratch, const float4* x4,
+                            float4* f4, double* ew, long long* pairs) {
+  __shared__ BigShared sh;
+  const BigCtx b = make_big_ctx(bd, rp);
+  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  if (threadIdx.x < 16) sh.ctrl[threadIdx.x] = 0;
+  for (int s = threadIdx.x; s < b.n; s += blockDim.x) {
+    const float4 xi = x4[s];
+    m.x[s] = make_float4(xi.x, xi.y, xi.z, __int_as_float(s));
+    m.v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  big_wrap(m, b.n, b.L, b.invL);
+  __syncthreads();
+  big_build(m, &sh, b.n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+  // forces use the positions as given (the list came from the wrapped ones)
+  for (int s = threadIdx.x; s < b.n; s += blockDim.x) {
+    const float4 xo = m.x[s];
+    const float4 xi = x4[__float_as_int(xo.w)];
+    m.x[s] = make_float4(xi.x, xi.y, xi.z, xo.w);
+  }
+  __syncthreads();
+  const FSums r = big_force_pass<true, true, true>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL,
+                                                   make_lj(rp));
+  for (int s = threadIdx.x; s < b.n; s += blockDim.x) f4[__float_as_int(m.x[s].w)] = m.f[s];
+  float q[8] = {0.5f * r.e,  0.5f * r.w0, 0.5f * r.w1, 0.5f * r.w2,
+                0.5f * r.w3, 0.5f * r.w4, 0.5f * r.w5, (float)r.np};
+  double out[8];
+  block_sum<8>(&sh, q, out);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 7; ++k) ew[k] = out[k];
+    if (pairs) pairs[0] = (long long)llrint(out[7]);
+    if (sh.ctrl[CTRL_OVERFLOW]) ew[0] = __longlong_as_double(0x7ff8000000000001ll);
+  }
+}
+
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    debug_big_md_kernel(BoxDesc bd, RunParams rp, unsigned char* scratch, float4* x4, float4* v4,
+                        int steps, double T_target, int rescale_every, double* epot,
+                        double* ekin, long long* cyc) {
+  __shared__ BigShared sh;
+  const BigCtx b = make_big_ctx(bd, rp);
+  const LJ lj = make_lj(rp);
+  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  const int n = b.n;
+  const double ndof = 3.0 * n - 3.0;
+  long long nbuild = 0;
+  if (threadIdx.x < 16) sh.ctrl[threadIdx.x] = 0;
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const float4 xi = x4[s], vi = v4[s];
+    m.x[s] = make_float4(xi.x, xi.y, xi.z, __int_as_float(s));
+    m.v[s] = make_float4(vi.x, vi.y, vi.z, 0.f);
+  }
+  __syncthreads();
+  big_wrap(m, n, b.L, b.invL);
+  __syncthreads();
+  big_build(m, &sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+  big_forces(m, b, lj, false, false);
+  __syncthreads();
+  for (int st = 0; st < steps; ++st) {
+    const bool need = big_kick_drift(m, b, rp, 1.0f);
+    if (__syncthreads_or(need)) {
+      big_wrap(m, n, b.L, b.invL);
+      __syncthreads();
+      big_build(m, &sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+      ++nbuild;
+    }
+    const FSums r = big_forces(m, b, lj, true, false);
+    float ke = 0.f;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+      const float4 fi = m.f[s];
+      float4 vi = m.v[s];
+      vi.x = fmaf(rp.hdtm, fi.x, vi.x);
+      vi.y = fmaf(rp.hdtm, fi.y, vi.y);
+      vi.z = fmaf(rp.hdtm, fi.z, vi.z);
+      m.v[s] = vi;
+      ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+    }
+    float q[2] = {0.5f * r.e, 0.5f * rp.mass_f * ke};
+    double tot[2];
+    block_sum<2>(&sh, q, tot);
+    if (threadIdx.x == 0) {
+      if (epot) epot[st] = tot[0];
+      if (ekin) ekin[st] = tot[1];
+    }
+    if (rescale_every > 0 && (st + 1) % rescale_every == 0) {
+      const float lam = (float)sqrt(T_target / (2.0 * tot[1] / ndof));
+      for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        float4 vi = m.v[s];
+        vi.x *= lam;
+        vi.y *= lam;
+        vi.z *= lam;
+        m.v[s] = vi;
+      }
+    }
+    __syncthreads();
+  }
+  big_wrap(m, n, b.L, b.invL);
+  __syncthreads();
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const float4 xi = m.x[s], vi = m.v[s];
+    const int id = __float_as_int(xi.w);
+    x4[id] = make_float4(xi.x, xi.y, xi.z, 0.f);
+    v4[id] = make_float4(vi.x, vi.y, vi.z, 0.f);
+  }
+  if (cyc && threadIdx.x == 0) {
+    for (int k = 0; k < 11; ++k) cyc[k] = 0;
+    cyc[4] = nbuild;
+  }
+}
+
+cudaError_t launch_debug_big_forces(const BoxDesc& bd, const RunParams& rp, unsigned char* scratch,
+                                    const float4* x4, float4* f4, double* ew, long long* pairs,
+                                    cudaStream_t st) {
+  debug_big_forces_kernel<<<1, kCtaThreads, 0, st>>>(bd, rp, scratch, x4, f4, ew, pairs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_big_md(const BoxDesc& bd, const RunParams& rp, unsigned char* scratch,
+                                float4* x4, float4* v4, int steps, double T, int every, double* ep,
+                                double* ek, long long* cyc, cudaStream_t st) {
+  debug_big_md_kernel<<<1, kCtaThreads, 0, st>>>(bd, rp, scratch, x4, v4, steps, T, every, ep, ek,
+                                                 cyc);
+  return cudaGetLastError();
 }
 
 cudaError_t set_debug_attributes(int max_smem) {

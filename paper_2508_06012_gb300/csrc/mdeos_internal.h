@@ -23,6 +23,22 @@ constexpr int kMaxAtoms = 4096;       // 1024 threads x 4 atoms per thread
 constexpr int kMaxSeBlocks = 32;
 constexpr int kMaxCells = 1024;       // cell-list cells per box
 constexpr int kRedSlots = 10;         // reduction quantities per warp
+// boxes above kMaxAtoms run one per CTA with their state in global memory
+constexpr int kMaxAtomsBig = 32768;   // uint16 neighbour indices
+constexpr int kMaxCellsBig = 32768;   // cells of the list build (<= 32 per axis)
+constexpr int kBigSharedBytes = 4096; // shared memory of a big-box CTA (reductions only)
+
+// per-CTA global scratch of a big box (layout in mdeos_big.cuh)
+__host__ __device__ inline int big_cap(int n) { return (n + 31) & ~31; }
+
+__host__ __device__ inline size_t big_cells_bytes(int ncell) {
+  return ((size_t)8 * (ncell + 1) + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t big_scratch_bytes(int n, int ncell, int maxnb) {
+  const size_t cap = (size_t)big_cap(n);
+  return 80 * cap + big_cells_bytes(ncell) + (size_t)(maxnb / 8) * cap * 16;
+}
 
 // Force-field and integrator constants (FP32 where the pair loop uses them).
 struct RunParams {
@@ -67,6 +83,7 @@ struct WorkItem {
   int smem_stride;          // bytes of dynamic shared memory per box group
   int ncell_cap;            // cells reserved per group
   int nl_stride;            // uint16 entries of neighbour scratch per group
+  int big;                  // 1: one box above the shared-memory limit (global-memory state)
   int box[kMaxBoxesPerItem];
 };
 

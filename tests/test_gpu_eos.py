@@ -138,7 +138,7 @@ def test_edge_cases_and_statuses(m, eng):
     reqs = [
         dict(base),                                  # ok
         dict(base, natoms=1),                        # too few atoms
-        dict(base, natoms=5000),                     # beyond the shared-memory path
+        dict(base, natoms=40000),                    # beyond uint16 atom indices
         dict(base, rho=-1.0),                        # bad density
         dict(base, steps_avg=5),                     # fewer than se_blocks
         dict(base, steps_equil=1),                   # fewer than lift_iters segments
