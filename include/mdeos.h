@@ -311,6 +311,69 @@ mdeos_status mdeos_hydro_eos_results(mdeos_hydro* hy, mdeos_result* out);
 
 mdeos_status mdeos_hydro_destroy(mdeos_hydro* hy);
 
+/* ---- serving loop (continuous batching) --------------------------------
+ * The paper has no serving layer (each FEM element waits for its own MD run);
+ * this is the many-client form of the same evaluation.  One persistent kernel
+ * grid (one CTA per SM) claims work items one at a time from a queue that the
+ * server's scheduler thread keeps appending to: arriving requests are planned
+ * into items (boxes of one size class, LPT order within an admission step) and
+ * published into host-mapped rings; every SM takes the next item as soon as it
+ * finishes one, and each request is reported as soon as its box is done (result
+ * and ready flag in host-mapped memory).  An idle grid exits after idle_ms and is
+ * relaunched when work arrives.  Warm starts are not used here. */
+typedef struct {
+  int32_t max_inflight;     /* requests admitted to the GPU and not finished, default 4096 */
+  int32_t max_batch;        /* requests planned together per admission step, default 2048 */
+  double max_wait_s;        /* waiting longer than this: shed (MDEOS_ECANCELLED); 0 = never */
+  int32_t max_queue;        /* waiting requests beyond this are shed on arrival; 0 = no cap */
+  int32_t idle_ms;          /* an idle kernel exits after this long, default 20 */
+  size_t hbm_budget_bytes;  /* device memory the server may hold (per-SM scratch for the
+                               largest box, 32768 atoms); creation fails above it; 0 = no cap */
+} mdeos_serve_config;
+
+/* One finished request.  Times are seconds on the server clock (mdeos_serve_clock):
+ * arrival = enqueue, launch = published to the GPU queue, done = when the server saw
+ * its result.  result.status: the box's status, MDEOS_ECANCELLED if shed,
+ * MDEOS_ENOMEM if its box needs more per-SM scratch than the server holds,
+ * MDEOS_EINVAL if rejected by the planner, MDEOS_ECUDA if the kernel failed. */
+typedef struct {
+  uint64_t id;
+  double t_arrival, t_launch, t_done;
+  mdeos_result result;
+} mdeos_served;
+
+typedef struct mdeos_server mdeos_server;
+
+/* Defaults: 4096 in flight, admission steps of up to 2048, no shedding, idle exit
+ * after 20 ms, no budget. */
+void mdeos_serve_config_default(mdeos_serve_config* cfg);
+
+/* Start a server on handle h (caller-owned, must outlive the server); cfg copied.
+ * Errors: MDEOS_EINVAL, MDEOS_ENOMEM (budget below the scratch), MDEOS_ECUDA. */
+mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_config* cfg,
+                                mdeos_server** out);
+
+/* Seconds since mdeos_serve_create (steady clock). */
+double mdeos_serve_clock(const mdeos_server* s);
+
+/* Queue n host requests (copied); ids (host uint64[n], may be NULL) receives their
+ * ids.  Thread-safe.  Arrivals beyond max_queue are shed at once. */
+mdeos_status mdeos_serve_enqueue(mdeos_server* s, const mdeos_request* reqs, int32_t n,
+                                 uint64_t* ids);
+
+/* Move up to max finished requests into out (host, caller-owned); *n_out = count.
+ * Non-blocking, thread-safe; completion order. */
+mdeos_status mdeos_serve_completed(mdeos_server* s, mdeos_served* out, int32_t max,
+                                   int32_t* n_out);
+
+/* counts (host int64[7], may be NULL): enqueued, admitted, finished, shed,
+ * kernel launches, waiting now, CUDA failures; bytes (host size_t[2], may be NULL):
+ * device bytes held by the server and the peak number of requests in flight. */
+mdeos_status mdeos_serve_stats(mdeos_server* s, long long* counts, size_t* bytes);
+
+/* Stop: waiting requests are shed, in-flight launches finish; then release. */
+mdeos_status mdeos_serve_destroy(mdeos_server* s);
+
 /* ---- single-box kernels exposed for parity tests ----------------------
  * These run one box through the same device code as the batch path. */
 

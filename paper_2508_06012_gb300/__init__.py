@@ -32,6 +32,8 @@ EXPORTED = [
     "mdeos_debug_md", "mdeos_submit_noalloc", "mdeos_warm_export", "mdeos_warm_import",
     "mdeos_warm_reset", "mdeos_hydro_config_default", "mdeos_hydro_create", "mdeos_hydro_step",
     "mdeos_hydro_state", "mdeos_hydro_eos_results", "mdeos_hydro_destroy",
+    "mdeos_serve_config_default", "mdeos_serve_create", "mdeos_serve_clock",
+    "mdeos_serve_enqueue", "mdeos_serve_completed", "mdeos_serve_stats", "mdeos_serve_destroy",
 ]
 
 
@@ -86,6 +88,14 @@ class mdeos_hydro_config(ctypes.Structure):
     ]
 
 
+class mdeos_serve_config(ctypes.Structure):
+    _fields_ = [
+        ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+        ("max_wait_s", ctypes.c_double), ("max_queue", ctypes.c_int32),
+        ("idle_ms", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
+    ]
+
+
 RESULT_DTYPE = np.dtype([
     ("P", "f8"), ("T", "f8"), ("sigma", "f8", (6,)), ("epot", "f8"), ("ekin", "f8"),
     ("e_achieved", "f8"), ("P_se", "f8"), ("T_se", "f8"), ("T_target", "f8"),
@@ -97,6 +107,8 @@ REQUEST_DTYPE = np.dtype([
     ("rho", "f8"), ("e", "f8"), ("e_ref", "f8"), ("natoms", "i4"), ("steps_equil", "i4"),
     ("steps_avg", "i4"), ("flags", "u4"), ("seed", "u8"), ("element_id", "u8"),
 ])
+SERVED_DTYPE = np.dtype([("id", "u8"), ("t_arrival", "f8"), ("t_launch", "f8"),
+                         ("t_done", "f8"), ("result", RESULT_DTYPE)])
 assert RESULT_DTYPE.itemsize == ctypes.sizeof(mdeos_result)
 assert REQUEST_DTYPE.itemsize == ctypes.sizeof(mdeos_request)
 
@@ -158,10 +170,20 @@ def lib():
         L.mdeos_hydro_state.argtypes = [vp] + [vp] * 8
         L.mdeos_hydro_eos_results.argtypes = [vp, vp]
         L.mdeos_hydro_destroy.argtypes = [vp]
+        L.mdeos_serve_config_default.argtypes = [P(mdeos_serve_config)]
+        L.mdeos_serve_config_default.restype = None
+        L.mdeos_serve_create.argtypes = [vp, P(mdeos_serve_config), P(vp)]
+        L.mdeos_serve_clock.argtypes = [vp]
+        L.mdeos_serve_clock.restype = d
+        L.mdeos_serve_enqueue.argtypes = [vp, vp, i32, vp]
+        L.mdeos_serve_completed.argtypes = [vp, vp, i32, P(i32)]
+        L.mdeos_serve_stats.argtypes = [vp, vp, vp]
+        L.mdeos_serve_destroy.argtypes = [vp]
         for name in EXPORTED:
             fn = getattr(L, name)
             if name not in ("mdeos_config_default", "mdeos_last_error",
-                            "mdeos_batch_device_results", "mdeos_hydro_config_default"):
+                            "mdeos_batch_device_results", "mdeos_hydro_config_default",
+                            "mdeos_serve_config_default", "mdeos_serve_clock"):
                 fn.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -404,6 +426,76 @@ class Hydro:
         if self.hy:
             lib().mdeos_hydro_destroy(self.hy)
             self.hy = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def mdeos_serve_config_default(**over) -> mdeos_serve_config:
+    c = mdeos_serve_config()
+    lib().mdeos_serve_config_default(ctypes.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+class Server:
+    """Continuous-batching server on a handle (mdeos_serve_*); the handle must outlive it."""
+
+    def __init__(self, h, cfg: mdeos_serve_config | None = None, **over):
+        self.cfg = cfg or mdeos_serve_config_default(**over)
+        self.s = ctypes.c_void_p()
+        _check(lib().mdeos_serve_create(h, ctypes.byref(self.cfg), ctypes.byref(self.s)))
+
+    def clock(self) -> float:
+        return lib().mdeos_serve_clock(self.s)
+
+    def enqueue(self, reqs) -> np.ndarray:
+        arr = as_requests(reqs)
+        ids = np.zeros(len(arr), dtype=np.uint64)
+        _check(lib().mdeos_serve_enqueue(self.s, arr.ctypes.data_as(ctypes.c_void_p), len(arr),
+                                         ids.ctypes.data_as(ctypes.c_void_p)))
+        return ids
+
+    def completed(self, max_n: int = 4096) -> np.ndarray:
+        out = np.empty(max_n, dtype=SERVED_DTYPE)
+        k = ctypes.c_int32()
+        _check(lib().mdeos_serve_completed(self.s, out.ctypes.data_as(ctypes.c_void_p), max_n,
+                                           ctypes.byref(k)))
+        return out[:k.value]
+
+    def stats(self) -> dict:
+        c = np.zeros(7, dtype=np.int64)
+        b = np.zeros(2, dtype=np.uint64)
+        _check(lib().mdeos_serve_stats(self.s, c.ctypes.data_as(ctypes.c_void_p),
+                                       b.ctypes.data_as(ctypes.c_void_p)))
+        keys = ("enqueued", "admitted", "finished", "shed", "launches", "waiting", "cuda_errors")
+        d = {k: int(v) for k, v in zip(keys, c)}
+        d["device_bytes"], d["peak_inflight"] = int(b[0]), int(b[1])
+        return d
+
+    def wait_all(self, n_expected: int, timeout_s: float = 600.0) -> np.ndarray:
+        """Collect completions until n_expected have arrived (or the timeout)."""
+        import time
+        got = []
+        t0 = time.time()
+        total = 0
+        while total < n_expected and time.time() - t0 < timeout_s:
+            c = self.completed()
+            if len(c):
+                got.append(c)
+                total += len(c)
+            else:
+                time.sleep(0.0005)
+        return np.concatenate(got) if got else np.zeros(0, dtype=SERVED_DTYPE)
+
+    def close(self):
+        if self.s:
+            lib().mdeos_serve_destroy(self.s)
+            self.s = None
 
     def __enter__(self):
         return self

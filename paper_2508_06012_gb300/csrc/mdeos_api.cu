@@ -16,13 +16,14 @@
 #include <unordered_set>
 #include <vector>
 
-#include "mdeos_internal.h"
+#include "mdeos_host.h"
 
 namespace mdeos {
 cudaError_t set_batch_attributes(int max_smem);
 cudaError_t launch_eos_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int* counter,
                              mdeos_result* results, uint16_t* nl, long long nl_elems_per_cta,
-                             const RunParams& rp, int grid, int smem, cudaStream_t st);
+                             const RunParams& rp, int grid, int smem, cudaStream_t st,
+                             int* ready);
 cudaError_t set_debug_attributes(int max_smem);
 cudaError_t launch_debug_lift(const BoxDesc& bd, const RunParams& rp, double T, int apt,
                               int ncell_cap, int smem, float4* x4, float4* v4, double* e_out,
@@ -524,7 +525,7 @@ extern "C" mdeos_status mdeos_create(const mdeos_config* cfg, mdeos_handle** out
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
   cudaDeviceGetAttribute(&h->smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  h->smem_max -= 1024;  // static shared memory of the kernels
+  h->smem_max -= 2048;  // static shared memory of the kernels (the serving kernel's is ~1.3 KB)
   e = set_batch_attributes(h->smem_max);
   if (e == cudaSuccess) e = set_debug_attributes(h->smem_max);
   if (e != cudaSuccess) {
@@ -683,7 +684,7 @@ extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs,
     CK(cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream));
     e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni, (int*)(d + off_cnt),
                          (mdeos_result*)(d + off_res), h->d_nl, plan.nl_per_cta, h->rp, plan.grid,
-                         plan.smem, h->stream);
+                         plan.smem, h->stream, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "eos_batch_kernel launch");
     h->launches += 1;
     CK(cudaMemcpyAsync(t.h_out.p, d + off_res, (size_t)n * sizeof(mdeos_result),
@@ -804,7 +805,7 @@ extern "C" mdeos_status mdeos_batch_create(mdeos_handle* h, const mdeos_request*
   cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
   if (ni > 0)
     launch_eos_batch(b->d_boxes, b->d_items, (int)ni, b->d_counter, b->d_results, b->d_nl,
-                     p.nl_per_cta, h->rp, p.grid, p.smem, cs);
+                     p.nl_per_cta, h->rp, p.grid, p.smem, cs, nullptr);
   e = cudaStreamEndCapture(cs, &b->graph);
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) {
@@ -1004,13 +1005,35 @@ mdeos_status eval_into_device(mdeos_handle* h, const mdeos_request* reqs, int n,
   CK(cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream));
   cudaError_t e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni,
                                    (int*)(d + off_cnt), d_results, h->d_nl, plan.nl_per_cta, h->rp,
-                                   plan.grid, plan.smem, h->stream);
+                                   plan.grid, plan.smem, h->stream, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "eos_batch_kernel launch");
   h->launches += 1;
   return MDEOS_OK;
 }
 
 void count_launch(mdeos_handle* h, long long k) { h->launches += k; }
+
+const RunParams& handle_run_params(const mdeos_handle* h) { return h->rp; }
+int handle_sm_count(const mdeos_handle* h) { return h->nsm; }
+int handle_smem_max(const mdeos_handle* h) { return h->smem_max; }
+
+void planning_result_of(mdeos_result& r, int status, const mdeos_request& q) {
+  planning_result(r, status, q);
+}
+
+// Planning with the handle's configuration and device limits (no warm store).
+mdeos_status plan_requests(const mdeos_handle* h, const mdeos_request* reqs, int n, PlanOut& out) {
+  Plan plan;
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan);
+  if (st != MDEOS_OK) return st;
+  out.boxes.swap(plan.boxes);
+  out.items.swap(plan.items);
+  out.status.swap(plan.status);
+  out.smem = plan.smem;
+  out.grid = plan.grid;
+  out.nl_per_cta = plan.nl_per_cta;
+  return MDEOS_OK;
+}
 
 }  // namespace mdeos
 

@@ -17,17 +17,9 @@
 #include <string>
 #include <vector>
 
-#include "mdeos_internal.h"
+#include "mdeos_host.h"
 
 namespace mdeos {
-
-mdeos_status set_error(mdeos_status st, const std::string& msg);
-mdeos_status eval_into_device(mdeos_handle* h, const mdeos_request* reqs, int n,
-                              mdeos_result* d_results);
-cudaStream_t handle_stream(const mdeos_handle* h);
-int handle_device(const mdeos_handle* h);
-const mdeos_config& handle_config(const mdeos_handle* h);
-void count_launch(mdeos_handle* h, long long k);
 
 enum { HY_ERR_STATE = 1, HY_ERR_EOS = 2, HY_ERR_DT = 3 };
 

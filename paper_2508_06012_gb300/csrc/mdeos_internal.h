@@ -87,6 +87,25 @@ struct WorkItem {
   int box[kMaxBoxesPerItem];
 };
 
+// Work queue of the serving kernel: rings in host-mapped memory written by the
+// host scheduler, a claim counter in device memory.  Ring slots are counter % cap.
+struct ServeQueue {
+  const BoxDesc* boxes;         // host-mapped, cap_boxes entries (out_index = ring slot)
+  const WorkItem* items;        // host-mapped, cap_items entries (box[] = box ring slots)
+  const unsigned* tail;         // host-mapped: items published so far (monotonic)
+  const int* stop;              // host-mapped: 1 = exit at the next claim
+  const int* linger;            // host-mapped: 1 = traffic is active, idle CTAs stay
+  unsigned* head;               // device: items claimed so far (monotonic)
+  int* slot_busy;               // device, nslots: per-SM scratch slots in use
+  int* alive;                   // host-mapped, nslots: 1 while a CTA holds the slot
+  int nslots;
+  mdeos_result* results;        // host-mapped, cap_boxes entries
+  int* ready;                   // host-mapped, cap_boxes flags
+  unsigned cap_items, cap_boxes;
+  long long idle_ns;            // a CTA with no work for this long exits (linger == 0)
+  long long max_idle_ns;        // ... and after this long in any case
+};
+
 constexpr int kAccDoubles = 2 * kMaxSeBlocks + 24;  // block sums of P and T, running sums, box constants
 
 // Shared-memory layout of one box group (host planner and device agree):

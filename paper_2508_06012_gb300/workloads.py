@@ -79,3 +79,23 @@ def random_boxes(seed: int, nbox: int, nmin: int, nmax: int, rho=(0.3, 1.2), T=(
     return [dict(rho=float(r[k]), T=float(t[k]), natoms=int(n[k]), steps_equil=steps_equil,
                  steps_avg=steps_avg, seed=box_seed(seed, k), element_id=k)
             for k in range(nbox)]
+
+
+def config4(base_seed: int = 20250809, nreq: int = 1000, steps_equil: int = 1000,
+            steps_avg: int = 1000):
+    """EOS serving stream: atom counts log-uniform on [256, 32000], rho* ~ U[0.3, 1.2],
+    T* log-uniform on [0.7, 3.0] (the 2000-step schedule of config 2)."""
+    rng = np.random.default_rng(base_seed)
+    n = np.exp(rng.uniform(np.log(256.0), np.log(32000.0), nreq)).astype(np.int64)
+    rho = rng.uniform(0.3, 1.2, nreq)
+    T = np.exp(rng.uniform(np.log(0.7), np.log(3.0), nreq))
+    return [dict(rho=float(rho[k]), T=float(T[k]), natoms=int(n[k]), steps_equil=steps_equil,
+                 steps_avg=steps_avg, seed=box_seed(base_seed, k), element_id=0)
+            for k in range(nreq)]
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson stream of the given mean rate."""
+    rng = np.random.default_rng(seed)
+    n = rng.poisson(rate * duration)
+    return np.sort(rng.uniform(0.0, duration, n))

@@ -52,18 +52,24 @@ def _fp32_force_bound(x, L, F):
     """Per-atom bound on the FP32 force error.  In a box of side L a position
     difference across the periodic boundary is rounded at the scale of L
     (2^-24 L per component); each pair force moves by |df/dr| times that.  Bound:
-    1e-4 max(|F_i|, F_rms) + 4 * 2^-24 L * sum_j |df_ij/dr|."""
+    1e-4 max(|F_i|, F_rms) + 4 * 2^-24 L * sum_j |df_ij/dr| + |f(rc)| per pair of
+    atom i within rounding of the cutoff."""
     from scipy.spatial import cKDTree
     t = cKDTree(np.mod(x, L), boxsize=L)
-    pr = t.query_pairs(RC, output_type="ndarray")
+    pr = t.query_pairs(RC * (1 + 4e-6), output_type="ndarray")
     d = x[pr[:, 0]] - x[pr[:, 1]]
     d -= L * np.round(d / L)
     r = np.sqrt((d ** 2).sum(axis=1))
     g = np.abs(24.0 * (-26.0 * r ** -14 + 7.0 * r ** -8))
     stiff = np.bincount(pr[:, 0], g, minlength=len(x)) + np.bincount(pr[:, 1], g, minlength=len(x))
+    # a pair within FP32 rounding of the cutoff may be in or out on either side:
+    # the truncated force jumps by |f(rc)| there
+    band = np.abs(r - RC) < 4e-6 * RC
+    amb = np.bincount(pr[band, 0], minlength=len(x)) + np.bincount(pr[band, 1], minlength=len(x))
+    f_rc = abs(24.0 * (2.0 * RC ** -13 - RC ** -7))
     fn = np.linalg.norm(F, axis=1)
     frms = np.sqrt((fn ** 2).mean())
-    return 1e-4 * np.maximum(fn, frms) + 4.0 * 2.0 ** -24 * L * stiff
+    return 1e-4 * np.maximum(fn, frms) + 4.0 * 2.0 ** -24 * L * stiff + 1.01 * f_rc * amb
 
 
 def _ordered_pairs(x, L, r):
