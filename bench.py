@@ -551,6 +551,137 @@ def serving(args):
     print(json.dumps(line), flush=True)
 
 
+SURROGATE = ("surrogate-gated EOS: ensemble of 4 MLPs 2-128-128-128-2 (BF16 weights, FP32 "
+             "accumulation, tensor-core layers) trained on 1e5 MD samples of the config-2 "
+             "distribution; requests above the disagreement threshold fall back to 4000-atom "
+             "MD; threshold tuned to 1% pressure error against 4000-atom MD")
+
+
+def surrogate(args):
+    """Config 5: train the ensemble on MD answers, tune the gate, compare with MD-only."""
+    import torch
+
+    import paper_2508_06012_gb300 as m
+    from paper_2508_06012_gb300 import workloads as w
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    m.build()
+    h = m.mdeos_create(m.mdeos_config_default(device=local))
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+    clocks = ClockSampler(gpu_idx)
+    clocks.start()
+    out = {}
+    # 1. training data: MD answers over the config-2 distribution
+    reqs = gpu_requests(m, w.config2(base_seed=777, nbox=args.train_n))
+    t0 = time.perf_counter()
+    res = m.mdeos_poll(h, m.mdeos_submit(h, reqs), len(reqs), -1)
+    out["md_training_data_s"] = time.perf_counter() - t0
+    # input = the energy each run actually sampled (e_achieved): a small box's lifting
+    # lands within ~T sqrt(3 / 2N) of the requested e
+    ok = res["status"] == 0
+    x = np.stack([np.array([r["rho"] for r in reqs]), res["e_achieved"]], axis=1)[ok]
+    y = np.stack([res["P"], res["T"]], axis=1)[ok]
+    out["training_samples"] = int(ok.sum())
+
+    # 2. reference: 4000-atom MD on validation and test queries of the same distribution
+    def queries(seed, n):
+        return [dict(rho=q["rho"], e=m.e_from_temperature(q["T"], 4000), natoms=4000,
+                     steps_equil=1000, steps_avg=1000, seed=q["seed"])
+                for q in w.config2(base_seed=seed, nbox=n)]
+    val = queries(778, args.val_n)
+    test = queries(779, args.test_n)
+    rv = m.mdeos_poll(h, m.mdeos_submit(h, val), len(val), -1)
+    # 3. training
+    sg = m.Surrogate(h, 4, 4096, seed=11)
+    t0 = time.perf_counter()
+    losses = sg.train(x, y, epochs=args.epochs, batch=1024, lr=2e-3, seed=5)
+    losses2 = sg.train(x, y, epochs=args.epochs, batch=1024, lr=3e-4, seed=6, set_norm=False)
+    out["train_s"] = time.perf_counter() - t0
+    out["train_epochs"] = 2 * args.epochs
+    out["train_loss_first_mid_last"] = [float(losses[0]), float(losses[-1]), float(losses2[-1])]
+    # 4. gate threshold: the largest disagreement level whose accepted validation queries
+    # have RMS pressure error <= 1% of max(|P_MD|, 1)
+    okv = rv["status"] == 0
+    xv = np.array([[q["rho"], q["e"]] for q in val])[okv]
+    mv, sv = sg.predict(xv)
+    pv = rv["P"][okv]
+    err = np.abs(mv[:, 0] - pv) / np.maximum(np.abs(pv), 1.0)
+    dis = sv[:, 0] / np.maximum(np.abs(mv[:, 0]), 1.0)
+    order = np.argsort(dis)
+    rms = np.sqrt(np.cumsum(err[order] ** 2) / np.arange(1, len(order) + 1))
+    def level(target):
+        good = np.flatnonzero(rms <= target)
+        k = int(good[-1]) if len(good) else -1
+        return k, (float(dis[order][k]) if k >= 0 else 0.0)
+    tradeoff = {}
+    for target in (0.01, 0.02, 0.03, 0.05):
+        k, t_ = level(target)
+        tradeoff[f"{target:.2f}"] = {"threshold_rel_sd": t_, "coverage_val": (k + 1) / len(order)}
+    k, thr = level(0.01)
+    out["gate"] = {"target_rms_rel_err": 0.01, "threshold_rel_sd": thr,
+                   "coverage_val": (k + 1) / len(order),
+                   "rms_err_accepted_val": float(rms[k]) if k >= 0 else None,
+                   "rms_err_all_val": float(np.sqrt(np.mean(err ** 2))),
+                   "median_rel_err_val": float(np.median(err)),
+                   "md4000_P_se_median": float(np.median(rv["P_se"][okv])),
+                   "coverage_by_target": tradeoff}
+    # 5. gated evaluation vs MD-only on the test queries (both at 4000 atoms)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rg, used = sg.gated_eval(test, thr, md_natoms=4000)
+    t_gated = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rm = m.mdeos_poll(h, m.mdeos_submit(h, test), len(test), -1)
+    t_md = time.perf_counter() - t0
+    acc = (rm["status"] == 0) & (rg["status"] == 0) & (used == 0)
+    et = np.abs(rg["P"] - rm["P"]) / np.maximum(np.abs(rm["P"]), 1.0)
+    k3, thr3 = level(0.03)
+    t0 = time.perf_counter()
+    rg3, used3 = sg.gated_eval(test, thr3, md_natoms=4000)
+    t_g3 = time.perf_counter() - t0
+    acc3 = (rm["status"] == 0) & (rg3["status"] == 0) & (used3 == 0)
+    et3 = np.abs(rg3["P"] - rm["P"]) / np.maximum(np.abs(rm["P"]), 1.0)
+    out["test_at_3pct"] = {"threshold_rel_sd": thr3, "surrogate_answered": int((used3 == 0).sum()),
+                           "gated_s": t_g3, "gated_eos_per_s": len(test) / t_g3,
+                           "speedup_vs_md_only": t_md / t_g3,
+                           "rms_err_surrogate_answers_vs_md":
+                               float(np.sqrt(np.mean(et3[acc3] ** 2))) if acc3.any() else None}
+    out["test"] = {"queries": len(test), "surrogate_answered": int((used == 0).sum()),
+                   "gated_s": t_gated, "md_only_s": t_md,
+                   "gated_eos_per_s": len(test) / t_gated, "md_only_eos_per_s": len(test) / t_md,
+                   "speedup": t_md / t_gated,
+                   "rms_err_surrogate_answers_vs_md":
+                       float(np.sqrt(np.mean(et[acc] ** 2))) if acc.any() else None,
+                   "md_P_se_median": float(np.median(rm["P_se"][rm["status"] == 0]))}
+    # 6. inference throughput on large batches (one copy of the ensemble, 64k per launch)
+    big = m.Surrogate(h, 4, 65536, seed=1)
+    big.set_params(*sg.get_params())
+    xi = np.tile(xv, (1000000 // max(len(xv), 1) + 1, 1))[:1000000]
+    big.predict(xi[:65536])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    big.predict(xi)
+    t_inf = time.perf_counter() - t0
+    flops = 4 * len(xi) * 2.0 * (2 * 128 + 2 * 128 * 128 + 128 * 2)
+    peaks = load_peaks()
+    out["inference"] = {"queries": len(xi), "seconds": t_inf, "queries_per_s": len(xi) / t_inf,
+                        "tflops_incl_host_copies": flops / t_inf / 1e12,
+                        "bf16_peak_tflops": peaks.get("bf16_tflops")}
+    big.close()
+    sg.close()
+    clk = clocks.stop()
+    m.mdeos_destroy(h)
+    line = {"metric": "surrogate-gated EOS/s at 1% pressure error",
+            "value": out["test"]["gated_eos_per_s"], "unit": "EOS/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": out["test"]["gated_s"] * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (MD answers of seeded LJ boxes)", "config": {
+                "workload": SURROGATE, "train_n": args.train_n, "val_n": args.val_n,
+                "test_n": args.test_n, "epochs": args.epochs},
+            "details": out, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,7 +693,12 @@ def main():
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush (profiling)")
     ap.add_argument("--boxes", type=int, default=0, help="reduced box count (profiling)")
     ap.add_argument("--md-steps", type=int, default=0, help="reduced MD steps per box")
-    ap.add_argument("--workload", choices=["uneven", "coupled", "serving"], default="uneven",
+    ap.add_argument("--train-n", type=int, default=100000, help="surrogate: MD training samples")
+    ap.add_argument("--val-n", type=int, default=2000, help="surrogate: validation queries")
+    ap.add_argument("--test-n", type=int, default=4000, help="surrogate: test queries")
+    ap.add_argument("--epochs", type=int, default=40, help="surrogate: training epochs")
+    ap.add_argument("--workload", choices=["uneven", "coupled", "serving", "surrogate"],
+                    default="uneven",
                     help="uneven: 4096-box batched EOS (default); coupled: MD-closed hydro; "
                          "serving: Poisson request stream")
     ap.add_argument("--rates", default="50,100,200,300", help="serving: arrival rates (1/s)")
@@ -575,6 +711,8 @@ def main():
         coupled(args)
     elif args.workload == "serving" and args.impl == "ours":
         serving(args)
+    elif args.workload == "surrogate" and args.impl == "ours":
+        surrogate(args)
     elif args.impl == "reference":
         reference_arm(args)
     else:

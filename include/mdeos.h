@@ -374,6 +374,60 @@ mdeos_status mdeos_serve_stats(mdeos_server* s, long long* counts, size_t* bytes
 /* Stop: waiting requests are shed, in-flight launches finish; then release. */
 mdeos_status mdeos_serve_destroy(mdeos_server* s);
 
+/* ---- surrogate EOS (MLP ensemble gate) ----------------------------------
+ * An ensemble of n_models MLPs 2 -> 128 -> 128 -> 128 -> 2 (tanh hidden layers)
+ * maps (rho, e), normalised by mean and standard deviation, to normalised (P, T).
+ * BF16 weights and hidden activations, FP32 accumulation and FP32 master weights;
+ * the 128-wide layers run on the tensor cores.  Trained with Adam on MD answers;
+ * used as a gate: where the ensemble agrees the surrogate answers, elsewhere the
+ * request goes to the MD path.  The paper runs MD for every query (Sec. III) and
+ * points to learned accelerators of such couplings (Sec. I); this is one.
+ * Parameter vector per model (FP32, 33,666 values): W1[128,2] b1[128] W2[128,128]
+ * b2[128] W3[128,128] b3[128] W4[2,128] b4[2] (W[out,in], row-major).
+ * Normalisers norm[8]: mean(rho), mean(e), sd(rho), sd(e), mean(P), mean(T), sd(P), sd(T). */
+#define MDEOS_SURROGATE_NPARAM 33666
+typedef struct mdeos_surrogate mdeos_surrogate;
+
+/* Create on handle h (caller-owned, outlives it) with Glorot-uniform weights from
+ * `seed`; batches up to max_batch samples per launch.  Errors: EINVAL, ECUDA. */
+mdeos_status mdeos_surrogate_create(mdeos_handle* h, int32_t n_models, int32_t max_batch,
+                                    uint64_t seed, mdeos_surrogate** out);
+
+/* Set (params: host float[n_models * NPARAM], resets Adam) and/or normalisers
+ * (norm: host double[8]); either may be NULL. */
+mdeos_status mdeos_surrogate_set_params(mdeos_surrogate* s, const float* params,
+                                        const double* norm);
+mdeos_status mdeos_surrogate_get_params(mdeos_surrogate* s, float* params, double* norm);
+
+/* Mean-squared-error gradients of one batch (x: host double[n][2] = (rho, e), y: host
+ * double[n][2] = (P, T), n <= max_batch) into grads (host float[n_models * NPARAM]);
+ * *loss = the batch loss averaged over the models.  No update. */
+mdeos_status mdeos_surrogate_grads(mdeos_surrogate* s, const double* x, const double* y,
+                                   int32_t n, float* grads, double* loss);
+
+/* Adam training (beta 0.9 / 0.999, eps 1e-8) for `epochs` passes over n samples in
+ * shuffled full batches of `batch`; set_norm != 0 first sets the normalisers from
+ * the data.  loss_out (host double[epochs], may be NULL): mean batch loss per epoch. */
+mdeos_status mdeos_surrogate_train(mdeos_surrogate* s, const double* x, const double* y,
+                                   int32_t n, int32_t epochs, int32_t batch, double lr,
+                                   uint64_t seed, int32_t set_norm, double* loss_out);
+
+/* Ensemble prediction for n inputs (host double[n][2]): mean and population standard
+ * deviation over the models of (P, T) (host double[n][2] each, may be NULL) and the
+ * per-model normalised outputs (host float[n_models][n][2], may be NULL). */
+mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double* x, int32_t n,
+                                     double* mean, double* sd, float* per_model);
+
+/* Gated evaluation of n requests: where sd(P) <= threshold * max(|mean P|, 1) the
+ * result is the ensemble mean (path = -2, P_se / T_se = the ensemble spread), else
+ * the request runs on the MD path with natoms = md_natoms (> 0) or its own.
+ * used_md (host int32[n], may be NULL) marks the MD answers.  Synchronous. */
+mdeos_status mdeos_surrogate_gated_eval(mdeos_surrogate* s, const mdeos_request* reqs, int32_t n,
+                                        double threshold, int32_t md_natoms, mdeos_result* out,
+                                        int32_t* used_md);
+
+mdeos_status mdeos_surrogate_destroy(mdeos_surrogate* s);
+
 /* ---- single-box kernels exposed for parity tests ----------------------
  * These run one box through the same device code as the batch path. */
 
@@ -406,6 +460,13 @@ mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float* v4, int32
                             int32_t steps, double T_target, int32_t rescale_every, int32_t path,
                             double skin, double* epot, double* ekin, long long* cycles,
                             void* stream);
+
+/* The surrogate's tensor-core GEMM on its own: C(m, n) = sum_k A(m, k) B(k, n) with
+ * A(m, k) = A[m * sa_m + k * sa_k], B(k, n) = B[k * sb_k + n * sb_n] (device bfloat16
+ * bit patterns) and C(m, n) = C[m * sc_m + n * sc_n] (device float). */
+mdeos_status mdeos_debug_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, int32_t M,
+                                   int32_t N, int32_t K, int64_t sa_m, int64_t sa_k, int64_t sb_k,
+                                   int64_t sb_n, int64_t sc_m, int64_t sc_n, void* stream);
 
 #ifdef __cplusplus
 }

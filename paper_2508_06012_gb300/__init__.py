@@ -34,7 +34,11 @@ EXPORTED = [
     "mdeos_hydro_state", "mdeos_hydro_eos_results", "mdeos_hydro_destroy",
     "mdeos_serve_config_default", "mdeos_serve_create", "mdeos_serve_clock",
     "mdeos_serve_enqueue", "mdeos_serve_completed", "mdeos_serve_stats", "mdeos_serve_destroy",
+    "mdeos_surrogate_create", "mdeos_surrogate_set_params", "mdeos_surrogate_get_params",
+    "mdeos_surrogate_grads", "mdeos_surrogate_train", "mdeos_surrogate_predict",
+    "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_debug_gemm_bf16",
 ]
+SURROGATE_NPARAM = 33666
 
 
 class mdeos_config(ctypes.Structure):
@@ -179,6 +183,17 @@ def lib():
         L.mdeos_serve_completed.argtypes = [vp, vp, i32, P(i32)]
         L.mdeos_serve_stats.argtypes = [vp, vp, vp]
         L.mdeos_serve_destroy.argtypes = [vp]
+        L.mdeos_surrogate_create.argtypes = [vp, i32, i32, ctypes.c_uint64, P(vp)]
+        L.mdeos_surrogate_set_params.argtypes = [vp, vp, vp]
+        L.mdeos_surrogate_get_params.argtypes = [vp, vp, vp]
+        L.mdeos_surrogate_grads.argtypes = [vp, vp, vp, i32, vp, P(d)]
+        L.mdeos_surrogate_train.argtypes = [vp, vp, vp, i32, i32, i32, d, ctypes.c_uint64, i32, vp]
+        L.mdeos_surrogate_predict.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.mdeos_surrogate_gated_eval.argtypes = [vp, vp, i32, d, i32, vp, vp]
+        L.mdeos_surrogate_destroy.argtypes = [vp]
+        i64 = ctypes.c_int64
+        L.mdeos_debug_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i64, i64, i64, i64, i64,
+                                            i64, vp]
         for name in EXPORTED:
             fn = getattr(L, name)
             if name not in ("mdeos_config_default", "mdeos_last_error",
@@ -502,6 +517,86 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _vp(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+class Surrogate:
+    """MLP-ensemble surrogate EOS on a handle (mdeos_surrogate_*)."""
+
+    def __init__(self, h, n_models: int = 4, max_batch: int = 4096, seed: int = 1):
+        self.E = n_models
+        self.s = ctypes.c_void_p()
+        _check(lib().mdeos_surrogate_create(h, n_models, max_batch, seed, ctypes.byref(self.s)))
+
+    def set_params(self, params=None, norm=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        nm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float64)
+        _check(lib().mdeos_surrogate_set_params(self.s, _vp(p), _vp(nm)))
+
+    def get_params(self):
+        p = np.zeros((self.E, SURROGATE_NPARAM), dtype=np.float32)
+        nm = np.zeros(8)
+        _check(lib().mdeos_surrogate_get_params(self.s, _vp(p), _vp(nm)))
+        return p, nm
+
+    def grads(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        g = np.zeros((self.E, SURROGATE_NPARAM), dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().mdeos_surrogate_grads(self.s, _vp(x), _vp(y), len(x), _vp(g),
+                                           ctypes.byref(loss)))
+        return g, loss.value
+
+    def train(self, x, y, epochs, batch=1024, lr=1e-3, seed=0, set_norm=True):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        out = np.zeros(max(epochs, 1))
+        _check(lib().mdeos_surrogate_train(self.s, _vp(x), _vp(y), len(x), epochs, batch, lr,
+                                           seed, int(set_norm), _vp(out)))
+        return out[:epochs]
+
+    def predict(self, x, per_model=False):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        n = len(x)
+        mean = np.zeros((n, 2))
+        sd = np.zeros((n, 2))
+        pm = np.zeros((self.E, n, 2), dtype=np.float32) if per_model else None
+        _check(lib().mdeos_surrogate_predict(self.s, _vp(x), n, _vp(mean), _vp(sd), _vp(pm)))
+        return (mean, sd, pm) if per_model else (mean, sd)
+
+    def gated_eval(self, reqs, threshold, md_natoms=0):
+        arr = as_requests(reqs)
+        out = np.zeros(len(arr), dtype=RESULT_DTYPE)
+        used = np.zeros(len(arr), dtype=np.int32)
+        _check(lib().mdeos_surrogate_gated_eval(self.s, _vp(arr), len(arr), threshold, md_natoms,
+                                                _vp(out), _vp(used)))
+        return out, used
+
+    def close(self):
+        if self.s:
+            lib().mdeos_surrogate_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def mdeos_debug_gemm_bf16(A_bits, B_bits, M, N, K, sa, sb, sc, stream=None):
+    """C = A B on the tensor-core GEMM; A_bits/B_bits: torch cuda int16 tensors of
+    bfloat16 bit patterns, strides (sa_m, sa_k), (sb_k, sb_n), (sc_m, sc_n).  Returns
+    the flat output buffer (element (m, n) at m * sc_m + n * sc_n)."""
+    import torch
+    C = torch.zeros((M - 1) * sc[0] + (N - 1) * sc[1] + 1, dtype=torch.float32, device="cuda")
+    _check(lib().mdeos_debug_gemm_bf16(_dptr(A_bits), _dptr(B_bits), _dptr(C), M, N, K, sa[0],
+                                       sa[1], sb[0], sb[1], sc[0], sc[1], _stream_ptr(stream)))
+    return C
 
 
 def e_from_temperature(T, natoms):

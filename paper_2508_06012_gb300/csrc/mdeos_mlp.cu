@@ -1,0 +1,694 @@
+// Surrogate EOS: an ensemble of MLPs 2 -> 128 -> 128 -> 128 -> 2 (tanh) mapping
+// normalised (rho, e) to normalised (P, T), trained on MD answers of this library,
+// used as a gate in front of the MD path (queries on which the ensemble disagrees
+// fall back to MD).
+//
+// Precision (BF16 weights, FP32 accumulation): weight matrices enter every product
+// rounded to bfloat16; hidden activations h1..h3 and the error signals dz2, dz3 that
+// feed tensor-core products are bfloat16; biases, pre-activations, outputs, gradients
+// and the Adam state are FP32 (FP32 master weights).
+//
+// The 128x128 layers (forward Z = H W^T, backward dW = dZ^T H and dH = dZ W) run on the
+// tensor cores through one GEMM kernel (mma.m16n8k16, bf16 x bf16 -> fp32), batched
+// over the ensemble members on grid z; the 2-wide layers and the elementwise steps
+// run on the CUDA cores.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "mdeos_host.h"
+
+namespace mdeos {
+
+constexpr int kH = 128;
+// parameter offsets of one model: W1[128,2] b1 W2[128,128] b2 W3[128,128] b3 W4[2,128] b4[2]
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * 2, kOffW2 = kOffB1 + kH;
+constexpr int kOffB2 = kOffW2 + kH * kH, kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kH;
+constexpr int kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + 2 * kH, kNParam = kOffB4 + 2;
+
+// ---------------------------------------------------------------------------
+// C[z](m, n) = sum_k A[z](m, k) B[z](k, n), bf16 operands with arbitrary strides (in
+// elements), fp32 result.  64x64 tile per CTA, k in steps of 32 staged in shared
+// memory as [row][k] for both operands, 4 warps of 32x32, mma.m16n8k16.
+struct GemmArgs {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  float* C;
+  int M, N, K;
+  long long sa_m, sa_k, sa_z, sb_k, sb_n, sb_z, sc_m, sc_n, sc_z;
+};
+
+constexpr int kTM = 64, kTN = 64, kTK = 32, kTKP = kTK + 8;  // padded rows: no bank conflicts
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) bf16_gemm_kernel(GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 As[kTM][kTKP];
+  __shared__ __align__(16) __nv_bfloat16 Bs[kTN][kTKP];
+  const int z = blockIdx.z;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const __nv_bfloat16* A = g.A + (long long)z * g.sa_z;
+  const __nv_bfloat16* B = g.B + (long long)z * g.sb_z;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int gq = lane >> 2, tq = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int k0 = 0; k0 < g.K; k0 += kTK) {
+    // stage: 64 x 32 elements of each operand, zero outside the matrix
+    for (int e = tid; e < kTM * kTK; e += 128) {
+      const int r = e / kTK, c = e % kTK;
+      const int m = m0 + r, n = n0 + r, k = k0 + c;
+      As[r][c] = (m < g.M && k < g.K) ? A[(long long)m * g.sa_m + (long long)k * g.sa_k] : zero;
+      Bs[r][c] = (n < g.N && k < g.K) ? B[(long long)k * g.sb_k + (long long)n * g.sb_n] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kTK; ks += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + gq;
+        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq]);
+        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq]);
+        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq + 8]);
+        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = wn + j * 8 + gq;
+        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * tq]);
+        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * tq + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  float* C = g.C + (long long)z * g.sc_z;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + i * 16 + gq + (r >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + 2 * tq + (r & 1);
+        if (m < g.M && n < g.N) C[(long long)m * g.sc_m + (long long)n * g.sc_n] = acc[i][j][r];
+      }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise parts; index layout [model][sample][unit]
+
+// refresh the bf16 weight copies from the FP32 master parameters
+__global__ void mlp_cast_weights(const float* P, __nv_bfloat16* W1b, __nv_bfloat16* W2b,
+                                 __nv_bfloat16* W3b, __nv_bfloat16* W4b, int E) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)E * kH * kH;
+  if (i >= n) return;
+  const int e = (int)(i / (kH * kH)), r = (int)(i % (kH * kH));
+  const float* p = P + (long long)e * kNParam;
+  W2b[i] = __float2bfloat16_rn(p[kOffW2 + r]);
+  W3b[i] = __float2bfloat16_rn(p[kOffW3 + r]);
+  if (r < 2 * kH) {
+    W1b[(long long)e * 2 * kH + r] = __float2bfloat16_rn(p[kOffW1 + r]);
+    W4b[(long long)e * 2 * kH + r] = __float2bfloat16_rn(p[kOffW4 + r]);
+  }
+}
+
+// h1 = bf16(tanh(W1 x + b1)); x [B][2] FP32 (normalised, shared by the models)
+__global__ void mlp_layer1(const float* X, const float* P, const __nv_bfloat16* W1b,
+                           __nv_bfloat16* H1, int B, int E) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)E * B * kH) return;
+  const int j = (int)(i % kH), b = (int)((i / kH) % B), e = (int)(i / ((long long)B * kH));
+  const float w0 = __bfloat162float(W1b[(long long)e * 2 * kH + 2 * j]);
+  const float w1 = __bfloat162float(W1b[(long long)e * 2 * kH + 2 * j + 1]);
+  const float z = X[2 * b] * w0 + X[2 * b + 1] * w1 + P[(long long)e * kNParam + kOffB1 + j];
+  H1[i] = __float2bfloat16_rn(tanhf(z));
+}
+
+// h = bf16(tanh(Z + b)) for layers 2 and 3
+__global__ void mlp_bias_tanh(const float* Z, const float* P, int off_b, __nv_bfloat16* Hout,
+                              int B, int E) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)E * B * kH) return;
+  const int j = (int)(i % kH), e = (int)(i / ((long long)B * kH));
+  Hout[i] = __float2bfloat16_rn(tanhf(Z[i] + P[(long long)e * kNParam + off_b + j]));
+}
+
+// y = W4 h3 + b4 (FP32 accumulation); with targets: dy = 2 (y - t) / (2 B) and the
+// squared-error sum (one atomic per block)
+__global__ void mlp_output(const __nv_bfloat16* H3, const float* P, const __nv_bfloat16* W4b,
+                           const float* T, float* Y, float* dY, float* loss, int B, int E) {
+  __shared__ float s_l[8];
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (i < (long long)E * B * 2) {
+    const int o = (int)(i % 2), b = (int)((i / 2) % B), e = (int)(i / (2LL * B));
+    const __nv_bfloat16* h = H3 + ((long long)e * B + b) * kH;
+    const __nv_bfloat16* w = W4b + (long long)e * 2 * kH + o * kH;
+    float y = 0.f;
+    for (int j = 0; j < kH; ++j) y = fmaf(__bfloat162float(w[j]), __bfloat162float(h[j]), y);
+    y += P[(long long)e * kNParam + kOffB4 + o];
+    Y[i] = y;
+    if (T) {
+      const float d = y - T[2 * b + o];
+      dY[i] = d / (float)B;  // 2 (y - t) / (2 B)
+      l = d * d;
+    }
+  }
+  if (T) {
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) s_l[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_l[w];
+      atomicAdd(loss, s);
+    }
+  }
+}
+
+// output layer backward: dW4, db4 (reductions over the batch, one thread per weight)
+__global__ void mlp_back_out_w(const float* dY, const __nv_bfloat16* H3, float* G, int B, int E) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E * (2 * kH + 2)) return;
+  const int e = i / (2 * kH + 2), r = i % (2 * kH + 2);
+  float s = 0.f;
+  if (r < 2 * kH) {
+    const int o = r / kH, j = r % kH;
+    for (int b = 0; b < B; ++b)
+      s = fmaf(dY[((long long)e * B + b) * 2 + o],
+               __bfloat162float(H3[((long long)e * B + b) * kH + j]), s);
+    G[(long long)e * kNParam + kOffW4 + r] = s;
+  } else {
+    const int o = r - 2 * kH;
+    for (int b = 0; b < B; ++b) s += dY[((long long)e * B + b) * 2 + o];
+    G[(long long)e * kNParam + kOffB4 + o] = s;
+  }
+}
+
+// dz3 = bf16((dy W4) * (1 - h3^2))
+__global__ void mlp_back_out_dz(const float* dY, const __nv_bfloat16* H3, const __nv_bfloat16* W4b,
+                                __nv_bfloat16* dZ3, int B, int E) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)E * B * kH) return;
+  const int j = (int)(i % kH), b = (int)((i / kH) % B), e = (int)(i / ((long long)B * kH));
+  const float* dy = dY + ((long long)e * B + b) * 2;
+  const __nv_bfloat16* w = W4b + (long long)e * 2 * kH;
+  const float dh = dy[0] * __bfloat162float(w[j]) + dy[1] * __bfloat162float(w[kH + j]);
+  const float h = __bfloat162float(H3[i]);
+  dZ3[i] = __float2bfloat16_rn(dh * (1.f - h * h));
+}
+
+// dz = dH (1 - h^2), rounded to bf16 (layer 2) or kept FP32 (layer 1)
+__global__ void mlp_deriv(const float* dH, const __nv_bfloat16* Hh, __nv_bfloat16* dZb, float* dZf,
+                          long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float h = __bfloat162float(Hh[i]);
+  const float d = dH[i] * (1.f - h * h);
+  if (dZb) dZb[i] = __float2bfloat16_rn(d);
+  if (dZf) dZf[i] = d;
+}
+
+// bias gradient: column sums of dz over the batch
+__global__ void mlp_bias_grad(const __nv_bfloat16* dZb, const float* dZf, float* G, int off_b,
+                              int B, int E) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E * kH) return;
+  const int e = i / kH, j = i % kH;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) {
+    const long long k = ((long long)e * B + b) * kH + j;
+    s += dZb ? __bfloat162float(dZb[k]) : dZf[k];
+  }
+  G[(long long)e * kNParam + off_b + j] = s;
+}
+
+// first-layer weight gradient dW1 = dz1^T x (FP32)
+__global__ void mlp_grad_w1(const float* dZ1, const float* X, float* G, int B, int E) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E * 2 * kH) return;
+  const int e = i / (2 * kH), r = i % (2 * kH), j = r / 2, c = r % 2;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s = fmaf(dZ1[((long long)e * B + b) * kH + j], X[2 * b + c], s);
+  G[(long long)e * kNParam + kOffW1 + r] = s;
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters; omb = 1 - beta and c = 1 - beta^t,
+// each evaluated in FP64 on the host and rounded once
+__global__ void mlp_adam(float* P, const float* G, float* Mm, float* Vv, long long n, float lr,
+                         float b1, float b2, float omb1, float omb2, float eps, float c1,
+                         float c2) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float m = b1 * Mm[i] + omb1 * g;
+  const float v = b2 * Vv[i] + omb2 * g * g;
+  Mm[i] = m;
+  Vv[i] = v;
+  P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// normalise physical inputs (rho, e) -> x, per sample
+__global__ void mlp_normalise(const double* Xp, float* X, int B, double m0, double m1, double s0,
+                              double s1) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  X[2 * b] = (float)((Xp[2 * b] - m0) / s0);
+  X[2 * b + 1] = (float)((Xp[2 * b + 1] - m1) / s1);
+}
+
+// ensemble mean and (population) standard deviation of the physical outputs
+__global__ void mlp_ensemble(const float* Y, int B, int E, double ym0, double ym1, double ys0,
+                             double ys1, double* mean, double* sd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * 2) return;
+  const int o = i % 2;
+  const double m = o ? ym1 : ym0, s = o ? ys1 : ys0;
+  double a = 0.0, q = 0.0;
+  for (int e = 0; e < E; ++e) {
+    const double y = (double)Y[(long long)e * B * 2 + i] * s + m;
+    a += y;
+    q += y * y;
+  }
+  a /= E;
+  mean[i] = a;
+  sd[i] = sqrt(fmax(q / E - a * a, 0.0));
+}
+
+}  // namespace mdeos
+
+using namespace mdeos;
+
+struct mdeos_surrogate {
+  mdeos_handle* h = nullptr;
+  int E = 4, maxB = 0;
+  double norm[8] = {0, 0, 1, 1, 0, 0, 1, 1};  // x mean(2), x std(2), y mean(2), y std(2)
+  long long step = 0;
+  float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr;
+  __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W4b = nullptr;
+  __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dZb = nullptr;
+  float *Z = nullptr, *dZf = nullptr, *X = nullptr, *T = nullptr, *Y = nullptr, *dY = nullptr;
+  float* loss = nullptr;
+  double *Xp = nullptr, *mean = nullptr, *sd = nullptr;
+  std::vector<void*> allocs;
+};
+
+#define SCK(call)                                                                      \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return set_error(MDEOS_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+static cudaError_t gemm(cudaStream_t st, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C,
+                        int M, int N, int K, long long sa_m, long long sa_k, long long sa_z,
+                        long long sb_k, long long sb_n, long long sb_z, long long sc_m,
+                        long long sc_n, long long sc_z, int Z) {
+  GemmArgs g{A, B, C, M, N, K, sa_m, sa_k, sa_z, sb_k, sb_n, sb_z, sc_m, sc_n, sc_z};
+  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, Z);
+  bf16_gemm_kernel<<<grid, 128, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+static int nblk(long long n, int t = 256) { return (int)((n + t - 1) / t); }
+
+// forward of all models on s->X (B samples): H1..H3, Y; with targets also dY and loss
+static cudaError_t forward(mdeos_surrogate* s, int B, const float* T, cudaStream_t st) {
+  const int E = s->E;
+  const long long EB = (long long)E * B;
+  const long long sz = (long long)B * kH;
+  cudaError_t e;
+  mlp_layer1<<<nblk(EB * kH), 256, 0, st>>>(s->X, s->P, s->W1b, s->H1, B, E);
+  // Z2 = H1 W2^T: A(m=b, k=j) = H1[b][j], B(k=j, n=o) = W2[o][j]
+  e = gemm(st, s->H1, s->W2b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
+  if (e != cudaSuccess) return e;
+  mlp_bias_tanh<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->P, kOffB2, s->H2, B, E);
+  e = gemm(st, s->H2, s->W3b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
+  if (e != cudaSuccess) return e;
+  mlp_bias_tanh<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->P, kOffB3, s->H3, B, E);
+  mlp_output<<<nblk(EB * 2), 256, 0, st>>>(s->H3, s->P, s->W4b, T, s->Y, s->dY, s->loss, B, E);
+  return cudaGetLastError();
+}
+
+// gradients of the mean-squared error of the batch into s->G
+static cudaError_t backward(mdeos_surrogate* s, int B, cudaStream_t st) {
+  const int E = s->E;
+  const long long EB = (long long)E * B;
+  const long long sz = (long long)B * kH;
+  cudaError_t e;
+  mlp_back_out_w<<<nblk(E * (2 * kH + 2)), 256, 0, st>>>(s->dY, s->H3, s->G, B, E);
+  mlp_back_out_dz<<<nblk(EB * kH), 256, 0, st>>>(s->dY, s->H3, s->W4b, s->dZb, B, E);
+  // dW3 = dZ3^T H2: A(m=o, k=b) = dZ3[b][o], B(k=b, n=j) = H2[b][j]
+  e = gemm(st, s->dZb, s->H2, s->G + kOffW3, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
+  if (e != cudaSuccess) return e;
+  mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(s->dZb, nullptr, s->G, kOffB3, B, E);
+  // dH2 = dZ3 W3: A(m=b, k=o) = dZ3[b][o], B(k=o, n=j) = W3[o][j]
+  e = gemm(st, s->dZb, s->W3b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
+  if (e != cudaSuccess) return e;
+  mlp_deriv<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->H2, s->dZb, nullptr, EB * kH);
+  e = gemm(st, s->dZb, s->H1, s->G + kOffW2, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
+  if (e != cudaSuccess) return e;
+  mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(s->dZb, nullptr, s->G, kOffB2, B, E);
+  e = gemm(st, s->dZb, s->W2b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
+  if (e != cudaSuccess) return e;
+  mlp_deriv<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->H1, nullptr, s->dZf, EB * kH);
+  mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(nullptr, s->dZf, s->G, kOffB1, B, E);
+  mlp_grad_w1<<<nblk(E * 2 * kH), 256, 0, st>>>(s->dZf, s->X, s->G, B, E);
+  return cudaGetLastError();
+}
+
+static cudaError_t cast_weights(mdeos_surrogate* s, cudaStream_t st) {
+  mlp_cast_weights<<<nblk((long long)s->E * kH * kH), 256, 0, st>>>(s->P, s->W1b, s->W2b, s->W3b,
+                                                                    s->W4b, s->E);
+  return cudaGetLastError();
+}
+
+extern "C" mdeos_status mdeos_surrogate_destroy(mdeos_surrogate* s);
+
+extern "C" mdeos_status mdeos_surrogate_create(mdeos_handle* h, int32_t n_models, int32_t max_batch,
+                                               uint64_t seed, mdeos_surrogate** out) {
+  if (!h || !out || n_models < 1 || n_models > 16 || max_batch < 1 || max_batch > (1 << 22))
+    return set_error(MDEOS_EINVAL, "bad surrogate_create arguments");
+  *out = nullptr;
+  mdeos_surrogate* s = new mdeos_surrogate();
+  s->h = h;
+  s->E = n_models;
+  s->maxB = max_batch;
+  const int E = n_models;
+  const long long EB = (long long)E * max_batch;
+  cudaError_t e = cudaSetDevice(handle_device(h));
+  auto dalloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+    if (e == cudaSuccess) s->allocs.push_back(*p);
+  };
+  const size_t np = (size_t)E * kNParam;
+  dalloc((void**)&s->P, np * 4);
+  dalloc((void**)&s->G, np * 4);
+  dalloc((void**)&s->Mm, np * 4);
+  dalloc((void**)&s->Vv, np * 4);
+  dalloc((void**)&s->W1b, (size_t)E * 2 * kH * 2);
+  dalloc((void**)&s->W2b, (size_t)E * kH * kH * 2);
+  dalloc((void**)&s->W3b, (size_t)E * kH * kH * 2);
+  dalloc((void**)&s->W4b, (size_t)E * 2 * kH * 2);
+  dalloc((void**)&s->H1, EB * kH * 2);
+  dalloc((void**)&s->H2, EB * kH * 2);
+  dalloc((void**)&s->H3, EB * kH * 2);
+  dalloc((void**)&s->dZb, EB * kH * 2);
+  dalloc((void**)&s->Z, EB * kH * 4);
+  dalloc((void**)&s->dZf, EB * kH * 4);
+  dalloc((void**)&s->X, (size_t)max_batch * 2 * 4);
+  dalloc((void**)&s->T, (size_t)max_batch * 2 * 4);
+  dalloc((void**)&s->Y, EB * 2 * 4);
+  dalloc((void**)&s->dY, EB * 2 * 4);
+  dalloc((void**)&s->loss, 256);
+  dalloc((void**)&s->Xp, (size_t)max_batch * 2 * 8);
+  dalloc((void**)&s->mean, (size_t)max_batch * 2 * 8);
+  dalloc((void**)&s->sd, (size_t)max_batch * 2 * 8);
+  if (e != cudaSuccess) {
+    mdeos_surrogate_destroy(s);
+    return set_error(MDEOS_ECUDA, std::string("surrogate_create: ") + cudaGetErrorString(e));
+  }
+  // Glorot-uniform weights, zero biases
+  std::vector<float> p(np, 0.f);
+  std::mt19937_64 rng(seed);
+  std::uniform_real_distribution<double> u(-1.0, 1.0);
+  for (int m = 0; m < E; ++m) {
+    float* q = p.data() + (size_t)m * kNParam;
+    const double l1 = std::sqrt(6.0 / (kH + 2)), l2 = std::sqrt(6.0 / (2 * kH));
+    for (int i = 0; i < 2 * kH; ++i) q[kOffW1 + i] = (float)(l1 * u(rng));
+    for (int i = 0; i < kH * kH; ++i) q[kOffW2 + i] = (float)(l2 * u(rng));
+    for (int i = 0; i < kH * kH; ++i) q[kOffW3 + i] = (float)(l2 * u(rng));
+    for (int i = 0; i < 2 * kH; ++i) q[kOffW4 + i] = (float)(l1 * u(rng));
+  }
+  cudaStream_t st = handle_stream(h);
+  e = cudaMemcpyAsync(s->P, p.data(), np * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cast_weights(s, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    mdeos_surrogate_destroy(s);
+    return set_error(MDEOS_ECUDA, std::string("surrogate init: ") + cudaGetErrorString(e));
+  }
+  *out = s;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_set_params(mdeos_surrogate* s, const float* params,
+                                                   const double* norm) {
+  if (!s) return set_error(MDEOS_EINVAL, "surrogate is NULL");
+  cudaStream_t st = handle_stream(s->h);
+  SCK(cudaSetDevice(handle_device(s->h)));
+  if (params) {
+    const size_t np = (size_t)s->E * kNParam;
+    SCK(cudaMemcpyAsync(s->P, params, np * 4, cudaMemcpyHostToDevice, st));
+    SCK(cudaMemsetAsync(s->Mm, 0, np * 4, st));
+    SCK(cudaMemsetAsync(s->Vv, 0, np * 4, st));
+    s->step = 0;
+    SCK(cast_weights(s, st));
+  }
+  if (norm) std::memcpy(s->norm, norm, sizeof(s->norm));
+  SCK(cudaStreamSynchronize(st));
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_get_params(mdeos_surrogate* s, float* params, double* norm) {
+  if (!s) return set_error(MDEOS_EINVAL, "surrogate is NULL");
+  SCK(cudaSetDevice(handle_device(s->h)));
+  cudaStream_t st = handle_stream(s->h);
+  if (params)
+    SCK(cudaMemcpyAsync(params, s->P, (size_t)s->E * kNParam * 4, cudaMemcpyDeviceToHost, st));
+  SCK(cudaStreamSynchronize(st));
+  if (norm) std::memcpy(norm, s->norm, sizeof(s->norm));
+  return MDEOS_OK;
+}
+
+// normalised inputs/targets of n samples into s->X / s->T (host FP64 in)
+static mdeos_status load_batch(mdeos_surrogate* s, const double* xp, const double* yp, int n,
+                               cudaStream_t st) {
+  std::vector<float> x(2 * (size_t)n), t;
+  for (int b = 0; b < n; ++b)
+    for (int c = 0; c < 2; ++c)
+      x[2 * b + c] = (float)((xp[2 * b + c] - s->norm[c]) / s->norm[2 + c]);
+  SCK(cudaMemcpyAsync(s->X, x.data(), x.size() * 4, cudaMemcpyHostToDevice, st));
+  if (yp) {
+    t.resize(2 * (size_t)n);
+    for (int b = 0; b < n; ++b)
+      for (int c = 0; c < 2; ++c)
+        t[2 * b + c] = (float)((yp[2 * b + c] - s->norm[4 + c]) / s->norm[6 + c]);
+    SCK(cudaMemcpyAsync(s->T, t.data(), t.size() * 4, cudaMemcpyHostToDevice, st));
+  }
+  SCK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_grads(mdeos_surrogate* s, const double* x, const double* y,
+                                              int32_t n, float* grads, double* loss) {
+  if (!s || !x || !y || n < 1 || n > s->maxB) return set_error(MDEOS_EINVAL, "bad grads arguments");
+  SCK(cudaSetDevice(handle_device(s->h)));
+  cudaStream_t st = handle_stream(s->h);
+  mdeos_status ms = load_batch(s, x, y, n, st);
+  if (ms != MDEOS_OK) return ms;
+  SCK(cudaMemsetAsync(s->loss, 0, 4, st));
+  SCK(forward(s, n, s->T, st));
+  SCK(backward(s, n, st));
+  count_launch(s->h, 20);
+  if (grads)
+    SCK(cudaMemcpyAsync(grads, s->G, (size_t)s->E * kNParam * 4, cudaMemcpyDeviceToHost, st));
+  float l = 0.f;
+  SCK(cudaMemcpyAsync(&l, s->loss, 4, cudaMemcpyDeviceToHost, st));
+  SCK(cudaStreamSynchronize(st));
+  if (loss) *loss = (double)l / (2.0 * n * s->E);
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_train(mdeos_surrogate* s, const double* x, const double* y,
+                                              int32_t n, int32_t epochs, int32_t batch, double lr,
+                                              uint64_t seed, int32_t set_norm, double* loss_out) {
+  if (!s || !x || !y || n < 1 || epochs < 0 || batch < 1 || batch > s->maxB || !(lr > 0))
+    return set_error(MDEOS_EINVAL, "bad train arguments");
+  if (set_norm) {  // normalisers from the training data: mean and standard deviation
+    for (int c = 0; c < 4; ++c) {
+      const double* a = c < 2 ? x : y;
+      const int col = c % 2;
+      double m = 0.0, q = 0.0;
+      for (int i = 0; i < n; ++i) m += a[2 * i + col];
+      m /= n;
+      for (int i = 0; i < n; ++i) q += (a[2 * i + col] - m) * (a[2 * i + col] - m);
+      const double sdv = std::sqrt(q / n);
+      s->norm[(c < 2 ? 0 : 4) + col] = m;
+      s->norm[(c < 2 ? 2 : 6) + col] = sdv > 0 ? sdv : 1.0;
+    }
+  }
+  SCK(cudaSetDevice(handle_device(s->h)));
+  cudaStream_t st = handle_stream(s->h);
+  std::mt19937_64 rng(seed);
+  std::vector<int> perm(n);
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  std::vector<double> bx(2 * (size_t)batch), by(2 * (size_t)batch);
+  const long long np = (long long)s->E * kNParam;
+  const float b1 = 0.9f, b2 = 0.999f;
+  for (int ep = 0; ep < epochs; ++ep) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    double lsum = 0.0;
+    int nb = 0;
+    for (int off = 0; off + batch <= n; off += batch) {  // full batches only
+      for (int k = 0; k < batch; ++k) {
+        const int i = perm[off + k];
+        bx[2 * k] = x[2 * i];
+        bx[2 * k + 1] = x[2 * i + 1];
+        by[2 * k] = y[2 * i];
+        by[2 * k + 1] = y[2 * i + 1];
+      }
+      mdeos_status ms = load_batch(s, bx.data(), by.data(), batch, st);
+      if (ms != MDEOS_OK) return ms;
+      SCK(cudaMemsetAsync(s->loss, 0, 4, st));
+      SCK(forward(s, batch, s->T, st));
+      SCK(backward(s, batch, st));
+      ++s->step;
+      const float c1 = (float)(1.0 - std::pow(0.9, (double)s->step));
+      const float c2 = (float)(1.0 - std::pow(0.999, (double)s->step));
+      mlp_adam<<<nblk(np), 256, 0, st>>>(s->P, s->G, s->Mm, s->Vv, np, (float)lr, b1, b2,
+                                         (float)(1.0 - 0.9), (float)(1.0 - 0.999), 1e-8f, c1, c2);
+      SCK(cudaGetLastError());
+      SCK(cast_weights(s, st));
+      count_launch(s->h, 22);
+      float l = 0.f;
+      SCK(cudaMemcpyAsync(&l, s->loss, 4, cudaMemcpyDeviceToHost, st));
+      SCK(cudaStreamSynchronize(st));
+      lsum += (double)l / (2.0 * batch * s->E);
+      ++nb;
+    }
+    if (loss_out) loss_out[ep] = nb ? lsum / nb : 0.0;
+  }
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double* x, int32_t n,
+                                                double* mean, double* sd, float* per_model) {
+  if (!s || !x || n < 0) return set_error(MDEOS_EINVAL, "bad predict arguments");
+  SCK(cudaSetDevice(handle_device(s->h)));
+  cudaStream_t st = handle_stream(s->h);
+  for (int off = 0; off < n; off += s->maxB) {
+    const int B = std::min(s->maxB, n - off);
+    SCK(cudaMemcpyAsync(s->Xp, x + 2 * (size_t)off, (size_t)B * 16, cudaMemcpyHostToDevice, st));
+    mlp_normalise<<<nblk(B), 256, 0, st>>>(s->Xp, s->X, B, s->norm[0], s->norm[1], s->norm[2],
+                                           s->norm[3]);
+    SCK(forward(s, B, nullptr, st));
+    mlp_ensemble<<<nblk(2 * B), 256, 0, st>>>(s->Y, B, s->E, s->norm[4], s->norm[5], s->norm[6],
+                                              s->norm[7], s->mean, s->sd);
+    SCK(cudaGetLastError());
+    count_launch(s->h, 9);
+    if (mean)
+      SCK(cudaMemcpyAsync(mean + 2 * (size_t)off, s->mean, (size_t)B * 16, cudaMemcpyDeviceToHost, st));
+    if (sd)
+      SCK(cudaMemcpyAsync(sd + 2 * (size_t)off, s->sd, (size_t)B * 16, cudaMemcpyDeviceToHost, st));
+    if (per_model)
+      for (int m = 0; m < s->E; ++m)
+        SCK(cudaMemcpyAsync(per_model + ((size_t)m * n + off) * 2, s->Y + (size_t)m * B * 2,
+                            (size_t)B * 8, cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+  }
+  return MDEOS_OK;
+}
+
+// Surrogate answer where the ensemble agrees (sd_P <= threshold * max(|P|, 1)),
+// the MD path (requests evaluated with natoms = md_natoms) elsewhere.
+extern "C" mdeos_status mdeos_surrogate_gated_eval(mdeos_surrogate* s, const mdeos_request* reqs,
+                                                   int32_t n, double threshold, int32_t md_natoms,
+                                                   mdeos_result* out, int32_t* used_md) {
+  if (!s || !reqs || !out || n < 0 || !(threshold >= 0))
+    return set_error(MDEOS_EINVAL, "bad gated_eval arguments");
+  std::vector<double> x(2 * (size_t)n), mean(2 * (size_t)n), sd(2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    x[2 * i] = reqs[i].rho;
+    x[2 * i + 1] = reqs[i].e;
+  }
+  mdeos_status ms = mdeos_surrogate_predict(s, x.data(), n, mean.data(), sd.data(), nullptr);
+  if (ms != MDEOS_OK) return ms;
+  std::vector<mdeos_request> md;
+  std::vector<int> idx;
+  for (int i = 0; i < n; ++i) {
+    const bool ok = sd[2 * i] <= threshold * std::max(std::fabs(mean[2 * i]), 1.0) &&
+                    (reqs[i].flags & MDEOS_REQ_TEMPERATURE) == 0;
+    if (used_md) used_md[i] = ok ? 0 : 1;
+    if (ok) {
+      mdeos_result& r = out[i];
+      std::memset(&r, 0, sizeof(r));
+      r.P = mean[2 * i];
+      r.T = mean[2 * i + 1];
+      r.P_se = sd[2 * i];
+      r.T_se = sd[2 * i + 1];
+      r.sigma[0] = r.sigma[1] = r.sigma[2] = r.P;
+      r.element_id = reqs[i].element_id;
+      r.natoms = 0;
+      r.status = MDEOS_OK;
+      r.path = -2;  // answered by the surrogate
+    } else {
+      mdeos_request q = reqs[i];
+      if (md_natoms > 0) q.natoms = md_natoms;
+      md.push_back(q);
+      idx.push_back(i);
+    }
+  }
+  if (!md.empty()) {
+    uint64_t t = 0;
+    ms = mdeos_submit(s->h, md.data(), (int)md.size(), &t);
+    if (ms != MDEOS_OK) return ms;
+    std::vector<mdeos_result> r(md.size());
+    ms = mdeos_poll(s->h, t, r.data(), -1);
+    if (ms != MDEOS_OK) return ms;
+    for (size_t k = 0; k < md.size(); ++k) out[idx[k]] = r[k];
+  }
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_destroy(mdeos_surrogate* s) {
+  if (!s) return MDEOS_OK;
+  if (s->h) {
+    cudaSetDevice(handle_device(s->h));
+    cudaStreamSynchronize(handle_stream(s->h));
+  }
+  for (void* p : s->allocs) cudaFree(p);
+  delete s;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_debug_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C,
+                                              int32_t M, int32_t N, int32_t K, int64_t sa_m,
+                                              int64_t sa_k, int64_t sb_k, int64_t sb_n,
+                                              int64_t sc_m, int64_t sc_n, void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1)
+    return set_error(MDEOS_EINVAL, "bad gemm arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  SCK(gemm(st, reinterpret_cast<const __nv_bfloat16*>(A),
+           reinterpret_cast<const __nv_bfloat16*>(B), C, M, N, K, sa_m, sa_k, 0, sb_k, sb_n, 0,
+           sc_m, sc_n, 0, 1));
+  SCK(cudaStreamSynchronize(st));
+  return MDEOS_OK;
+}

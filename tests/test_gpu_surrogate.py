@@ -1,0 +1,162 @@
+"""GPU tests of the surrogate EOS (mdeos_surrogate_*) against the FP64 surrogate oracle
+(oracle/surrogate.py): the tensor-core GEMM, the forward pass, the gradients and the
+Adam step on identical parameters and batches, and the disagreement gate.
+
+Tolerances: GEMM results within the FP32 accumulation bound K * 2^-23 * sum|a b|.
+Forward and gradients: the oracle applies the same bfloat16 roundings in FP64; where
+an FP32 value and its FP64 counterpart straddle a bfloat16 rounding boundary the two
+round one ulp apart, so the comparison bounds the mean and the worst difference and
+requires the GPU to sit much closer to the bfloat16 oracle than the bfloat16 oracle
+sits to the plain FP64 network.
+"""
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2508_06012_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def h(m):
+    hd = m.mdeos_create()
+    yield hd
+    m.mdeos_destroy(hd)
+
+
+def _bits(a):
+    import torch
+    u = S.bf16(a).astype(np.float32).view(np.uint32) >> 16
+    return torch.from_numpy(u.astype(np.uint16).view(np.int16).copy()).cuda()
+
+
+@pytest.mark.parametrize("M,N,K,ta,tb", [(1, 1, 1, 0, 0), (64, 64, 32, 0, 1), (100, 70, 45, 1, 0),
+                                         (128, 128, 1024, 1, 0), (257, 128, 128, 0, 1)])
+def test_tensor_core_gemm(m, M, N, K, ta, tb):
+    rng = np.random.default_rng(M + N + K)
+    A = S.bf16(rng.standard_normal((M, K)))
+    B = S.bf16(rng.standard_normal((K, N)))
+    Ast = A.T.copy() if ta else A          # stored transposed: A(m, k) = Ast[k, m]
+    Bst = B.T.copy() if tb else B          # stored transposed: B(k, n) = Bst[n, k]
+    sa = (1, M) if ta else (K, 1)
+    sb = (1, K) if tb else (N, 1)
+    C = m.mdeos_debug_gemm_bf16(_bits(Ast.ravel()), _bits(Bst.ravel()), M, N, K, sa, sb, (N, 1))
+    C = C.cpu().numpy()[:M * N].reshape(M, N).astype(np.float64)
+    ref = A @ B
+    bound = K * 2.0 ** -23 * (np.abs(A) @ np.abs(B)) + 1e-30
+    assert (np.abs(C - ref) <= bound).all()
+
+
+def _params(seed, E=4):
+    rng = np.random.default_rng(seed)
+    p = S.init_params(seed, E)
+    for e in range(E):   # non-zero biases so every term of the forward pass matters
+        d = S.unpack(p[e])
+        for name in ("b1", "b2", "b3", "b4"):
+            d[name] = 0.1 * rng.standard_normal(d[name].shape)
+        p[e] = S.pack(d)
+    return p.astype(np.float32).astype(np.float64)
+
+
+NORM = np.array([0.75, -1.0, 0.25, 2.0, 1.5, 1.2, 2.0, 0.6])
+
+
+def _inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0.3, 1.2, n), rng.uniform(-5.0, 3.0, n)], axis=1)
+
+
+def test_forward_matches_oracle(m, h):
+    p = _params(11)
+    x = _inputs(1000, 12)
+    with m.Surrogate(h, 4, 512, seed=1) as sg:
+        sg.set_params(p, NORM)
+        mean, sd, pm = sg.predict(x, per_model=True)
+    xn = (x - NORM[:2]) / NORM[2:4]
+    ref16 = np.array([S.forward(p[e], xn)[0] for e in range(4)])
+    ref64 = np.array([S.forward(p[e], xn, bf16_mode=False)[0] for e in range(4)])
+    d = np.abs(pm - ref16)
+    assert d.max() <= 2e-2 and d.mean() <= 2e-4, (d.max(), d.mean())
+    assert d.mean() < 0.1 * np.abs(ref16 - ref64).mean()
+    phys = ref16 * NORM[6:8] + NORM[4:6]
+    assert np.allclose(mean, phys.mean(axis=0), atol=5e-2)
+    assert np.allclose(sd, phys.std(axis=0), atol=5e-2)
+
+
+def test_gradients_match_oracle(m, h):
+    p = _params(21)
+    x = _inputs(300, 22)
+    y = np.stack([x[:, 0] * (x[:, 1] + 3.0), 0.5 * x[:, 1] + 2.0], axis=1)
+    with m.Surrogate(h, 4, 512, seed=1) as sg:
+        sg.set_params(p, NORM)
+        g, loss = sg.grads(x, y)
+    xn = (x - NORM[:2]) / NORM[2:4]
+    yn = (y - NORM[4:6]) / NORM[6:8]
+    losses = []
+    for e in range(4):
+        l16, g16 = S.loss_and_grad(p[e], xn, yn)
+        _, g64 = S.loss_and_grad(p[e], xn, yn, bf16_mode=False)
+        losses.append(l16)
+        dg = np.linalg.norm(g[e] - g16)
+        assert dg <= 2e-2 * np.linalg.norm(g16), (e, dg / np.linalg.norm(g16))
+        assert dg <= 0.5 * np.linalg.norm(g16 - g64)
+    assert loss == pytest.approx(np.mean(losses), rel=1e-4)
+
+
+def test_adam_step_matches_oracle(m, h):
+    p = _params(31, 2)
+    x = _inputs(256, 32)
+    y = np.stack([x[:, 0] ** 2, x[:, 1]], axis=1)
+    with m.Surrogate(h, 2, 256, seed=1) as sg:
+        sg.set_params(p, NORM)
+        g, _ = sg.grads(x, y)
+        sg.train(x, y, epochs=1, batch=256, lr=1e-3, set_norm=False)   # one step, same batch
+        p1, _ = sg.get_params()
+    for e in range(2):
+        ge = g[e].astype(np.float64)
+        ref, _, _ = S.adam_step(p[e], ge, np.zeros(S.NPARAM), np.zeros(S.NPARAM), 1, lr=1e-3)
+        # first step = lr g / (|g| + eps): where |g| is far above eps it does not depend on
+        # the batch summation order (the training step sums in another order)
+        big = np.abs(ge) > 1e-6
+        assert big.mean() > 0.9
+        assert np.abs(p1[e] - ref)[big].max() <= 2e-7
+        assert np.abs(p1[e] - p[e]).max() <= 1e-3 * (1 + 1e-5)   # first step: at most lr
+
+
+def test_training_fit_and_disagreement_gate(m, h):
+    """A smooth EOS-like map is learned; off the training domain the members disagree
+    and the gate sends those requests to MD."""
+    rng = np.random.default_rng(41)
+    n = 8192
+    x = _inputs(n, 42)
+    y = np.stack([x[:, 0] * (2.0 / 3.0) * (x[:, 1] + 6.0) - x[:, 0] ** 2,
+                  (x[:, 1] + 6.0) / 1.5 - x[:, 0]], axis=1)
+    with m.Surrogate(h, 4, 1024, seed=5) as sg:
+        losses = sg.train(x, y, epochs=30, batch=512, lr=2e-3, seed=3)
+        assert losses[-1] < 0.01 * losses[0], losses[[0, -1]]
+        xin = _inputs(500, 43)
+        yin = np.stack([xin[:, 0] * (2.0 / 3.0) * (xin[:, 1] + 6.0) - xin[:, 0] ** 2,
+                        (xin[:, 1] + 6.0) / 1.5 - xin[:, 0]], axis=1)
+        mean, sd = sg.predict(xin)
+        assert np.abs(mean - yin).mean() < 0.05
+        xout = np.stack([rng.uniform(4.0, 6.0, 200), rng.uniform(20.0, 40.0, 200)], axis=1)
+        _, sd_out = sg.predict(xout)
+        assert np.median(sd_out[:, 0]) > 10 * np.median(sd[:, 0])
+        thr = float(np.percentile(sd[:, 0] / np.maximum(np.abs(mean[:, 0]), 1.0), 99))
+        reqs = [dict(rho=float(r), e=float(e), natoms=108, steps_equil=20, steps_avg=20, seed=k)
+                for k, (r, e) in enumerate(xin[:20])]
+        reqs += [dict(rho=1.0, e=50.0, natoms=108, steps_equil=20, steps_avg=20, seed=99)]
+        out, used = sg.gated_eval(reqs, thr)
+    assert used[-1] == 1 and out["path"][-1] >= 0            # off-domain: MD
+    assert (used[:20] == 0).sum() >= 15                       # in-domain: mostly surrogate
+    assert (out["path"][:20][used[:20] == 0] == -2).all()
