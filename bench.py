@@ -32,7 +32,8 @@ FLOPS_PER_PAIR = 27  # nominal FP32 flops per in-cutoff pair
 # DRAM traffic of one eos_batch_kernel launch (dram__bytes_read + write) from the
 # ncu capture summarised in profiles/eos_batch_kernel_config2.md, keyed by a hash
 # of the kernel sources: any change to csrc/ invalidates it (reported as null).
-MEASURED_TRAFFIC = {"csrc_sha256_12": "352c3e164e53", "bytes_per_launch": 3.16e11}
+MEASURED_TRAFFIC = {"csrc_sha256_12": "478e341e1098", "bytes_per_launch": 3.84e11,
+                    "executed_fp32_frac": 0.180}
 
 
 def kernel_source_hash() -> str:
@@ -284,6 +285,9 @@ def ours(args):
                     if kernel_source_hash() == MEASURED_TRAFFIC["csrc_sha256_12"] else None),
         "traffic_note": "bytes per launch; ncu capture of a 456-box x 200-step case scaled by "
                         "atom-steps (x90.5)",
+        "executed_fp32_frac_ncu": (MEASURED_TRAFFIC["executed_fp32_frac"]
+                                   if kernel_source_hash() == MEASURED_TRAFFIC["csrc_sha256_12"]
+                                   else None),
         "kernel": "eos_batch_kernel",
         "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flop x {fmax:.0f} MHz (max SM clock)",
         "flops_basis": f"{FLOPS_PER_PAIR} flop x in-cutoff ordered pairs counted in this run",
