@@ -209,6 +209,12 @@ def ours(args):
     reqs = gpu_requests(m, boxes)
     nbox = len(reqs)
     h = m.mdeos_create(m.mdeos_config_default(device=local))
+    tune = None
+    if not args.no_autotune:  # measured skin per atom count (outside the timed region)
+        t_tune = time.perf_counter()
+        tab = m.mdeos_autotune(h, reqs, steps=200)
+        tune = {"seconds": time.perf_counter() - t_tune,
+                "skin_by_natoms": {str(int(r[0])): float(r[1]) for r in tab}}
     b = m.mdeos_batch_create(h, reqs)
     info = m.mdeos_batch_info(b)
     stream = torch.cuda.Stream()
@@ -318,7 +324,7 @@ def ours(args):
                        "boxes_per_gpu": nbox,
                        "l2": "flushed between timed iterations (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (independent boxes)",
-                       "plan": info},
+                       "plan": info, "autotune": tune},
             "pairs_per_s": pairs_per_launch * args.steps * world / (dev_ms_max / 1000.0),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": clk, "wall_s_timed": wall,
@@ -695,6 +701,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush (profiling)")
+    ap.add_argument("--no-autotune", action="store_true", help="planner default skin 0.3")
     ap.add_argument("--boxes", type=int, default=0, help="reduced box count (profiling)")
     ap.add_argument("--md-steps", type=int, default=0, help="reduced MD steps per box")
     ap.add_argument("--train-n", type=int, default=100000, help="surrogate: MD training samples")

@@ -214,6 +214,19 @@ mdeos_status mdeos_stats(const mdeos_handle* h, size_t* last_h2d_bytes, size_t* 
 mdeos_status mdeos_submit_noalloc(const mdeos_config* cfg, const mdeos_request* reqs, int32_t n,
                                   mdeos_result* d_results, void* stream);
 
+/* ---- autotuner ----------------------------------------------------------
+ * The Verlet skin trades list rebuilds (rarer with a larger skin) against pair
+ * candidates per step (more with a larger skin); the best value depends on the box
+ * size.  For every atom count among the Verlet-list boxes of reqs (host, n), one
+ * full-GPU wave of such boxes (cycled from reqs, `steps` MD steps each) is timed with
+ * CUDA events for each skin in {0.2, 0.25, 0.3, 0.35, 0.4, 0.5}; the fastest whose
+ * boxes all succeed is kept in the handle and used by later planning of boxes with
+ * that atom count while cfg.skin <= 0.  table (host double[3 * max_out], may be NULL)
+ * receives (natoms, skin, ms per box) rows and *n_out their number.  Synchronous.
+ * Errors: MDEOS_EINVAL (steps < 20), MDEOS_ENOMEM, MDEOS_ECUDA. */
+mdeos_status mdeos_autotune(mdeos_handle* h, const mdeos_request* reqs, int32_t n, int32_t steps,
+                            double* table, int32_t max_out, int32_t* n_out);
+
 /* ---- warm-start store -------------------------------------------------
  * Slot rules: an element_id first seen takes the next free slot (none free:
  * evaluated cold, not stored); a slot is rewritten by every successful

@@ -37,6 +37,7 @@ EXPORTED = [
     "mdeos_surrogate_create", "mdeos_surrogate_set_params", "mdeos_surrogate_get_params",
     "mdeos_surrogate_grads", "mdeos_surrogate_train", "mdeos_surrogate_predict",
     "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_debug_gemm_bf16",
+    "mdeos_autotune",
 ]
 SURROGATE_NPARAM = 33666
 
@@ -191,6 +192,7 @@ def lib():
         L.mdeos_surrogate_predict.argtypes = [vp, vp, i32, vp, vp, vp]
         L.mdeos_surrogate_gated_eval.argtypes = [vp, vp, i32, d, i32, vp, vp]
         L.mdeos_surrogate_destroy.argtypes = [vp]
+        L.mdeos_autotune.argtypes = [vp, vp, i32, i32, vp, i32, P(i32)]
         i64 = ctypes.c_int64
         L.mdeos_debug_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i64, i64, i64, i64, i64,
                                             i64, vp]
@@ -517,6 +519,17 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def mdeos_autotune(h, reqs, steps: int = 200) -> np.ndarray:
+    """Measure the best Verlet skin per atom count on this GPU and keep it in the
+    handle; returns rows (natoms, skin, ms of GPU time per box)."""
+    arr = as_requests(reqs)
+    tab = np.zeros((64, 3))
+    k = ctypes.c_int32()
+    _check(lib().mdeos_autotune(h, arr.ctypes.data_as(ctypes.c_void_p), len(arr), steps,
+                                tab.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(k)))
+    return tab[:k.value]
 
 
 def _vp(a):

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -138,6 +139,9 @@ static RunParams make_run_params(const mdeos_config* c) {
 // ---------------------------------------------------------------------------
 // planner: one box
 
+// Verlet skin per atom count measured by mdeos_autotune (used when cfg.skin <= 0)
+using SkinTable = std::map<int, float>;
+
 struct BoxPlan {
   BoxDesc bd;
   int warps = 4, apt = 1;
@@ -153,7 +157,8 @@ static int round_apt(int a) { return a <= 1 ? 1 : (a <= 2 ? 2 : 4); }
 // minimum image) simulate the same box.
 static double box_side(int n, double rho) { return (double)(float)std::cbrt((double)n / rho); }
 
-static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, bool allow_big) {
+static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, bool allow_big,
+                        const SkinTable* tuned) {
   BoxPlan p;
   BoxDesc& b = p.bd;
   std::memset(&b, 0, sizeof(b));
@@ -189,7 +194,13 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
   }
   const double steps = (double)r.steps_equil + r.steps_avg;
   // path choice (autotuner defaults; a measured table can override per class)
-  double skin = c.skin > 0 ? c.skin : 0.3;
+  double skin = 0.3;
+  if (c.skin > 0) {
+    skin = c.skin;
+  } else if (tuned) {
+    const auto it = tuned->find(n);
+    if (it != tuned->end()) skin = it->second;
+  }
   const double smax = 0.5 * L - c.rc;
   if (n > kMaxAtoms) {
     // above the shared-memory limit: Verlet list, state in global memory
@@ -270,14 +281,15 @@ struct Plan {
 };
 
 static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_config& c, int nsm,
-                              int smem_max, Plan& plan, bool allow_big = true) {
+                              int smem_max, Plan& plan, bool allow_big = true,
+                              const SkinTable* tuned = nullptr) {
   plan.boxes.clear();
   plan.items.clear();
   plan.status.assign(n, MDEOS_OK);
   std::vector<BoxPlan> bp;
   bp.reserve(n);
   for (int i = 0; i < n; ++i) {
-    BoxPlan p = plan_box(reqs[i], c, i, allow_big);
+    BoxPlan p = plan_box(reqs[i], c, i, allow_big, tuned);
     plan.status[i] = p.status;
     if (p.status == MDEOS_OK) bp.push_back(p);
   }
@@ -422,6 +434,7 @@ struct WarmSlot {
 
 struct mdeos_handle {
   mdeos_config cfg;
+  SkinTable tuned_skin;  // from mdeos_autotune
   // warm-start store: slot k holds x float4[warm_atoms] then v float4[warm_atoms]
   float4* d_warm = nullptr;
   int* d_warm_flag = nullptr;
@@ -634,7 +647,7 @@ extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs,
   std::lock_guard<std::mutex> lock(h->mu);
   CK(cudaSetDevice(h->device));
   Plan plan;
-  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan);
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin);
   if (st != MDEOS_OK) return st;
   assign_warm(h, plan, reqs);
   TicketState t;
@@ -762,7 +775,8 @@ extern "C" mdeos_status mdeos_batch_create(mdeos_handle* h, const mdeos_request*
   mdeos_batch* b = new mdeos_batch();
   b->h = h;
   b->n = n;
-  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, b->plan);
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, b->plan, true,
+                              &h->tuned_skin);
   if (st != MDEOS_OK) {
     delete b;
     return st;
@@ -865,6 +879,114 @@ extern "C" mdeos_status mdeos_batch_destroy(mdeos_batch* b) {
 }
 
 // ---------------------------------------------------------------------------
+// autotuner: Verlet skin per atom count
+
+// Upload a plan and run it on the handle's stream, returning the kernel time
+// (CUDA events on that stream) and the box statuses (host).
+static mdeos_status time_plan(mdeos_handle* h, const Plan& plan, int n, float* ms,
+                              std::vector<int>& status) {
+  const size_t nb = plan.boxes.size(), ni = plan.items.size();
+  const size_t off_items = (nb * sizeof(BoxDesc) + 255) & ~size_t(255);
+  const size_t in_bytes = off_items + ni * sizeof(WorkItem);
+  const size_t off_cnt = (in_bytes + 255) & ~size_t(255);
+  const size_t off_res = off_cnt + 256;
+  const size_t bytes = off_res + (size_t)n * sizeof(mdeos_result);
+  std::vector<char> host(in_bytes);
+  std::memcpy(host.data(), plan.boxes.data(), nb * sizeof(BoxDesc));
+  std::memcpy(host.data() + off_items, plan.items.data(), ni * sizeof(WorkItem));
+  mdeos_status st = ensure_scratch(h, (size_t)plan.grid * plan.nl_per_cta * sizeof(uint16_t));
+  if (st != MDEOS_OK) return st;
+  char* d = nullptr;
+  CK(cudaMalloc(&d, bytes));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, host.data(), in_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+  if (e == cudaSuccess)
+    e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni, (int*)(d + off_cnt),
+                         (mdeos_result*)(d + off_res), h->d_nl, plan.nl_per_cta, h->rp, plan.grid,
+                         plan.smem, h->stream, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+  std::vector<mdeos_result> res(n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(res.data(), d + off_res, (size_t)n * sizeof(mdeos_result),
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
+  h->launches += 1;
+  status.resize(n);
+  for (int i = 0; i < n; ++i) status[i] = plan.status[i] != MDEOS_OK ? plan.status[i] : res[i].status;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_autotune(mdeos_handle* h, const mdeos_request* reqs, int32_t n,
+                                       int32_t steps, double* table, int32_t max_out,
+                                       int32_t* n_out) {
+  if (!h || !reqs || n < 1 || steps < 2 * 10 || max_out < 0)
+    return fail(MDEOS_EINVAL, "bad autotune arguments");
+  std::lock_guard<std::mutex> lock(h->mu);
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));
+  // size classes: Verlet-path boxes grouped by atom count
+  std::map<int, std::vector<int>> cls;
+  std::map<int, int> per_cta;
+  for (int i = 0; i < n; ++i) {
+    const BoxPlan p = plan_box(reqs[i], h->cfg, i, true, nullptr);
+    if (p.status != MDEOS_OK || p.bd.path != PATH_NLIST) continue;
+    cls[reqs[i].natoms].push_back(i);
+    per_cta[reqs[i].natoms] = p.big ? 1 : std::min(kCtaThreads / (p.warps * 32), kMaxBoxesPerItem);
+  }
+  const float cand[] = {0.2f, 0.25f, 0.3f, 0.35f, 0.4f, 0.5f};
+  int k_out = 0;
+  for (const auto& kv : cls) {
+    // one full wave of the GPU: nSM CTAs, each with as many boxes as an item holds
+    const int count = h->nsm * per_cta[kv.first];
+    std::vector<mdeos_request> trial(count);
+    for (int i = 0; i < count; ++i) {
+      trial[i] = reqs[kv.second[i % kv.second.size()]];
+      trial[i].steps_equil = steps / 2;
+      trial[i].steps_avg = steps - steps / 2;
+      trial[i].element_id = 0;
+      trial[i].seed += (uint64_t)i;
+    }
+    float best = 0.f, best_skin = 0.f;
+    for (float sk : cand) {
+      mdeos_config c = h->cfg;
+      c.skin = sk;
+      Plan plan;
+      if (make_plan(trial.data(), count, c, h->nsm, h->smem_max, plan) != MDEOS_OK) continue;
+      float ms = 0.f;
+      std::vector<int> status;
+      const mdeos_status st = time_plan(h, plan, count, &ms, status);
+      if (st != MDEOS_OK) return st;
+      bool ok = true;
+      for (int v : status) ok = ok && v == MDEOS_OK;
+      if (ok && (best_skin == 0.f || ms < best)) {
+        best = ms;
+        best_skin = sk;
+      }
+    }
+    if (best_skin > 0.f) {
+      h->tuned_skin[kv.first] = best_skin;
+      if (table && k_out < max_out) {
+        table[3 * k_out] = kv.first;
+        table[3 * k_out + 1] = best_skin;
+        table[3 * k_out + 2] = best / count;  // ms of GPU time per box (one wave)
+        ++k_out;
+      }
+    }
+  }
+  if (n_out) *n_out = k_out;
+  return MDEOS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // warm-start store
 
 extern "C" mdeos_status mdeos_warm_export(mdeos_handle* h, uint64_t element_id, int32_t natoms,
@@ -959,7 +1081,7 @@ mdeos_status eval_into_device(mdeos_handle* h, const mdeos_request* reqs, int n,
   CK(cudaSetDevice(h->device));
   CK(cudaStreamSynchronize(h->stream));
   Plan plan;
-  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan);
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin);
   if (st != MDEOS_OK) return st;
   assign_warm(h, plan, reqs);
   const size_t nb = plan.boxes.size(), ni = plan.items.size();
@@ -1024,7 +1146,7 @@ void planning_result_of(mdeos_result& r, int status, const mdeos_request& q) {
 // Planning with the handle's configuration and device limits (no warm store).
 mdeos_status plan_requests(const mdeos_handle* h, const mdeos_request* reqs, int n, PlanOut& out) {
   Plan plan;
-  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan);
+  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin);
   if (st != MDEOS_OK) return st;
   out.boxes.swap(plan.boxes);
   out.items.swap(plan.items);
