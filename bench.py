@@ -212,8 +212,10 @@ def ours(args):
     tune = None
     if not args.no_autotune:  # measured skin per atom count (outside the timed region)
         t_tune = time.perf_counter()
+        l0 = m.mdeos_stats(h)["launches"]
         tab = m.mdeos_autotune(h, reqs, steps=200)
         tune = {"seconds": time.perf_counter() - t_tune,
+                "trial_launches": m.mdeos_stats(h)["launches"] - l0,
                 "skin_by_natoms": {str(int(r[0])): float(r[1]) for r in tab}}
     b = m.mdeos_batch_create(h, reqs)
     info = m.mdeos_batch_info(b)
