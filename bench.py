@@ -31,17 +31,19 @@ FLOPS_PER_PAIR = 27  # nominal FP32 flops per in-cutoff pair
 
 # DRAM traffic of one eos_batch_kernel launch (dram__bytes_read + write) from the
 # ncu capture summarised in profiles/eos_batch_kernel_config2.md, keyed by a hash
-# of the kernel sources: any change to csrc/ invalidates it (reported as null).
+# of the sources that build that kernel and plan its launch: any change to them
+# invalidates it (reported as null).
+BATCH_KERNEL_SOURCES = ("mdeos_internal.h", "mdeos_device.cuh", "mdeos_big.cuh",
+                        "mdeos_batch.cu", "mdeos_api.cu", "mdeos_host.h")
 MEASURED_TRAFFIC = {"csrc_sha256_12": "478e341e1098", "bytes_per_launch": 3.84e11,
                     "executed_fp32_frac": 0.180}
 
 
 def kernel_source_hash() -> str:
-    import glob
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2508_06012_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in BATCH_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2508_06012_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 WORKLOAD = ("batched uneven MD-EOS: 4096 LJ boxes, N=4n^3 n~U{3..10} (108-4000 atoms), "
             "rho*~U[0.3,1.2], T*~logU[0.7,3.0], rc=2.5, dt=0.005, 1000 lifting + 1000 "
@@ -679,6 +681,27 @@ def surrogate(args):
     out["inference"] = {"queries": len(xi), "seconds": t_inf, "queries_per_s": len(xi) / t_inf,
                         "tflops_incl_host_copies": flops / t_inf / 1e12,
                         "bf16_peak_tflops": peaks.get("bf16_tflops")}
+    # device-resident inference (inputs and outputs in HBM), CUDA events on the launching
+    # stream, fused tcgen05 kernel vs the layered mma.sync path
+    xd = torch.from_numpy(xi).cuda()
+    md, sdd = torch.zeros_like(xd), torch.zeros_like(xd)
+    st = torch.cuda.Stream()
+    dev = {}
+    for name, path in (("tcgen05_fused", m.SURROGATE_INFER_TC), ("mma_layered", m.SURROGATE_INFER_MMA)):
+        big.set_infer_path(path)
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                big.infer_device(xd, md, sdd, stream=st)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(st)
+            for _ in range(5):
+                big.infer_device(xd, md, sdd, stream=st)
+            ev1.record(st)
+        st.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3 / 5
+        dev[name] = {"ms": sec * 1e3, "queries_per_s": len(xi) / sec,
+                     "tflops": flops / sec / 1e12}
+    out["inference"]["device_resident"] = dev
     big.close()
     sg.close()
     clk = clocks.stop()

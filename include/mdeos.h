@@ -427,9 +427,29 @@ mdeos_status mdeos_surrogate_train(mdeos_surrogate* s, const double* x, const do
 
 /* Ensemble prediction for n inputs (host double[n][2]): mean and population standard
  * deviation over the models of (P, T) (host double[n][2] each, may be NULL) and the
- * per-model normalised outputs (host float[n_models][n][2], may be NULL). */
+ * per-model normalised outputs (host float[n_models][n][2], may be NULL).
+ * Synchronous.  ETIMEDOUT if a tensor-core completion wait ran out (about 1 s). */
 mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double* x, int32_t n,
                                      double* mean, double* sd, float* per_model);
+
+/* Inference paths.  TC (default): one fused kernel per 128 inputs and model; layer 1
+ * on the CUDA cores, the two 128 x 128 layers as tcgen05.mma with the accumulator in
+ * tensor memory, bias + tanh + the output layer in the epilogue.  MMA: the layered
+ * path the training step uses (mma.sync GEMMs and elementwise kernels, activations
+ * through device memory).  Both apply the same bf16 roundings; they differ only in
+ * the FP32 summation order.  EINVAL for any other value. */
+#define MDEOS_SURROGATE_INFER_TC 0
+#define MDEOS_SURROGATE_INFER_MMA 1
+mdeos_status mdeos_surrogate_set_infer_path(mdeos_surrogate* s, int32_t path);
+
+/* Prediction on device arrays, asynchronous on `stream` (cudaStream_t; NULL = the
+ * handle's stream): d_x device double[n][2] = (rho, e) in; d_mean and d_sd device
+ * double[n][2] = ensemble mean and spread of (P, T) out (all caller-owned, non-NULL
+ * when n > 0).  Uses the surrogate's scratch: serialise with its other calls.  A
+ * tensor-core wait that ran out writes NaN for its inputs (and makes the next
+ * mdeos_surrogate_predict return ETIMEDOUT).  Errors: EINVAL, ECUDA. */
+mdeos_status mdeos_surrogate_infer_device(mdeos_surrogate* s, const double* d_x, int32_t n,
+                                          double* d_mean, double* d_sd, void* stream);
 
 /* Gated evaluation of n requests: where sd(P) <= threshold * max(|mean P|, 1) the
  * result is the ensemble mean (path = -2, P_se / T_se = the ensemble spread), else

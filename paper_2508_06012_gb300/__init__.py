@@ -36,10 +36,12 @@ EXPORTED = [
     "mdeos_serve_enqueue", "mdeos_serve_completed", "mdeos_serve_stats", "mdeos_serve_destroy",
     "mdeos_surrogate_create", "mdeos_surrogate_set_params", "mdeos_surrogate_get_params",
     "mdeos_surrogate_grads", "mdeos_surrogate_train", "mdeos_surrogate_predict",
-    "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_debug_gemm_bf16",
+    "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_surrogate_set_infer_path",
+    "mdeos_surrogate_infer_device", "mdeos_debug_gemm_bf16",
     "mdeos_autotune",
 ]
 SURROGATE_NPARAM = 33666
+SURROGATE_INFER_TC, SURROGATE_INFER_MMA = 0, 1
 
 
 class mdeos_config(ctypes.Structure):
@@ -192,6 +194,8 @@ def lib():
         L.mdeos_surrogate_predict.argtypes = [vp, vp, i32, vp, vp, vp]
         L.mdeos_surrogate_gated_eval.argtypes = [vp, vp, i32, d, i32, vp, vp]
         L.mdeos_surrogate_destroy.argtypes = [vp]
+        L.mdeos_surrogate_set_infer_path.argtypes = [vp, i32]
+        L.mdeos_surrogate_infer_device.argtypes = [vp, vp, i32, vp, vp, vp]
         L.mdeos_autotune.argtypes = [vp, vp, i32, i32, vp, i32, P(i32)]
         i64 = ctypes.c_int64
         L.mdeos_debug_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i64, i64, i64, i64, i64,
@@ -580,6 +584,21 @@ class Surrogate:
         pm = np.zeros((self.E, n, 2), dtype=np.float32) if per_model else None
         _check(lib().mdeos_surrogate_predict(self.s, _vp(x), n, _vp(mean), _vp(sd), _vp(pm)))
         return (mean, sd, pm) if per_model else (mean, sd)
+
+    def set_infer_path(self, path: int):
+        """SURROGATE_INFER_TC (fused tcgen05 kernel, default) or SURROGATE_INFER_MMA."""
+        _check(lib().mdeos_surrogate_set_infer_path(self.s, path))
+
+    def infer_device(self, x, mean, sd, stream=None):
+        """Asynchronous prediction on device tensors: x (n, 2) float64 (rho, e) in;
+        mean and sd (n, 2) float64 out; on `stream` (torch.cuda.Stream) or the handle's."""
+        import torch
+        for t in (x, mean, sd):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                    and tuple(t.shape) == (x.shape[0], 2)):
+                raise ValueError("infer_device wants contiguous (n, 2) float64 CUDA tensors")
+        _check(lib().mdeos_surrogate_infer_device(self.s, _dptr(x), x.shape[0], _dptr(mean),
+                                                  _dptr(sd), _stream_ptr(stream)))
 
     def gated_eval(self, reqs, threshold, md_natoms=0):
         arr = as_requests(reqs)

@@ -301,6 +301,211 @@ __global__ void mlp_ensemble(const float* Y, int B, int E, double ym0, double ym
   sd[i] = sqrt(fmax(q / E - a * a, 0.0));
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference on the 5th-generation tensor cores: one CTA of 128 threads takes
+// 128 samples of one model.  Layer 1 (2 -> 128) runs on the CUDA cores and writes h1
+// into shared memory; layers 2 and 3 are tcgen05.mma (M = N = 128, K = 128 in steps
+// of 16, bf16 x bf16 -> fp32) with the accumulator in tensor memory (128 columns),
+// completion signalled on an mbarrier; each thread reads its sample's row back
+// (tcgen05.ld, 32 columns at a time), adds the bias, applies tanh and writes the next
+// operand, and after layer 3 evaluates the 128 -> 2 output layer in registers.
+//
+// Operand layout in shared memory (no swizzle, K contiguous): 8 x 8 "core matrices"
+// of 128 bytes; element (r, k) at (r / 8) * SBO + (k / 8) * LBO + (r % 8) * 16 +
+// (k % 8) * 2 with LBO = 128 B (next core matrix along K) and SBO = 2048 B (next
+// 8-row group).  Every address an MMA can form stays inside its 32 KB tile.
+
+constexpr int kTcRows = 128;                   // samples per CTA (TMEM lanes)
+constexpr uint32_t kLbo = 128, kSbo = 2048;    // bytes
+constexpr int kTcTile = kH * kH * 2;           // 32 KB per operand tile
+constexpr int kTcSmem = 3 * kTcTile + 1024 + 64;
+
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {
+  return (uint32_t)((r >> 3) * kSbo + (k >> 3) * kLbo + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start, LBO, SBO (all >> 4), version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kSbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, N = M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
+                            ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long tc_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait on an mbarrier phase for at most ~1 s; false if it did not complete
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const unsigned long long t0 = tc_clock_ns();
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && tc_clock_ns() - t0 > 1000000000ull) break;
+  }
+  return false;
+}
+
+// 32 consecutive fp32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(const float* X, const float* P,
+                                                               const __nv_bfloat16* W1b,
+                                                               const __nv_bfloat16* W2b,
+                                                               const __nv_bfloat16* W3b,
+                                                               const __nv_bfloat16* W4b, float* Y,
+                                                               int B, int* err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const uint32_t sbase = ((uint32_t)__cvta_generic_to_shared(tsm) + 1023u) & ~1023u;
+  unsigned char* gbase = tsm + (sbase - (uint32_t)__cvta_generic_to_shared(tsm));
+  const uint32_t sA = sbase, sW2 = sbase + kTcTile, sW3 = sbase + 2 * kTcTile;
+  const uint32_t sMbar = sbase + 3 * kTcTile, sTmem = sMbar + 8;
+  unsigned char* gA = gbase;
+  const int e = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
+  const int b0 = blockIdx.x * kTcRows;
+  const float* p = P + (long long)e * kNParam;
+  // weights of this model into the canonical layout, 16 bytes at a time; consecutive
+  // threads fill consecutive 16-byte rows of the core matrices (no bank conflicts)
+  for (int q = tid; q < kH * kH / 8; q += kTcRows) {
+    const int n = (q >> 7) * 8 + (q & 7), k = ((q >> 3) & 15) * 8;
+    const uint4 w2 = *reinterpret_cast<const uint4*>(W2b + (long long)e * kH * kH + n * kH + k);
+    const uint4 w3 = *reinterpret_cast<const uint4*>(W3b + (long long)e * kH * kH + n * kH + k);
+    *reinterpret_cast<uint4*>(gbase + kTcTile + tc_off(n, k)) = w2;
+    *reinterpret_cast<uint4*>(gbase + 2 * kTcTile + tc_off(n, k)) = w3;
+  }
+  // layer 1 on the CUDA cores: this thread's sample (row) -> h1 (bf16) in tile A
+  const int m = tid, b = b0 + m;
+  const float x0 = b < B ? X[2 * b] : 0.f, x1 = b < B ? X[2 * b + 1] : 0.f;
+  for (int c = 0; c < kH; c += 8) {  // 8 units = one 16-byte core-matrix row
+    uint4 pk;
+    __nv_bfloat162* h2p = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const __nv_bfloat16* w = W1b + (long long)e * 2 * kH + 2 * (c + j);
+      const float z0 =
+          x0 * __bfloat162float(w[0]) + x1 * __bfloat162float(w[1]) + p[kOffB1 + c + j];
+      const float z1 =
+          x0 * __bfloat162float(w[2]) + x1 * __bfloat162float(w[3]) + p[kOffB1 + c + j + 1];
+      h2p[j >> 1] = __floats2bfloat162_rn(tanhf(z0), tanhf(z1));
+    }
+    *reinterpret_cast<uint4*>(gA + tc_off(m, c)) = pk;
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sMbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // 128 TMEM columns: the 128 x 128 fp32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(sTmem), "r"(kH) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands -> tensor core
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 3 * kTcTile + 8);
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  bool ok = true;
+  int pending = -1;  // phase of an MMA group not yet seen complete
+  float y0 = 0.f, y1 = 0.f;
+  for (int layer = 0; layer < 2; ++layer) {
+    if (tid == 0) {
+      const uint32_t sW = layer == 0 ? sW2 : sW3;
+#pragma unroll
+      for (int ks = 0; ks < kH / 16; ++ks)  // K step of 16 = two core matrices along K
+        tc_mma(tmem, tc_desc(sA + ks * 2 * kLbo), tc_desc(sW + ks * 2 * kLbo), ks > 0);
+      tc_commit(sMbar);
+    }
+    __syncwarp();
+    const bool done = mbar_wait(sMbar, (uint32_t)layer);
+    ok = __syncthreads_and(done) != 0;  // the same decision in every thread
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+      pending = layer;
+      break;
+    }
+    const int off_b = layer == 0 ? kOffB2 : kOffB3;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float v[32];
+      tc_ld32(trow + (uint32_t)c0, v);
+      if (layer == 0) {  // h2 = bf16(tanh(z2 + b2)) -> tile A (its MMA has completed)
+#pragma unroll
+        for (int j8 = 0; j8 < 32; j8 += 8) {
+          uint4 pk;
+          __nv_bfloat162* h2p = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+          for (int j = 0; j < 8; j += 2)
+            h2p[j >> 1] = __floats2bfloat162_rn(tanhf(v[j8 + j] + p[off_b + c0 + j8 + j]),
+                                                tanhf(v[j8 + j + 1] + p[off_b + c0 + j8 + j + 1]));
+          *reinterpret_cast<uint4*>(gA + tc_off(m, c0 + j8)) = pk;
+        }
+      } else {           // h3 and the output layer, in registers
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float h = __bfloat162float(__float2bfloat16_rn(tanhf(v[j] + p[off_b + c0 + j])));
+          y0 = fmaf(__bfloat162float(W4b[(long long)e * 2 * kH + c0 + j]), h, y0);
+          y1 = fmaf(__bfloat162float(W4b[(long long)e * 2 * kH + kH + c0 + j]), h, y1);
+        }
+      }
+    }
+    if (layer == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (b < B) {  // a wait that ran out leaves NaN outputs for this tile
+    Y[((long long)e * B + b) * 2] = ok ? y0 + p[kOffB4] : __int_as_float(0x7fc00000);
+    Y[((long long)e * B + b) * 2 + 1] = ok ? y1 + p[kOffB4 + 1] : __int_as_float(0x7fc00000);
+  }
+  if (!ok) {  // let the MMAs in flight finish (bounded) before the columns are freed
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(sMbar, (uint32_t)pending);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  __syncwarp();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kH)
+                 : "memory");
+}
+
 }  // namespace mdeos
 
 using namespace mdeos;
@@ -316,6 +521,9 @@ struct mdeos_surrogate {
   float *Z = nullptr, *dZf = nullptr, *X = nullptr, *T = nullptr, *Y = nullptr, *dY = nullptr;
   float* loss = nullptr;
   double *Xp = nullptr, *mean = nullptr, *sd = nullptr;
+  int* err = nullptr;  // set by the fused kernel when an MMA wait ran out
+  int infer_path = MDEOS_SURROGATE_INFER_TC;
+  bool tc_ready = false;
   std::vector<void*> allocs;
 };
 
@@ -431,6 +639,7 @@ extern "C" mdeos_status mdeos_surrogate_create(mdeos_handle* h, int32_t n_models
   dalloc((void**)&s->Xp, (size_t)max_batch * 2 * 8);
   dalloc((void**)&s->mean, (size_t)max_batch * 2 * 8);
   dalloc((void**)&s->sd, (size_t)max_batch * 2 * 8);
+  dalloc((void**)&s->err, 256);
   if (e != cudaSuccess) {
     mdeos_surrogate_destroy(s);
     return set_error(MDEOS_ECUDA, std::string("surrogate_create: ") + cudaGetErrorString(e));
@@ -589,6 +798,57 @@ extern "C" mdeos_status mdeos_surrogate_train(mdeos_surrogate* s, const double* 
   return MDEOS_OK;
 }
 
+// inference of B <= maxB inputs (device FP64 [B][2]) -> per-model s->Y and the ensemble
+// mean / sd (device FP64 [B][2]) on stream st
+static cudaError_t infer(mdeos_surrogate* s, const double* dx, int B, double* dmean, double* dsd,
+                         int path, cudaStream_t st) {
+  mlp_normalise<<<nblk(B), 256, 0, st>>>(dx, s->X, B, s->norm[0], s->norm[1], s->norm[2],
+                                         s->norm[3]);
+  cudaError_t e;
+  if (path == MDEOS_SURROGATE_INFER_MMA) {
+    e = forward(s, B, nullptr, st);
+    count_launch(s->h, 9);
+  } else {
+    if (!s->tc_ready) {
+      e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kTcSmem);
+      if (e != cudaSuccess) return e;
+      s->tc_ready = true;
+    }
+    dim3 grid((B + kTcRows - 1) / kTcRows, s->E);
+    mlp_infer_tc_kernel<<<grid, kTcRows, kTcSmem, st>>>(s->X, s->P, s->W1b, s->W2b, s->W3b,
+                                                          s->W4b, s->Y, B, s->err);
+    e = cudaGetLastError();
+    count_launch(s->h, 3);
+  }
+  if (e != cudaSuccess) return e;
+  mlp_ensemble<<<nblk(2 * B), 256, 0, st>>>(s->Y, B, s->E, s->norm[4], s->norm[5], s->norm[6],
+                                            s->norm[7], dmean, dsd);
+  return cudaGetLastError();
+}
+
+extern "C" mdeos_status mdeos_surrogate_set_infer_path(mdeos_surrogate* s, int32_t path) {
+  if (!s || (path != MDEOS_SURROGATE_INFER_TC && path != MDEOS_SURROGATE_INFER_MMA))
+    return set_error(MDEOS_EINVAL, "bad inference path");
+  s->infer_path = path;
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_infer_device(mdeos_surrogate* s, const double* d_x,
+                                                     int32_t n, double* d_mean, double* d_sd,
+                                                     void* stream) {
+  if (!s || (n > 0 && (!d_x || !d_mean || !d_sd)) || n < 0)
+    return set_error(MDEOS_EINVAL, "bad infer_device arguments");
+  SCK(cudaSetDevice(handle_device(s->h)));
+  cudaStream_t st = stream ? (cudaStream_t)stream : handle_stream(s->h);
+  for (int off = 0; off < n; off += s->maxB) {
+    const int B = std::min(s->maxB, n - off);
+    SCK(infer(s, d_x + 2 * (size_t)off, B, d_mean + 2 * (size_t)off, d_sd + 2 * (size_t)off,
+              s->infer_path, st));
+  }
+  return MDEOS_OK;
+}
+
 extern "C" mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double* x, int32_t n,
                                                 double* mean, double* sd, float* per_model) {
   if (!s || !x || n < 0) return set_error(MDEOS_EINVAL, "bad predict arguments");
@@ -597,13 +857,7 @@ extern "C" mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double
   for (int off = 0; off < n; off += s->maxB) {
     const int B = std::min(s->maxB, n - off);
     SCK(cudaMemcpyAsync(s->Xp, x + 2 * (size_t)off, (size_t)B * 16, cudaMemcpyHostToDevice, st));
-    mlp_normalise<<<nblk(B), 256, 0, st>>>(s->Xp, s->X, B, s->norm[0], s->norm[1], s->norm[2],
-                                           s->norm[3]);
-    SCK(forward(s, B, nullptr, st));
-    mlp_ensemble<<<nblk(2 * B), 256, 0, st>>>(s->Y, B, s->E, s->norm[4], s->norm[5], s->norm[6],
-                                              s->norm[7], s->mean, s->sd);
-    SCK(cudaGetLastError());
-    count_launch(s->h, 9);
+    SCK(infer(s, s->Xp, B, s->mean, s->sd, s->infer_path, st));
     if (mean)
       SCK(cudaMemcpyAsync(mean + 2 * (size_t)off, s->mean, (size_t)B * 16, cudaMemcpyDeviceToHost, st));
     if (sd)
@@ -614,6 +868,11 @@ extern "C" mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double
                             (size_t)B * 8, cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
   }
+  int err = 0;
+  SCK(cudaMemcpyAsync(&err, s->err, 4, cudaMemcpyDeviceToHost, st));
+  SCK(cudaMemsetAsync(s->err, 0, 4, st));
+  SCK(cudaStreamSynchronize(st));
+  if (err) return set_error(MDEOS_ETIMEDOUT, "surrogate: a tensor-core wait ran out");
   return MDEOS_OK;
 }
 

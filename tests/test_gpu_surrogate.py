@@ -76,11 +76,14 @@ def _inputs(n, seed):
     return np.stack([rng.uniform(0.3, 1.2, n), rng.uniform(-5.0, 3.0, n)], axis=1)
 
 
-def test_forward_matches_oracle(m, h):
+@pytest.mark.parametrize("path", [0, 1], ids=["tcgen05", "mma"])
+def test_forward_matches_oracle(m, h, path):
+    """1000 inputs in chunks of 512: several 128-row tiles and a ragged tail."""
     p = _params(11)
     x = _inputs(1000, 12)
     with m.Surrogate(h, 4, 512, seed=1) as sg:
         sg.set_params(p, NORM)
+        sg.set_infer_path(path)
         mean, sd, pm = sg.predict(x, per_model=True)
     xn = (x - NORM[:2]) / NORM[2:4]
     ref16 = np.array([S.forward(p[e], xn)[0] for e in range(4)])
@@ -91,6 +94,47 @@ def test_forward_matches_oracle(m, h):
     phys = ref16 * NORM[6:8] + NORM[4:6]
     assert np.allclose(mean, phys.mean(axis=0), atol=5e-2)
     assert np.allclose(sd, phys.std(axis=0), atol=5e-2)
+
+
+@pytest.mark.parametrize("E,n,maxb", [(1, 1, 64), (16, 129, 128), (3, 127, 4096), (4, 777, 300)])
+def test_tensor_core_path_matches_layered_path(m, h, E, n, maxb):
+    """The fused tcgen05 kernel against the layered mma.sync path on the same weights:
+    the same bf16 roundings, another FP32 summation order, so outputs agree to FP32
+    rounding except where a hidden unit rounds one bf16 ulp apart."""
+    p = _params(51, E)
+    x = _inputs(n, 52)
+    out = {}
+    with m.Surrogate(h, E, maxb, seed=1) as sg:
+        sg.set_params(p, NORM)
+        for path in (m.SURROGATE_INFER_TC, m.SURROGATE_INFER_MMA):
+            sg.set_infer_path(path)
+            out[path] = sg.predict(x, per_model=True)
+        with pytest.raises(m.MdeosError):
+            sg.set_infer_path(2)
+    a, b = out[m.SURROGATE_INFER_TC][2], out[m.SURROGATE_INFER_MMA][2]
+    assert np.isfinite(a).all() and a.shape == (E, n, 2)
+    d = np.abs(a.astype(np.float64) - b)
+    assert d.max() <= 2e-2 and d.mean() <= 1e-4, (d.max(), d.mean())
+    assert np.median(d) <= 1e-5
+
+
+def test_device_inference_equals_host_prediction(m, h):
+    import torch
+    p = _params(61)
+    x = _inputs(5000, 62)
+    with m.Surrogate(h, 4, 2048, seed=1) as sg:
+        sg.set_params(p, NORM)
+        mean, sd = sg.predict(x)
+        xd = torch.from_numpy(x).cuda()
+        md = torch.zeros_like(xd)
+        sdd = torch.zeros_like(xd)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            sg.infer_device(xd, md, sdd, stream=st)
+        st.synchronize()
+        sg.infer_device(xd[:0], md[:0], sdd[:0])          # empty input
+    assert md.cpu().numpy().tobytes() == mean.tobytes()
+    assert sdd.cpu().numpy().tobytes() == sd.tobytes()
 
 
 def test_gradients_match_oracle(m, h):
