@@ -35,8 +35,8 @@ FLOPS_PER_PAIR = 27  # nominal FP32 flops per in-cutoff pair
 # invalidates it (reported as null).
 BATCH_KERNEL_SOURCES = ("mdeos_internal.h", "mdeos_device.cuh", "mdeos_big.cuh",
                         "mdeos_batch.cu", "mdeos_api.cu", "mdeos_host.h")
-MEASURED_TRAFFIC = {"csrc_sha256_12": "478e341e1098", "bytes_per_launch": 3.84e11,
-                    "executed_fp32_frac": 0.180}
+MEASURED_TRAFFIC = {"csrc_sha256_12": "daf74e5d8a49", "bytes_per_launch": 7.56e11,
+                    "executed_fp32_frac": 0.197}
 
 
 def kernel_source_hash() -> str:
@@ -294,7 +294,7 @@ def ours(args):
         "traffic": (MEASURED_TRAFFIC["bytes_per_launch"]
                     if kernel_source_hash() == MEASURED_TRAFFIC["csrc_sha256_12"] else None),
         "traffic_note": "bytes per launch; ncu capture of a 456-box x 200-step case scaled by "
-                        "atom-steps (x90.5)",
+                        "atom-steps (x90.48)",
         "executed_fp32_frac_ncu": (MEASURED_TRAFFIC["executed_fp32_frac"]
                                    if kernel_source_hash() == MEASURED_TRAFFIC["csrc_sha256_12"]
                                    else None),
@@ -717,6 +717,99 @@ def surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+SURROGATE_INFER = ("surrogate inference: ensemble of 4 MLPs 2-128-128-128-2 (bf16 weights and "
+                   "activations, fp32 accumulation), random-init weights, (rho, e) queries "
+                   "resident in HBM, 2^18 per launch")
+
+
+def surrogate_infer(args):
+    """Inference throughput of the surrogate ensemble on device-resident queries: the
+    fused tcgen05 kernel (timed) against the layered mma.sync path (reported beside)."""
+    import torch
+
+    import paper_2508_06012_gb300 as m
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    m.build()
+    h = m.mdeos_create(m.mdeos_config_default(device=local))
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+    E, n, chunk = 4, args.queries, 1 << 18
+    sg = m.Surrogate(h, E, chunk, seed=3)
+    sg.set_params(None, np.array([0.75, -1.0, 0.25, 2.0, 1.5, 1.2, 2.0, 0.6]))
+    rng = np.random.default_rng(7)
+    xh = np.stack([rng.uniform(0.3, 1.2, n), rng.uniform(-5.0, 3.0, n)], axis=1)
+    xd = torch.from_numpy(xh).cuda()
+    md, sdd = torch.zeros_like(xd), torch.zeros_like(xd)
+    flops = E * n * 2.0 * (2 * 128 + 2 * 128 * 128 + 128 * 2)
+    st = torch.cuda.Stream()
+    clocks = ClockSampler(gpu_idx)
+    res = {}
+    l0 = m.mdeos_stats(h)["launches"]
+    for name, path in (("tcgen05_fused", m.SURROGATE_INFER_TC),
+                       ("mma_layered", m.SURROGATE_INFER_MMA)):
+        sg.set_infer_path(path)
+        with torch.cuda.stream(st):
+            for _ in range(args.warmup):
+                sg.infer_device(xd, md, sdd, stream=st)
+            st.synchronize()
+            if name == "tcgen05_fused":
+                clocks.start()
+                l0 = m.mdeos_stats(h)["launches"]
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(st)
+            for _ in range(args.steps):
+                sg.infer_device(xd, md, sdd, stream=st)
+            ev1.record(st)
+        st.synchronize()
+        if name == "tcgen05_fused":
+            clk = clocks.stop()
+            launches = m.mdeos_stats(h)["launches"] - l0
+        sec = ev0.elapsed_time(ev1) / 1e3 / args.steps
+        res[name] = {"ms_per_step": sec * 1e3, "queries_per_s": n / sec, "tflops": flops / sec / 1e12}
+    # end to end: host arrays through mdeos_surrogate_predict (copies in the timed region)
+    sg.set_infer_path(m.SURROGATE_INFER_TC)
+    sg.predict(xh[:chunk])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sg.predict(xh)
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    cpu = None
+    if not args.no_cpu:   # the FP64 oracle's forward pass on a bounded sample
+        from oracle import surrogate as S
+        p, nm = sg.get_params()
+        k = 20000
+        xn = (xh[:k] - nm[:2]) / nm[2:4]
+        t0 = time.perf_counter()
+        for e in range(E):
+            S.forward(p[e].astype(np.float64), xn)
+        tc = time.perf_counter() - t0
+        cpu = {"value": k / tc, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{k} queries x {E} models, numpy FP64 with bf16 rounding points"}
+    sg.close()
+    m.mdeos_destroy(h)
+    peaks = load_peaks()
+    peak = peaks.get("bf16_tflops")
+    tc = res["tcgen05_fused"]
+    line = {"metric": "surrogate queries/s (4-model ensemble)", "value": tc["queries_per_s"],
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tc["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic queries, random-init weights",
+            "config": {"workload": SURROGATE_INFER, "queries": n, "models": E,
+                       "l2": f"inputs and outputs {n * 48 / 2**20:.0f} MiB per step (larger "
+                             "than L2 at the default size); weights 256 KiB stay in L2"},
+            "roofline": {"bound": "tensor", "achieved": tc["tflops"], "peak": peak,
+                         "unit": "TFLOP/s", "frac": tc["tflops"] / peak if peak else None,
+                         "traffic": None, "kernel": "mlp_infer_tc_kernel",
+                         "peak_basis": "measured cuBLAS bf16 (burst)",
+                         "flops_basis": "2 x (2*128 + 2*128*128 + 128*2) per query and model"},
+            "paths": res,
+            "cpu_baseline": cpu,
+            "e2e": {"value": n / t_e2e, "unit": "queries/s", "h2d_bytes_per_step": n * 16,
+                    "d2h_bytes_per_step": n * 32, "api": "mdeos_surrogate_predict (host arrays)"},
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -733,7 +826,9 @@ def main():
     ap.add_argument("--val-n", type=int, default=2000, help="surrogate: validation queries")
     ap.add_argument("--test-n", type=int, default=4000, help="surrogate: test queries")
     ap.add_argument("--epochs", type=int, default=40, help="surrogate: training epochs")
-    ap.add_argument("--workload", choices=["uneven", "coupled", "serving", "surrogate"],
+    ap.add_argument("--queries", type=int, default=1 << 23, help="surrogate-infer: queries")
+    ap.add_argument("--workload", choices=["uneven", "coupled", "serving", "surrogate",
+                                           "surrogate-infer"],
                     default="uneven",
                     help="uneven: 4096-box batched EOS (default); coupled: MD-closed hydro; "
                          "serving: Poisson request stream")
@@ -747,6 +842,8 @@ def main():
         coupled(args)
     elif args.workload == "serving" and args.impl == "ours":
         serving(args)
+    elif args.workload == "surrogate-infer" and args.impl == "ours":
+        surrogate_infer(args)
     elif args.workload == "surrogate" and args.impl == "ours":
         surrogate(args)
     elif args.impl == "reference":

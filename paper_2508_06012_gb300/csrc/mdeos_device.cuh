@@ -168,7 +168,7 @@ __device__ inline BoxCtx make_ctx(const BoxDesc& bd, const RunParams& rp) {
 
 // pair constants, passed by value into the force pass
 struct LJ {
-  float rc2, eps4, eps24, sig6, ucut;
+  float rc2, eps4, eps24, eps48, sig6, ucut;
 };
 
 __device__ __forceinline__ LJ make_lj(const RunParams& rp) {
@@ -176,6 +176,7 @@ __device__ __forceinline__ LJ make_lj(const RunParams& rp) {
   c.rc2 = rp.rc2;
   c.eps4 = rp.eps4;
   c.eps24 = rp.eps24;
+  c.eps48 = 2.0f * rp.eps24;
   c.sig6 = rp.sig6;
   c.ucut = rp.ucut;
   return c;
@@ -189,7 +190,7 @@ __device__ __forceinline__ void lj_pair(float dx, float dy, float dz, bool ok, c
   bool in = ok && (r2 < c.rc2);
   float ir2 = rcp_approx(r2);
   float s6 = c.sig6 * ir2 * ir2 * ir2;
-  float fr = c.eps24 * s6 * fmaf(2.0f, s6, -1.0f) * ir2;
+  float fr = s6 * fmaf(c.eps48, s6, -c.eps24) * ir2;  // 24 eps s6 (2 s6 - 1) / r^2
   fr = in ? fr : 0.0f;
   fx = fmaf(fr, dx, fx);
   fy = fmaf(fr, dy, fy);
@@ -220,16 +221,16 @@ __device__ __forceinline__ float4 ld_shared4(uint32_t a) {
   return v;
 }
 
-// Round to the nearest integer (ties to even) on the FP32 adder: adding and
-// subtracting 1.5 * 2^23 leaves no fraction bits for |x| < 2^22.  Same result as
-// rintf, without the conversion pipe.
-__device__ __forceinline__ float round_nearest(float x) {
-  const float magic = 12582912.0f;
-  return __fsub_rn(__fadd_rn(x, magic), magic);
-}
-
+// Minimum image of a coordinate difference, d - L k with k the integer nearest to
+// d / L, on the FP32 pipe (no conversion instructions): one fused multiply-add adds
+// 1.5 * 2^23 to the exact product d * invL, which leaves no fraction bits for
+// |d * invL| < 2^22, and subtracting the constant again gives k (ties to even).  Only
+// where d is within rounding of +-L/2 can k differ from rintf(d * invL); such a pair
+// is beyond the cutoff on every path that uses one image (L >= 2 rc).
 __device__ __forceinline__ float min_img(float d, float L, float invL) {
-  return fmaf(-L, round_nearest(d * invL), d);
+  const float magic = 12582912.0f;
+  const float k = __fsub_rn(__fmaf_rn(d, invL, magic), magic);
+  return fmaf(-L, k, d);
 }
 
 // Verlet-list pair: minimum image across the periodic box; `ok` masks padding
