@@ -302,20 +302,21 @@ __global__ void mlp_ensemble(const float* Y, int B, int E, double ym0, double ym
 }
 
 // ---------------------------------------------------------------------------
-// Fused inference on the 5th-generation tensor cores: one CTA of 128 threads takes
-// 128 samples of one model.  Layer 1 (2 -> 128) runs on the CUDA cores and writes h1
-// into shared memory; layers 2 and 3 are tcgen05.mma (M = N = 128, K = 128 in steps
-// of 16, bf16 x bf16 -> fp32) with the accumulator in tensor memory (128 columns),
-// completion signalled on an mbarrier; each thread reads its sample's row back
-// (tcgen05.ld, 32 columns at a time), adds the bias, applies tanh and writes the next
-// operand, and after layer 3 evaluates the 128 -> 2 output layer in registers.
+// Fused inference on the 5th-generation tensor cores, in tiles of 128 samples of one
+// model.  Layer 1 (2 -> 128) runs on the CUDA cores and writes h1 into shared memory;
+// layers 2 and 3 are tcgen05.mma (M = N = 128, K = 128 in steps of 16, bf16 x bf16 ->
+// fp32) with the accumulator in tensor memory (128 columns), completion signalled on
+// an mbarrier; threads read their row back (tcgen05.ld, 32 columns at a time), add
+// the bias, apply tanh and write the next operand into the same tile; the 128 -> 2
+// output layer reads h3 back from shared memory.
 //
 // Operand layout in shared memory (no swizzle, K contiguous): 8 x 8 "core matrices"
 // of 128 bytes; element (r, k) at (r / 8) * SBO + (k / 8) * LBO + (r % 8) * 16 +
 // (k % 8) * 2 with LBO = 128 B (next core matrix along K) and SBO = 2048 B (next
 // 8-row group).  Every address an MMA can form stays inside its 32 KB tile.
 
-constexpr int kTcRows = 128;                   // samples per CTA (TMEM lanes)
+constexpr int kTcRows = 128;                   // samples per tile (TMEM lanes)
+constexpr int kTcThreads = 256;                // two threads per row (column halves)
 constexpr uint32_t kLbo = 128, kSbo = 2048;    // bytes
 constexpr int kTcTile = kH * kH * 2;           // 32 KB per operand tile
 constexpr int kTcSmem = 3 * kTcTile + 1024 + 64;
@@ -385,12 +386,26 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(const float* X, const float* P,
-                                                               const __nv_bfloat16* W1b,
-                                                               const __nv_bfloat16* W2b,
-                                                               const __nv_bfloat16* W3b,
-                                                               const __nv_bfloat16* W4b, float* Y,
-                                                               int B, int* err) {
+// bf16(tanh(z + bias)) of 8 consecutive units, packed as one 16-byte core-matrix row
+__device__ __forceinline__ uint4 tanh_pack8(const float* z, const float* bias) {
+  uint4 pk;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+  for (int j = 0; j < 8; j += 2)
+    h[j >> 1] = __floats2bfloat162_rn(tanhf(z[j] + bias[j]), tanhf(z[j + 1] + bias[j + 1]));
+  return pk;
+}
+
+// Persistent: grid (CTAs per model, models).  The CTA stages its model's W2 and W3
+// once, then takes 128-input tiles tile = blockIdx.x, + gridDim.x, ...  Thread t
+// serves row m = t % 128 (TMEM lane m) and column half t / 128: warps w and w + 4
+// read the same 32 lanes, columns 0-63 and 64-127.
+__global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* X, const float* P,
+                                                                  const __nv_bfloat16* W1b,
+                                                                  const __nv_bfloat16* W2b,
+                                                                  const __nv_bfloat16* W3b,
+                                                                  const __nv_bfloat16* W4b,
+                                                                  float* Y, int B, int* err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const uint32_t sbase = ((uint32_t)__cvta_generic_to_shared(tsm) + 1023u) & ~1023u;
   unsigned char* gbase = tsm + (sbase - (uint32_t)__cvta_generic_to_shared(tsm));
@@ -398,33 +413,19 @@ __global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(const float* X, c
   const uint32_t sMbar = sbase + 3 * kTcTile, sTmem = sMbar + 8;
   unsigned char* gA = gbase;
   const int e = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
-  const int b0 = blockIdx.x * kTcRows;
+  const int m = tid & (kTcRows - 1), half = tid >> 7, c_lo = half * (kH / 2);
+  const int ntiles = (B + kTcRows - 1) / kTcRows;
   const float* p = P + (long long)e * kNParam;
+  const __nv_bfloat16* w1 = W1b + (long long)e * 2 * kH;
+  const __nv_bfloat16* w4 = W4b + (long long)e * 2 * kH + half * kH;  // output unit = half
   // weights of this model into the canonical layout, 16 bytes at a time; consecutive
   // threads fill consecutive 16-byte rows of the core matrices (no bank conflicts)
-  for (int q = tid; q < kH * kH / 8; q += kTcRows) {
+  for (int q = tid; q < kH * kH / 8; q += kTcThreads) {
     const int n = (q >> 7) * 8 + (q & 7), k = ((q >> 3) & 15) * 8;
-    const uint4 w2 = *reinterpret_cast<const uint4*>(W2b + (long long)e * kH * kH + n * kH + k);
-    const uint4 w3 = *reinterpret_cast<const uint4*>(W3b + (long long)e * kH * kH + n * kH + k);
-    *reinterpret_cast<uint4*>(gbase + kTcTile + tc_off(n, k)) = w2;
-    *reinterpret_cast<uint4*>(gbase + 2 * kTcTile + tc_off(n, k)) = w3;
-  }
-  // layer 1 on the CUDA cores: this thread's sample (row) -> h1 (bf16) in tile A
-  const int m = tid, b = b0 + m;
-  const float x0 = b < B ? X[2 * b] : 0.f, x1 = b < B ? X[2 * b + 1] : 0.f;
-  for (int c = 0; c < kH; c += 8) {  // 8 units = one 16-byte core-matrix row
-    uint4 pk;
-    __nv_bfloat162* h2p = reinterpret_cast<__nv_bfloat162*>(&pk);
-#pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-      const __nv_bfloat16* w = W1b + (long long)e * 2 * kH + 2 * (c + j);
-      const float z0 =
-          x0 * __bfloat162float(w[0]) + x1 * __bfloat162float(w[1]) + p[kOffB1 + c + j];
-      const float z1 =
-          x0 * __bfloat162float(w[2]) + x1 * __bfloat162float(w[3]) + p[kOffB1 + c + j + 1];
-      h2p[j >> 1] = __floats2bfloat162_rn(tanhf(z0), tanhf(z1));
-    }
-    *reinterpret_cast<uint4*>(gA + tc_off(m, c)) = pk;
+    const uint4 a2 = *reinterpret_cast<const uint4*>(W2b + (long long)e * kH * kH + n * kH + k);
+    const uint4 a3 = *reinterpret_cast<const uint4*>(W3b + (long long)e * kH * kH + n * kH + k);
+    *reinterpret_cast<uint4*>(gbase + kTcTile + tc_off(n, k)) = a2;
+    *reinterpret_cast<uint4*>(gbase + 2 * kTcTile + tc_off(n, k)) = a3;
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sMbar) : "memory");
@@ -435,68 +436,84 @@ __global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(const float* X, c
                  ::"r"(sTmem), "r"(kH) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands -> tensor core
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 3 * kTcTile + 8);
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  // this thread's lane quarter (warp % 4) and column half
+  const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c_lo;
+  uint32_t commits = 0;  // MMA groups committed so far (mbarrier phase parity)
   bool ok = true;
-  int pending = -1;  // phase of an MMA group not yet seen complete
-  float y0 = 0.f, y1 = 0.f;
-  for (int layer = 0; layer < 2; ++layer) {
-    if (tid == 0) {
-      const uint32_t sW = layer == 0 ? sW2 : sW3;
-#pragma unroll
-      for (int ks = 0; ks < kH / 16; ++ks)  // K step of 16 = two core matrices along K
-        tc_mma(tmem, tc_desc(sA + ks * 2 * kLbo), tc_desc(sW + ks * 2 * kLbo), ks > 0);
-      tc_commit(sMbar);
-    }
-    __syncwarp();
-    const bool done = mbar_wait(sMbar, (uint32_t)layer);
-    ok = __syncthreads_and(done) != 0;  // the same decision in every thread
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) {
-      pending = layer;
-      break;
-    }
-    const int off_b = layer == 0 ? kOffB2 : kOffB3;
+  int tile = blockIdx.x;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int b = tile * kTcRows + m;
+    // layer 1 on the CUDA cores: this row's units c_lo .. c_lo + 63 -> tile A
+    const float x0 = b < B ? X[2 * b] : 0.f, x1 = b < B ? X[2 * b + 1] : 0.f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < kH; c0 += 32) {
-      float v[32];
-      tc_ld32(trow + (uint32_t)c0, v);
-      if (layer == 0) {  // h2 = bf16(tanh(z2 + b2)) -> tile A (its MMA has completed)
+    for (int c = c_lo; c < c_lo + kH / 2; c += 8) {
+      float z[8];
 #pragma unroll
-        for (int j8 = 0; j8 < 32; j8 += 8) {
-          uint4 pk;
-          __nv_bfloat162* h2p = reinterpret_cast<__nv_bfloat162*>(&pk);
+      for (int j = 0; j < 8; ++j)
+        z[j] = x0 * __bfloat162float(w1[2 * (c + j)]) + x1 * __bfloat162float(w1[2 * (c + j) + 1]);
+      *reinterpret_cast<uint4*>(gA + tc_off(m, c)) = tanh_pack8(z, p + kOffB1 + c);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // h1 -> tensor core
+    __syncthreads();
+    for (int layer = 0; layer < 2; ++layer) {
+      if (tid == 0) {
+        const uint32_t sW = layer == 0 ? sW2 : sW3;
 #pragma unroll
-          for (int j = 0; j < 8; j += 2)
-            h2p[j >> 1] = __floats2bfloat162_rn(tanhf(v[j8 + j] + p[off_b + c0 + j8 + j]),
-                                                tanhf(v[j8 + j + 1] + p[off_b + c0 + j8 + j + 1]));
-          *reinterpret_cast<uint4*>(gA + tc_off(m, c0 + j8)) = pk;
-        }
-      } else {           // h3 and the output layer, in registers
+        for (int ks = 0; ks < kH / 16; ++ks)  // K step of 16 = two core matrices along K
+          tc_mma(tmem, tc_desc(sA + ks * 2 * kLbo), tc_desc(sW + ks * 2 * kLbo), ks > 0);
+        tc_commit(sMbar);
+      }
+      __syncwarp();
+      const bool done = mbar_wait(sMbar, commits & 1u);
+      ++commits;
+      ok = __syncthreads_and(done) != 0;  // the same decision in every thread
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) break;
+      // epilogue: h = bf16(tanh(z + b)) of this row's 64 units -> tile A (the MMA that
+      // read it has completed): h2 feeds layer 3, h3 the output layer
+      const float* bias = p + (layer == 0 ? kOffB2 : kOffB3) + c_lo;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kH / 2; c0 += 32) {
+        float v[32];
+        tc_ld32(tq + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float h = __bfloat162float(__float2bfloat16_rn(tanhf(v[j] + p[off_b + c0 + j])));
-          y0 = fmaf(__bfloat162float(W4b[(long long)e * 2 * kH + c0 + j]), h, y0);
-          y1 = fmaf(__bfloat162float(W4b[(long long)e * 2 * kH + kH + c0 + j]), h, y1);
-        }
+        for (int j8 = 0; j8 < 32; j8 += 8)
+          *reinterpret_cast<uint4*>(gA + tc_off(m, c_lo + c0 + j8)) =
+              tanh_pack8(v + j8, bias + c0 + j8);
+      }
+      if (layer == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (!ok) break;
+    // output unit `half` of row m: sum over the 128 units of h3 in order, FP32
+    float y = 0.f;
+#pragma unroll 1
+    for (int c = 0; c < kH; c += 8) {
+      const uint4 pk = *reinterpret_cast<const uint4*>(gA + tc_off(m, c));
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&pk);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 hf = __bfloat1622float2(h[j]);
+        y = fmaf(__bfloat162float(w4[c + 2 * j]), hf.x, y);
+        y = fmaf(__bfloat162float(w4[c + 2 * j + 1]), hf.y, y);
       }
     }
-    if (layer == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (b < B) Y[((long long)e * B + b) * 2 + half] = y + p[kOffB4 + half];
+    __syncthreads();  // tile A is rewritten by the next tile's layer 1
   }
-  if (b < B) {  // a wait that ran out leaves NaN outputs for this tile
-    Y[((long long)e * B + b) * 2] = ok ? y0 + p[kOffB4] : __int_as_float(0x7fc00000);
-    Y[((long long)e * B + b) * 2 + 1] = ok ? y1 + p[kOffB4 + 1] : __int_as_float(0x7fc00000);
-  }
-  if (!ok) {  // let the MMAs in flight finish (bounded) before the columns are freed
+  if (!ok) {  // NaN for this CTA's unfinished tiles; let MMAs in flight finish (bounded)
     if (tid == 0) atomicExch(err, 1);
-    mbar_wait(sMbar, (uint32_t)pending);
+    for (; tile < ntiles; tile += gridDim.x) {
+      const int b = tile * kTcRows + m;
+      if (b < B) Y[((long long)e * B + b) * 2 + half] = __int_as_float(0x7fc00000);
+    }
+    mbar_wait(sMbar, (commits - 1u) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -524,6 +541,7 @@ struct mdeos_surrogate {
   int* err = nullptr;  // set by the fused kernel when an MMA wait ran out
   int infer_path = MDEOS_SURROGATE_INFER_TC;
   bool tc_ready = false;
+  int nsm = 1;
   std::vector<void*> allocs;
 };
 
@@ -813,10 +831,17 @@ static cudaError_t infer(mdeos_surrogate* s, const double* dx, int B, double* dm
       e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kTcSmem);
       if (e != cudaSuccess) return e;
+      int dev = 0;
+      e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
       s->tc_ready = true;
     }
-    dim3 grid((B + kTcRows - 1) / kTcRows, s->E);
-    mlp_infer_tc_kernel<<<grid, kTcRows, kTcSmem, st>>>(s->X, s->P, s->W1b, s->W2b, s->W3b,
+    // two resident CTAs per SM in all (shared memory bounds it at two)
+    const int tiles = (B + kTcRows - 1) / kTcRows;
+    const int per_model = std::max(1, std::min(tiles, (2 * s->nsm + s->E - 1) / s->E));
+    dim3 grid(per_model, s->E);
+    mlp_infer_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(s->X, s->P, s->W1b, s->W2b, s->W3b,
                                                           s->W4b, s->Y, B, s->err);
     e = cudaGetLastError();
     count_launch(s->h, 3);
