@@ -94,8 +94,12 @@ struct Group {
   __device__ __forceinline__ float4* x() const { return reinterpret_cast<float4*>(base); }
   __device__ __forceinline__ float4* f() const { return reinterpret_cast<float4*>(base) + npad; }
   __device__ __forceinline__ float4* v() const { return reinterpret_cast<float4*>(base) + 2 * npad; }
+  // force-pass order: slot processed at position tid + a * nt (0xffff: none)
+  __device__ __forceinline__ uint16_t* order() const {
+    return reinterpret_cast<uint16_t*>(base + (size_t)48 * npad);
+  }
   __device__ __forceinline__ int* cell() const {
-    return reinterpret_cast<int*>(base + (size_t)48 * npad);
+    return reinterpret_cast<int*>(base + (size_t)50 * npad);
   }
   __device__ __forceinline__ float* red() const { return reinterpret_cast<float*>(base + off_red); }
   __device__ __forceinline__ double* bc() const {
@@ -245,6 +249,12 @@ __device__ __forceinline__ void nl_pair_bd(uint32_t xs_a, int j, bool ok, const 
   lj_pair<EN, VIR>(dx, dy, dz, ok, c, fx, fy, fz, e, w, np);
 }
 
+__device__ __forceinline__ int ld_shared_u16(uint32_t a) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return (int)v;
+}
+
 // per-thread partial sums of one force pass
 struct FSums {
   float e, w0, w1, w2, w3, w4, w5;
@@ -256,17 +266,24 @@ struct FSums {
 // halves E and W).  Not inlined and fed only scalars: it runs with the whole
 // register budget for the pair loop while the caller's step state is saved once
 // per call, and positions are read with explicit shared-memory loads.
+//
+// ord_a (shared address, 0 = none): the slot to take at position tid + a * nt, from
+// the last list build (slots by list length, longest first, dealt over the rows in a
+// snake), so the lanes of a warp walk lists of similar length and the warps of the
+// group carry similar totals.  Only force-only passes use it: which thread computes
+// an atom then changes no result.
 template <int APT, int PATH, bool EN, bool VIR, bool CNT>
 __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16_t* nl, int tid,
                                          int nt, int npad, int n, int maxnb, float L, float invL,
-                                         LJ c) {
+                                         LJ c, uint32_t ord_a) {
   // energy, virial and pair count accumulate over all of the thread's atoms
   float e = 0.f;
   float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int np = 0;
 #pragma unroll 1
   for (int a = 0; a < APT; ++a) {
-    const int i = tid + a * nt;
+    int i = tid + a * nt;
+    if (ord_a != 0u) i = ld_shared_u16(ord_a + 2u * (uint32_t)i);
     if (i < n) {
       const float4 xi = ld_shared4(xs_a + 16u * (uint32_t)i);
       const float cw = fs[i].w;  // packed list lengths (Verlet path), kept across steps
@@ -346,8 +363,15 @@ template <int APT, int PATH, bool EN, bool VIR, bool CNT>
 __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, const RunParams& rp,
                                                float& e_acc, float (&w_acc)[6], int& pair_acc) {
   const uint32_t xs_a = (uint32_t)__cvta_generic_to_shared(g.x());
+  // the length order only where no sum depends on which thread takes which atom
+  const uint32_t ord_a = (PATH == PATH_NLIST && !EN && !VIR && !CNT)
+                             ? (uint32_t)__cvta_generic_to_shared(g.order())
+                             : 0u;
   const FSums r = force_pass<APT, PATH, EN, VIR, CNT>(xs_a, g.f(), g.nl, g.tid, g.nt, g.npad, b.n,
-                                                      b.maxnb, b.L, b.invL, make_lj(rp));
+                                                      b.maxnb, b.L, b.invL, make_lj(rp), ord_a);
+  // in the length order a thread's forces belong to other threads' atoms: every
+  // force is written before any thread reads its own atoms' forces
+  if (ord_a != 0u) gbar(g.bar, g.nt);
   if (EN) e_acc += r.e;
   if (VIR) {
     w_acc[0] += r.w0;
@@ -382,6 +406,59 @@ __device__ __forceinline__ int cell_of(const float4& x, float cinv, int nc) {
   const int cy = min((int)(x.y * cinv), nc - 1);
   const int cz = min((int)(x.z * cinv), nc - 1);
   return (cz * nc + cy) * nc + cx;
+}
+
+// Force-pass order after a list build: slots counting-sorted by list length into 32
+// classes (longest first), rank r dealt to position r in even rows of nt and mirrored
+// in odd rows (a snake), so each thread's APT atoms mix long and short lists.  The
+// class counters live in the x components of the force array (dead until the next
+// force pass; the lengths sit in its w components).  Order within a class follows
+// the shared-memory atomics: the order is used only where that changes no result.
+template <int APT>
+__device__ void build_order(const Group& g, const BoxCtx& b) {
+  const int n = b.n, nt = g.nt;
+  float4* f = g.f();
+  uint16_t* ord = g.order();
+  int* cnt = reinterpret_cast<int*>(f);  // class k counter at int index 4 k (f[k].x)
+  if (g.tid < 32) cnt[4 * g.tid] = 0;
+  gbar(g.bar, g.nt);
+  int cls[APT];
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int sl = g.tid + a * nt;
+    cls[a] = 0;
+    if (sl < n) {
+      const int len = __float_as_int(f[sl].w);
+      cls[a] = 31 - min(31, (int)(((long long)len * 32) / (b.maxnb + 1)));
+      atomicAdd(&cnt[4 * cls[a]], 1);
+    }
+  }
+  gbar(g.bar, g.nt);
+  if (g.warp() == 0) {  // exclusive scan over the 32 classes, one per lane
+    const int lane = g.lane();
+    const int c0 = cnt[4 * lane];
+    int incl = c0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    cnt[4 * lane] = incl - c0;
+  }
+  gbar(g.bar, g.nt);
+#pragma unroll
+  for (int a = 0; a < APT; ++a) {
+    const int p = g.tid + a * nt;
+    const int q = (a & 1) ? a * nt + (nt - 1 - g.tid) : p;  // rank taken at position p
+    if (q >= n) ord[p] = 0xffff;
+    const int sl = p;
+    if (sl < n) {
+      const int r = atomicAdd(&cnt[4 * cls[a]], 1);
+      const int ra = r / nt, rt = r - ra * nt;
+      ord[(ra & 1) ? ra * nt + (nt - 1 - rt) : r] = (uint16_t)sl;
+    }
+  }
+  gbar(g.bar, g.nt);
 }
 
 template <int APT>
@@ -564,6 +641,7 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, long long* prof = n
     gbar(g.bar, g.nt);
     MDEOS_PHASE(5)
   }
+  build_order<APT>(g, b);
 #undef MDEOS_PHASE
 }
 

@@ -110,6 +110,7 @@ constexpr int kAccDoubles = 2 * kMaxSeBlocks + 24;  // block sums of P and T, ru
 
 // Shared-memory layout of one box group (host planner and device agree):
 //   positions, forces, velocities  float4[npad] each (48 B per atom slot)
+//   force-pass order               uint16[npad] (slots by list length)
 //   cell counts / starts           int[2 * ncell_cap + 2]
 //   per-warp partials              float[warps][kRedSlots]    (16-B aligned)
 //   FP64 broadcast slots           double[8]
@@ -118,7 +119,7 @@ constexpr int kAccDoubles = 2 * kMaxSeBlocks + 24;  // block sums of P and T, ru
 //   control words                  int[16]
 __host__ __device__ inline int group_red_offset(int warps, int apt, int ncell_cap) {
   int npad = warps * 32 * apt;
-  int b = npad * 48 + (2 * ncell_cap + 2) * 4;
+  int b = npad * 50 + (2 * ncell_cap + 2) * 4;
   return (b + 15) & ~15;
 }
 
