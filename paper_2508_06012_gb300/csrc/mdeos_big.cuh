@@ -36,7 +36,17 @@ struct BigMem {
   int *cnt, *start;
   uint4* nl;
   int cap;
+  uint32_t sx_a;  // shared-memory copy of the positions for the force pass (0: none)
 };
+
+// Shared address of a position cache of n float4 at dynamic shared memory offset
+// `off`, or 0 when the launch's dynamic shared memory is too small for it.
+__device__ __forceinline__ uint32_t big_pos_cache(const unsigned char* dyn_base, int off, int n) {
+  uint32_t dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  if ((long long)off + 16LL * n > (long long)dyn) return 0u;
+  return (uint32_t)__cvta_generic_to_shared(dyn_base) + (uint32_t)off;
+}
 
 __device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
   BigMem m;
@@ -51,6 +61,7 @@ __device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
   m.cnt = reinterpret_cast<int*>(c);
   m.start = m.cnt + ncell + 1;
   m.nl = reinterpret_cast<uint4*>(c + big_cells_bytes(ncell));
+  m.sx_a = 0u;
   return m;
 }
 
@@ -230,17 +241,19 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
 
 // Forces on every atom (strided over the CTA) from the Verlet list, minimum image
 // on every entry; partial sums over the thread's atoms.  Out of line and fed
-// scalars, like force_pass.  Positions are read with ordinary (L1-cached) loads:
-// they were written by this CTA before the last barrier.
-template <bool EN, bool VIR, bool CNT>
-__device__ __noinline__ FSums big_force_pass(const float4* x, float4* f, const uint4* nl, int cap,
-                                             int n, float L, float invL, LJ c) {
+// scalars, like force_pass.  Positions come from the shared-memory copy at sx_a
+// (SM) or from global memory with ordinary (L1-cached) loads: they were written by
+// this CTA before the last barrier.
+template <bool EN, bool VIR, bool CNT, bool SM>
+__device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, float4* f,
+                                             const uint4* nl, int cap, int n, float L, float invL,
+                                             LJ c) {
   float e = 0.f;
   float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int np = 0;
 #pragma unroll 1
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    const float4 xi = x[s];
+    const float4 xi = SM ? ld_shared4(sx_a + 16u * (uint32_t)s) : x[s];
     const float cw = f[s].w;
     const int cn = __float_as_int(cw);
     const int nw = (cn + 7) >> 3;
@@ -257,7 +270,8 @@ __device__ __noinline__ FSums big_force_pass(const float4* x, float4* f, const u
         const unsigned wd = u < 2 ? cur.x : (u < 4 ? cur.y : (u < 6 ? cur.z : cur.w));
         const int jj = (int)((wd >> (16 * (u & 1))) & 0xffffu);
         const bool ok = u < left;
-        const float4 xj = x[ok ? jj : s];
+        const int jr = ok ? jj : s;
+        const float4 xj = SM ? ld_shared4(sx_a + 16u * (uint32_t)jr) : x[jr];
         const float dx = min_img(xi.x - xj.x, L, invL);
         const float dy = min_img(xi.y - xj.y, L, invL);
         const float dz = min_img(xi.z - xj.z, L, invL);
@@ -289,11 +303,22 @@ __device__ inline BigCtx make_big_ctx(const BoxDesc& bd, const RunParams& rp) {
   return b;
 }
 
+// Force pass; with a position cache the positions are first copied into shared
+// memory (every caller has a barrier since the positions were last written, and
+// the next write comes after the barrier that follows the next drift).
 __device__ __forceinline__ FSums big_forces(const BigMem& m, const BigCtx& b, const LJ& c, bool en,
                                             bool vir) {
-  if (vir) return big_force_pass<true, true, true>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
-  if (en) return big_force_pass<true, false, false>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
-  return big_force_pass<false, false, false>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+  if (m.sx_a != 0u) {
+    float4* sx = reinterpret_cast<float4*>(__cvta_shared_to_generic(m.sx_a));
+    for (int s = threadIdx.x; s < b.n; s += blockDim.x) sx[s] = m.x[s];
+    __syncthreads();
+    if (vir) return big_force_pass<true, true, true, true>(m.x, m.sx_a, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+    if (en) return big_force_pass<true, false, false, true>(m.x, m.sx_a, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+    return big_force_pass<false, false, false, true>(m.x, m.sx_a, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+  }
+  if (vir) return big_force_pass<true, true, true, false>(m.x, 0u, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+  if (en) return big_force_pass<true, false, false, false>(m.x, 0u, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+  return big_force_pass<false, false, false, false>(m.x, 0u, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
 }
 
 // Maxwell velocities at T (Eq. 9): Philox keyed by the seed, counter = atom id,
@@ -374,6 +399,8 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   const BigCtx b = make_big_ctx(bd, rp);
   const LJ lj = make_lj(rp);
   BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  // positions in the CTA's otherwise idle shared memory, behind BigShared, when they fit
+  m.sx_a = big_pos_cache(reinterpret_cast<const unsigned char*>(sh), kBigSharedBytes, b.n);
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
   const double V = bd.L * bd.L * bd.L;

@@ -287,8 +287,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     m.x[s] = make_float4(xi.x, xi.y, xi.z, xo.w);
   }
   __syncthreads();
-  const FSums r = big_force_pass<true, true, true>(m.x, m.f, m.nl, m.cap, b.n, b.L, b.invL,
-                                                   make_lj(rp));
+  extern __shared__ __align__(128) unsigned char dyn[];
+  m.sx_a = big_pos_cache(dyn, 0, b.n);  // the batch kernel's path when the box fits
+  const FSums r = big_forces(m, b, make_lj(rp), true, true);
   for (int s = threadIdx.x; s < b.n; s += blockDim.x) f4[__float_as_int(m.x[s].w)] = m.f[s];
   float q[8] = {0.5f * r.e,  0.5f * r.w0, 0.5f * r.w1, 0.5f * r.w2,
                 0.5f * r.w3, 0.5f * r.w4, 0.5f * r.w5, (float)r.np};
@@ -306,9 +307,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                         int steps, double T_target, int rescale_every, double* epot,
                         double* ekin, long long* cyc) {
   __shared__ BigShared sh;
+  extern __shared__ __align__(128) unsigned char dyn[];
   const BigCtx b = make_big_ctx(bd, rp);
   const LJ lj = make_lj(rp);
   BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  m.sx_a = big_pos_cache(dyn, 0, b.n);  // the batch kernel's path when the box fits
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
   long long nbuild = 0;
@@ -376,18 +379,26 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   }
 }
 
+// dynamic shared memory for the big-box debug kernels: the position cache when it fits
+static int g_debug_big_smem_max = 0;
+static int debug_big_smem(int n) {
+  const int bytes = 16 * big_cap(n);
+  return bytes <= g_debug_big_smem_max ? bytes : 0;
+}
+
 cudaError_t launch_debug_big_forces(const BoxDesc& bd, const RunParams& rp, unsigned char* scratch,
                                     const float4* x4, float4* f4, double* ew, long long* pairs,
                                     cudaStream_t st) {
-  debug_big_forces_kernel<<<1, kCtaThreads, 0, st>>>(bd, rp, scratch, x4, f4, ew, pairs);
+  debug_big_forces_kernel<<<1, kCtaThreads, debug_big_smem(bd.natoms), st>>>(bd, rp, scratch, x4,
+                                                                             f4, ew, pairs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_debug_big_md(const BoxDesc& bd, const RunParams& rp, unsigned char* scratch,
                                 float4* x4, float4* v4, int steps, double T, int every, double* ep,
                                 double* ek, long long* cyc, cudaStream_t st) {
-  debug_big_md_kernel<<<1, kCtaThreads, 0, st>>>(bd, rp, scratch, x4, v4, steps, T, every, ep, ek,
-                                                 cyc);
+  debug_big_md_kernel<<<1, kCtaThreads, debug_big_smem(bd.natoms), st>>>(
+      bd, rp, scratch, x4, v4, steps, T, every, ep, ek, cyc);
   return cudaGetLastError();
 }
 
@@ -397,7 +408,17 @@ cudaError_t set_debug_attributes(int max_smem) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(debug_forces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(debug_md_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  e = cudaFuncSetAttribute(debug_md_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e != cudaSuccess) return e;
+  // the big-box kernels also hold a static BigShared
+  const int big_max = max_smem - (int)sizeof(BigShared);
+  e = cudaFuncSetAttribute(debug_big_forces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big_max);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(debug_big_md_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big_max);
+  if (e == cudaSuccess) g_debug_big_smem_max = big_max;
+  return e;
 }
 
 cudaError_t launch_debug_lift(const BoxDesc& bd, const RunParams& rp, double T, int apt,
