@@ -322,9 +322,10 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
       wi.nl_stride = (int)(((bytes + 15) & ~(size_t)15) / 2);
       wi.box[0] = (int)plan.boxes.size();
       plan.boxes.push_back(bp[k].bd);
-      // room for the box's positions behind the CTA's BigShared when they fit
+      // room for position windows behind the CTA's BigShared: the whole box when it
+      // fits, else all the shared memory there is
       const int cache = kBigSharedBytes + 16 * big_cap(bp[k].bd.natoms);
-      plan.smem = std::max(plan.smem, cache <= smem_max ? cache : kBigSharedBytes);
+      plan.smem = std::max(plan.smem, std::min(cache, smem_max));
       plan.nl_per_cta = std::max(plan.nl_per_cta, (long long)wi.nl_stride);
       items.push_back({wi, bp[k].cost});
       ++k;

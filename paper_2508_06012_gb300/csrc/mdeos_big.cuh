@@ -20,6 +20,8 @@
 namespace mdeos {
 
 // shared memory of a big-box CTA
+constexpr int kMaxRounds = 16;  // force-pass rounds of a big box (position windows)
+
 struct BigShared {
   float red[32 * kRedSlots];
   double bc[8];
@@ -27,6 +29,10 @@ struct BigShared {
   int bcnt[kMaxSeBlocks];
   int ctrl[16];
   int scan[32];
+  int wlo[kMaxRounds];  // first slot of each round's position window
+  int wsz[kMaxRounds];  // its length in slots (cyclic over the box)
+  int nround;           // rounds (0: no shared-memory positions)
+  int rsz;              // slots per round (a multiple of the CTA's threads)
 };
 
 static_assert(sizeof(BigShared) <= kBigSharedBytes, "big-box shared memory");
@@ -36,16 +42,20 @@ struct BigMem {
   int *cnt, *start;
   uint4* nl;
   int cap;
-  uint32_t sx_a;  // shared-memory copy of the positions for the force pass (0: none)
+  uint32_t sx_a;  // shared-memory position windows for the force pass (0: none)
+  int sx_cap;     // their capacity in atoms
+  int nround, rsz;           // force-pass rounds from the last build (0: none)
+  const int *wlo, *wsz;      // their windows (shared memory)
 };
 
-// Shared address of a position cache of n float4 at dynamic shared memory offset
-// `off`, or 0 when the launch's dynamic shared memory is too small for it.
-__device__ __forceinline__ uint32_t big_pos_cache(const unsigned char* dyn_base, int off, int n) {
+// Position windows in the dynamic shared memory from offset `off` on: address and
+// capacity (in float4) of what the launch provides, at least 1024 atoms, else none.
+__device__ __forceinline__ void big_pos_cache(BigMem& m, const unsigned char* dyn_base, int off) {
   uint32_t dyn;
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-  if ((long long)off + 16LL * n > (long long)dyn) return 0u;
-  return (uint32_t)__cvta_generic_to_shared(dyn_base) + (uint32_t)off;
+  const int cap = (int)(((long long)dyn - off) / 16);
+  m.sx_a = cap >= 1024 ? (uint32_t)__cvta_generic_to_shared(dyn_base) + (uint32_t)off : 0u;
+  m.sx_cap = cap >= 1024 ? cap : 0;
 }
 
 __device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
@@ -62,6 +72,10 @@ __device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
   m.start = m.cnt + ncell + 1;
   m.nl = reinterpret_cast<uint4*>(c + big_cells_bytes(ncell));
   m.sx_a = 0u;
+  m.sx_cap = 0;
+  m.nround = 0;
+  m.rsz = n;
+  m.wlo = m.wsz = nullptr;
   return m;
 }
 
@@ -199,9 +213,54 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
     m.v = m.v2;
     m.v2 = t;
   }
+  // Force-pass rounds: slots [q rsz, (q + 1) rsz) lie in cell layers z0..z1 (cells
+  // are z-major), so their neighbours lie in layers z0 - 1 .. z1 + 1 (cyclic; a
+  // neighbour across the y or x boundary can be anywhere in its layer).  The slots of
+  // those whole layers (contiguous, cyclic over the box) are the round's position
+  // window.  The fewest rounds whose windows all fit the shared memory; none if even
+  // kMaxRounds do not.  List entries are stored relative to the window start, so the
+  // pass indexes the window directly.
+  if (tid == 0) {
+    sh->nround = 0;
+    sh->rsz = n;
+    if (m.sx_cap > 0) {
+      const int nc2 = nc * nc;
+      for (int R = 1; R <= kMaxRounds; ++R) {
+        const int rsz = ((n + R - 1) / R + nt - 1) / nt * nt;
+        const int nr = (n + rsz - 1) / rsz;
+        bool fits = true;
+        for (int q = 0; q < nr && fits; ++q) {
+          const int s0 = q * rsz, s1 = min(n, s0 + rsz) - 1;
+          const int z0 = cell_of(m.x[s0], cinv, nc) / nc2, z1 = cell_of(m.x[s1], cinv, nc) / nc2;
+          int lo = 0, sz = n;
+          if (z1 - z0 + 3 < nc) {
+            const int lz = (z0 - 1 + nc) % nc, hz = (z1 + 1) % nc;
+            lo = m.start[lz * nc2];
+            const int hi = m.start[(hz + 1) * nc2];
+            sz = lz <= hz ? hi - lo : (n - lo) + hi;
+          }
+          fits = sz <= m.sx_cap;
+          sh->wlo[q] = lo;
+          sh->wsz[q] = sz;
+        }
+        if (fits) {
+          sh->nround = nr;
+          sh->rsz = rsz;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  m.nround = sh->nround;
+  m.rsz = sh->rsz;
+  m.wlo = sh->wlo;
+  m.wsz = sh->wsz;
   uint16_t* row = reinterpret_cast<uint16_t*>(m.nl);
   const size_t wstride = (size_t)m.cap * 8;  // uint16 entries between words of one slot
   for (int s = tid; s < n; s += nt) {
+    const int q = m.nround > 0 ? s / m.rsz : 0;
+    const int wl = m.nround > 0 ? m.wlo[q] : 0, ws = m.nround > 0 ? m.wsz[q] : n;
     const float4 xi = m.x[s];
     const int cx = min((int)(xi.x * cinv), nc - 1);
     const int cy = min((int)(xi.y * cinv), nc - 1);
@@ -226,7 +285,13 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
             const float ddx = xi.x - (xj.x + sx), ddy = xi.y - (xj.y + sy), ddz = xi.z - (xj.z + sz);
             const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
             if (j != s && r2 < rs2) {
-              if (k < maxnb) row[(size_t)(k >> 3) * wstride + (size_t)s * 8 + (k & 7)] = (uint16_t)j;
+              int e = j - wl;  // window-relative slot
+              if (e < 0) e += n;
+              if (e >= ws) {  // cannot happen by construction; fail the box, read in bounds
+                atomicOr(&sh->ctrl[CTRL_OVERFLOW], 1);
+                e = 0;
+              }
+              if (k < maxnb) row[(size_t)(k >> 3) * wstride + (size_t)s * 8 + (k & 7)] = (uint16_t)e;
               ++k;
             }
           }
@@ -244,16 +309,25 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
 // scalars, like force_pass.  Positions come from the shared-memory copy at sx_a
 // (SM) or from global memory with ordinary (L1-cached) loads: they were written by
 // this CTA before the last barrier.
+//
+// SM: slots [s0, s1) of one round, positions from the round's window in shared
+// memory (slot wl at index 0, cyclic over the n slots; list entries are window
+// indices).  Otherwise all slots, positions and list entries as global slots.
 template <bool EN, bool VIR, bool CNT, bool SM>
-__device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, float4* f,
-                                             const uint4* nl, int cap, int n, float L, float invL,
-                                             LJ c) {
+__device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, int s0, int s1,
+                                             int wl, float4* f, const uint4* nl, int cap, int n,
+                                             float L, float invL, LJ c) {
   float e = 0.f;
   float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int np = 0;
 #pragma unroll 1
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    const float4 xi = SM ? ld_shared4(sx_a + 16u * (uint32_t)s) : x[s];
+  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    int si = s;  // the atom's own index in the position source
+    if (SM) {
+      si = s - wl;
+      if (si < 0) si += n;
+    }
+    const float4 xi = SM ? ld_shared4(sx_a + 16u * (uint32_t)si) : x[s];
     const float cw = f[s].w;
     const int cn = __float_as_int(cw);
     const int nw = (cn + 7) >> 3;
@@ -270,7 +344,7 @@ __device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, flo
         const unsigned wd = u < 2 ? cur.x : (u < 4 ? cur.y : (u < 6 ? cur.z : cur.w));
         const int jj = (int)((wd >> (16 * (u & 1))) & 0xffffu);
         const bool ok = u < left;
-        const int jr = ok ? jj : s;
+        const int jr = ok ? jj : si;
         const float4 xj = SM ? ld_shared4(sx_a + 16u * (uint32_t)jr) : x[jr];
         const float dx = min_img(xi.x - xj.x, L, invL);
         const float dy = min_img(xi.y - xj.y, L, invL);
@@ -303,22 +377,46 @@ __device__ inline BigCtx make_big_ctx(const BoxDesc& bd, const RunParams& rp) {
   return b;
 }
 
-// Force pass; with a position cache the positions are first copied into shared
-// memory (every caller has a barrier since the positions were last written, and
-// the next write comes after the barrier that follows the next drift).
+// Force pass.  With position windows from the last build: per round, the window's
+// positions are copied into shared memory, a barrier, the round's slots, a barrier
+// (before the next window overwrites it); per-thread sums add up over the rounds.
+// Every caller has a barrier since the positions were last written.
+template <bool EN, bool VIR, bool CNT>
+__device__ __forceinline__ FSums big_forces_t(const BigMem& m, const BigCtx& b, const LJ& c) {
+  if (m.nround == 0)
+    return big_force_pass<EN, VIR, CNT, false>(m.x, 0u, 0, b.n, 0, m.f, m.nl, m.cap, b.n, b.L,
+                                               b.invL, c);
+  FSums t = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+  float4* sx = reinterpret_cast<float4*>(__cvta_shared_to_generic(m.sx_a));
+  for (int q = 0; q < m.nround; ++q) {
+    const int wl = m.wlo[q], ws = m.wsz[q];
+    for (int k = threadIdx.x; k < ws; k += blockDim.x) {
+      int g = wl + k;
+      if (g >= b.n) g -= b.n;
+      sx[k] = m.x[g];
+    }
+    __syncthreads();
+    const int s0 = q * m.rsz, s1 = min(b.n, s0 + m.rsz);
+    const FSums r = big_force_pass<EN, VIR, CNT, true>(m.x, m.sx_a, s0, s1, wl, m.f, m.nl, m.cap,
+                                                       b.n, b.L, b.invL, c);
+    __syncthreads();
+    t.e += r.e;
+    t.w0 += r.w0;
+    t.w1 += r.w1;
+    t.w2 += r.w2;
+    t.w3 += r.w3;
+    t.w4 += r.w4;
+    t.w5 += r.w5;
+    t.np += r.np;
+  }
+  return t;
+}
+
 __device__ __forceinline__ FSums big_forces(const BigMem& m, const BigCtx& b, const LJ& c, bool en,
                                             bool vir) {
-  if (m.sx_a != 0u) {
-    float4* sx = reinterpret_cast<float4*>(__cvta_shared_to_generic(m.sx_a));
-    for (int s = threadIdx.x; s < b.n; s += blockDim.x) sx[s] = m.x[s];
-    __syncthreads();
-    if (vir) return big_force_pass<true, true, true, true>(m.x, m.sx_a, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
-    if (en) return big_force_pass<true, false, false, true>(m.x, m.sx_a, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
-    return big_force_pass<false, false, false, true>(m.x, m.sx_a, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
-  }
-  if (vir) return big_force_pass<true, true, true, false>(m.x, 0u, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
-  if (en) return big_force_pass<true, false, false, false>(m.x, 0u, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
-  return big_force_pass<false, false, false, false>(m.x, 0u, m.f, m.nl, m.cap, b.n, b.L, b.invL, c);
+  if (vir) return big_forces_t<true, true, true>(m, b, c);
+  if (en) return big_forces_t<true, false, false>(m, b, c);
+  return big_forces_t<false, false, false>(m, b, c);
 }
 
 // Maxwell velocities at T (Eq. 9): Philox keyed by the seed, counter = atom id,
@@ -399,8 +497,8 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   const BigCtx b = make_big_ctx(bd, rp);
   const LJ lj = make_lj(rp);
   BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
-  // positions in the CTA's otherwise idle shared memory, behind BigShared, when they fit
-  m.sx_a = big_pos_cache(reinterpret_cast<const unsigned char*>(sh), kBigSharedBytes, b.n);
+  // position windows in the CTA's otherwise idle shared memory, behind BigShared
+  big_pos_cache(m, reinterpret_cast<const unsigned char*>(sh), kBigSharedBytes);
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
   const double V = bd.L * bd.L * bd.L;

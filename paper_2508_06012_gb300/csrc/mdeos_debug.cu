@@ -270,6 +270,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   __shared__ BigShared sh;
   const BigCtx b = make_big_ctx(bd, rp);
   BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  extern __shared__ __align__(128) unsigned char dyn[];
+  big_pos_cache(m, dyn, 0);  // position windows, as in the batch kernel
   if (threadIdx.x < 16) sh.ctrl[threadIdx.x] = 0;
   for (int s = threadIdx.x; s < b.n; s += blockDim.x) {
     const float4 xi = x4[s];
@@ -287,8 +289,6 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     m.x[s] = make_float4(xi.x, xi.y, xi.z, xo.w);
   }
   __syncthreads();
-  extern __shared__ __align__(128) unsigned char dyn[];
-  m.sx_a = big_pos_cache(dyn, 0, b.n);  // the batch kernel's path when the box fits
   const FSums r = big_forces(m, b, make_lj(rp), true, true);
   for (int s = threadIdx.x; s < b.n; s += blockDim.x) f4[__float_as_int(m.x[s].w)] = m.f[s];
   float q[8] = {0.5f * r.e,  0.5f * r.w0, 0.5f * r.w1, 0.5f * r.w2,
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   const BigCtx b = make_big_ctx(bd, rp);
   const LJ lj = make_lj(rp);
   BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
-  m.sx_a = big_pos_cache(dyn, 0, b.n);  // the batch kernel's path when the box fits
+  big_pos_cache(m, dyn, 0);  // position windows, as in the batch kernel
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
   long long nbuild = 0;
@@ -379,12 +379,10 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   }
 }
 
-// dynamic shared memory for the big-box debug kernels: the position cache when it fits
+// dynamic shared memory for the big-box debug kernels: position windows of the
+// whole box when it fits, else all that the device allows
 static int g_debug_big_smem_max = 0;
-static int debug_big_smem(int n) {
-  const int bytes = 16 * big_cap(n);
-  return bytes <= g_debug_big_smem_max ? bytes : 0;
-}
+static int debug_big_smem(int n) { return std::min(16 * big_cap(n), g_debug_big_smem_max); }
 
 cudaError_t launch_debug_big_forces(const BoxDesc& bd, const RunParams& rp, unsigned char* scratch,
                                     const float4* x4, float4* f4, double* ew, long long* pairs,
