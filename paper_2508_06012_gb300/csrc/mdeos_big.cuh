@@ -258,48 +258,73 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
   m.wsz = sh->wsz;
   uint16_t* row = reinterpret_cast<uint16_t*>(m.nl);
   const size_t wstride = (size_t)m.cap * 8;  // uint16 entries between words of one slot
-  for (int s = tid; s < n; s += nt) {
-    const int q = m.nround > 0 ? s / m.rsz : 0;
-    const int wl = m.nround > 0 ? m.wlo[q] : 0, ws = m.nround > 0 ? m.wsz[q] : n;
-    const float4 xi = m.x[s];
-    const int cx = min((int)(xi.x * cinv), nc - 1);
-    const int cy = min((int)(xi.y * cinv), nc - 1);
-    const int cz = min((int)(xi.z * cinv), nc - 1);
-    int k = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-      int zz = cz + dz;
-      float sz = 0.f;
-      if (zz < 0) { zz += nc; sz = -L; } else if (zz >= nc) { zz -= nc; sz = L; }
-      for (int dy = -1; dy <= 1; ++dy) {
-        int yy = cy + dy;
-        float sy = 0.f;
-        if (yy < 0) { yy += nc; sy = -L; } else if (yy >= nc) { yy -= nc; sy = L; }
-        for (int dx = -1; dx <= 1; ++dx) {
-          int xx = cx + dx;
-          float sx = 0.f;
-          if (xx < 0) { xx += nc; sx = -L; } else if (xx >= nc) { xx -= nc; sx = L; }
-          const int c = (zz * nc + yy) * nc + xx;
-          const int j1 = m.start[c + 1];
-          for (int j = m.start[c]; j < j1; ++j) {
-            const float4 xj = m.x[j];
-            const float ddx = xi.x - (xj.x + sx), ddy = xi.y - (xj.y + sy), ddz = xi.z - (xj.z + sz);
-            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-            if (j != s && r2 < rs2) {
-              int e = j - wl;  // window-relative slot
-              if (e < 0) e += n;
-              if (e >= ws) {  // cannot happen by construction; fail the box, read in bounds
-                atomicOr(&sh->ctrl[CTRL_OVERFLOW], 1);
-                e = 0;
+  // The search runs in the same rounds, candidates read from the round's window: a
+  // cell's slots are contiguous in the window (the window's cyclic seam falls on a
+  // cell boundary), so one offset per cell maps them.  A cell or slot outside its
+  // window (impossible by construction) fails the box without any read.
+  const bool win = m.nround > 0;
+  for (int q = 0; q < (win ? m.nround : 1); ++q) {
+    const int wl = win ? m.wlo[q] : 0, ws = win ? m.wsz[q] : n;
+    const int sb = win ? q * m.rsz : 0, se = win ? min(n, sb + m.rsz) : n;
+    if (win) {
+      float4* sx = reinterpret_cast<float4*>(__cvta_shared_to_generic(m.sx_a));
+      for (int k = tid; k < ws; k += nt) {
+        int g = wl + k;
+        if (g >= n) g -= n;
+        sx[k] = m.x[g];
+      }
+      __syncthreads();
+    }
+    for (int s = sb + tid; s < se; s += nt) {
+      int si = s - wl;
+      if (si < 0) si += n;
+      if (si >= ws) {
+        atomicOr(&sh->ctrl[CTRL_OVERFLOW], 1);
+        m.f[s].w = __int_as_float(0);
+        continue;
+      }
+      const float4 xi = win ? ld_shared4(m.sx_a + 16u * (uint32_t)si) : m.x[s];
+      const int cx = min((int)(xi.x * cinv), nc - 1);
+      const int cy = min((int)(xi.y * cinv), nc - 1);
+      const int cz = min((int)(xi.z * cinv), nc - 1);
+      int k = 0;
+      for (int dz = -1; dz <= 1; ++dz) {
+        int zz = cz + dz;
+        float sz = 0.f;
+        if (zz < 0) { zz += nc; sz = -L; } else if (zz >= nc) { zz -= nc; sz = L; }
+        for (int dy = -1; dy <= 1; ++dy) {
+          int yy = cy + dy;
+          float sy = 0.f;
+          if (yy < 0) { yy += nc; sy = -L; } else if (yy >= nc) { yy -= nc; sy = L; }
+          for (int dx = -1; dx <= 1; ++dx) {
+            int xx = cx + dx;
+            float sx_ = 0.f;
+            if (xx < 0) { xx += nc; sx_ = -L; } else if (xx >= nc) { xx -= nc; sx_ = L; }
+            const int c = (zz * nc + yy) * nc + xx;
+            const int j0 = m.start[c], j1 = m.start[c + 1];
+            int jb = j0 - wl;  // window index of the cell's first slot
+            if (jb < 0) jb += n;
+            if (jb + (j1 - j0) > ws) {
+              atomicOr(&sh->ctrl[CTRL_OVERFLOW], 1);
+              continue;
+            }
+            for (int j = j0; j < j1; ++j) {
+              const int e = jb + (j - j0);  // window-relative slot (= j without windows)
+              const float4 xj = win ? ld_shared4(m.sx_a + 16u * (uint32_t)e) : m.x[j];
+              const float ddx = xi.x - (xj.x + sx_), ddy = xi.y - (xj.y + sy), ddz = xi.z - (xj.z + sz);
+              const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+              if (j != s && r2 < rs2) {
+                if (k < maxnb) row[(size_t)(k >> 3) * wstride + (size_t)s * 8 + (k & 7)] = (uint16_t)e;
+                ++k;
               }
-              if (k < maxnb) row[(size_t)(k >> 3) * wstride + (size_t)s * 8 + (k & 7)] = (uint16_t)e;
-              ++k;
             }
           }
         }
       }
+      if (k > maxnb) atomicOr(&sh->ctrl[CTRL_OVERFLOW], 1);
+      m.f[s].w = __int_as_float(min(k, maxnb));
     }
-    if (k > maxnb) atomicOr(&sh->ctrl[CTRL_OVERFLOW], 1);
-    m.f[s].w = __int_as_float(min(k, maxnb));
+    if (win) __syncthreads();  // before the next window overwrites this one
   }
   __syncthreads();
 }
