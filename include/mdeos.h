@@ -91,7 +91,8 @@ typedef struct {
   double rho;          /* number density, > 0 */
   double e;            /* specific internal energy per atom (temperature with the flag) */
   double e_ref;        /* energy zero per atom, used with MDEOS_REF_FIXED */
-  int32_t natoms;      /* atoms in the MD box, 2..4096 */
+  int32_t natoms;      /* atoms in the MD box, 2..32768 (above 4096: one box per CTA with its
+                          state in device memory; mdeos_submit_noalloc takes up to 4096) */
   int32_t steps_equil; /* lifting steps, split into lift_iters NVE segments (0 = none) */
   int32_t steps_avg;   /* production steps averaged by the restriction, >= se_blocks */
   uint32_t flags;      /* MDEOS_REQ_* */
@@ -208,7 +209,9 @@ mdeos_status mdeos_stats(const mdeos_handle* h, size_t* last_h2d_bytes, size_t* 
  * call's contents; the call clears what must start at zero): calls whose work
  * overlaps on the GPU race, so serialise them (one stream, or events).  A batch
  * whose work table plus one CTA's Verlet lists exceed the array is rejected
- * with MDEOS_EINVAL; smaller scratch per CTA runs on fewer CTAs.
+ * with MDEOS_EINVAL; smaller scratch per CTA runs on fewer CTAs.  Requests above
+ * 4096 atoms get MDEOS_EINVAL in their result (their per-box device state would
+ * need an allocation).
  * Errors: MDEOS_EINVAL, MDEOS_ECUDA. */
 #define MDEOS_NOALLOC_SCRATCH_BYTES ((size_t)128 << 20)
 mdeos_status mdeos_submit_noalloc(const mdeos_config* cfg, const mdeos_request* reqs, int32_t n,
