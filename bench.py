@@ -35,7 +35,7 @@ FLOPS_PER_PAIR = 27  # nominal FP32 flops per in-cutoff pair
 # invalidates it (reported as null).
 BATCH_KERNEL_SOURCES = ("mdeos_internal.h", "mdeos_device.cuh", "mdeos_big.cuh",
                         "mdeos_batch.cu", "mdeos_api.cu", "mdeos_host.h")
-MEASURED_TRAFFIC = {"csrc_sha256_12": "c23dac12d07d", "bytes_per_launch": 709,
+MEASURED_TRAFFIC = {"csrc_sha256_12": "c23dac12d07d", "bytes_per_launch": 7.09e11,
                     "executed_fp32_frac": 0.196}
 
 
