@@ -182,3 +182,22 @@ def test_poll_semantics(m):
     s = m.mdeos_stats(h)
     assert s["launches"] >= 3
     m.mdeos_destroy(h)
+
+
+def test_empty_inputs(m):
+    """An empty batch is an argument error on every submission path (n >= 1); an empty
+    surrogate query set is a no-op."""
+    import torch
+    h = m.mdeos_create()
+    try:
+        buf = torch.zeros(m.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        for call in (lambda: m.mdeos_submit(h, []), lambda: m.mdeos_batch_create(h, []),
+                     lambda: m.mdeos_submit_noalloc([], buf.data_ptr())):
+            with pytest.raises(m.MdeosError) as ei:
+                call()
+            assert ei.value.status == m.MDEOS_EINVAL
+        with m.Surrogate(h, 2, 64) as sg:
+            mean, sd = sg.predict(np.zeros((0, 2)))
+        assert mean.shape == (0, 2) and sd.shape == (0, 2)
+    finally:
+        m.mdeos_destroy(h)
