@@ -27,7 +27,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FLOPS_PER_PAIR = 27  # nominal FP32 flops per in-cutoff pair
+# nominal FP32 flops per in-cutoff pair: difference 3, r^2 5, reciprocal 1, r^-6 2,
+# force scalar 4, three force FMAs 6, energy 4, virial trace 2
+FLOPS_PER_PAIR = 27
 
 # DRAM traffic of one eos_batch_kernel launch (dram__bytes_read + write) from the
 # ncu capture summarised in profiles/eos_batch_kernel_config2.md, keyed by a hash
@@ -585,8 +587,12 @@ def surrogate(args):
     clocks = ClockSampler(gpu_idx)
     clocks.start()
     out = {}
-    # 1. training data: MD answers over the config-2 distribution
-    reqs = gpu_requests(m, w.config2(base_seed=777, nbox=args.train_n))
+    # 1. training data: MD answers over the config-2 distribution (with --train-natoms,
+    # its (rho, T) distribution at that one box size)
+    boxes = w.config2(base_seed=777, nbox=args.train_n)
+    if args.train_natoms:
+        boxes = [dict(b, natoms=args.train_natoms) for b in boxes]
+    reqs = gpu_requests(m, boxes)
     t0 = time.perf_counter()
     res = m.mdeos_poll(h, m.mdeos_submit(h, reqs), len(reqs), -1)
     out["md_training_data_s"] = time.perf_counter() - t0
@@ -711,7 +717,8 @@ def surrogate(args):
             "steps": 1, "warmup": 0, "ms_per_step": out["test"]["gated_s"] * 1000.0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (MD answers of seeded LJ boxes)", "config": {
-                "workload": SURROGATE, "train_n": args.train_n, "val_n": args.val_n,
+                "workload": SURROGATE, "train_n": args.train_n,
+                "train_natoms": args.train_natoms or "config-2 mix", "val_n": args.val_n,
                 "test_n": args.test_n, "epochs": args.epochs},
             "details": out, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -826,6 +833,8 @@ def main():
     ap.add_argument("--val-n", type=int, default=2000, help="surrogate: validation queries")
     ap.add_argument("--test-n", type=int, default=4000, help="surrogate: test queries")
     ap.add_argument("--epochs", type=int, default=40, help="surrogate: training epochs")
+    ap.add_argument("--train-natoms", type=int, default=0,
+                    help="surrogate: one box size for the training MD (0: the config-2 mix)")
     ap.add_argument("--queries", type=int, default=1 << 23, help="surrogate-infer: queries")
     ap.add_argument("--workload", choices=["uneven", "coupled", "serving", "surrogate",
                                            "surrogate-infer"],

@@ -11,7 +11,7 @@
  * TEST INFRASTRUCTURE ONLY: called from tests/, the smoke check and the CPU
  * baseline of bench.py; never from the product library.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - Eq. 6/7 conflict for alpha != 1; lattice constant a = (alpha/n)^(1/3)
  *    with alpha = 4 (FCC) and N = alpha * V / a^3.
  *  - N_DOF = 3N - 3 (total momentum removed).

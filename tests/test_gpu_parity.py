@@ -1,7 +1,8 @@
 """GPU parity of the single-box kernels against the FP64 oracle, element by element
 on identical inputs, through the C ABI.
 
-Tolerances (derived in the design doc):
+Tolerances (FP32 pair arithmetic against FP64; the largest forces and the
+per-thread FP32 partial sums set the scale):
   forces     max_i |F_gpu - F_ref| / max(|F_ref,i|, F_rms) <= 1e-5
   energy     |E_gpu - E_ref| <= 1e-6 |E_ref| + 1e-5 N
   virial     |W_gpu - W_ref| <= 2e-5 max|W_ref| + 1e-4 N
