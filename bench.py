@@ -569,8 +569,9 @@ def serving(args):
 
 SURROGATE = ("surrogate-gated EOS: ensemble of 4 MLPs 2-128-128-128-2 (BF16 weights, FP32 "
              "accumulation, tensor-core layers) trained on 1e5 MD samples of the config-2 "
-             "distribution; requests above the disagreement threshold fall back to 4000-atom "
-             "MD; threshold tuned to 1% pressure error against 4000-atom MD")
+             "(rho*, T*) distribution at the fallback's box size (4000 atoms; --train-natoms 0: "
+             "the config-2 size mix); requests above the disagreement threshold fall back to "
+             "4000-atom MD; threshold tuned to 1% pressure error against 4000-atom MD")
 
 
 def surrogate(args):
@@ -833,8 +834,9 @@ def main():
     ap.add_argument("--val-n", type=int, default=2000, help="surrogate: validation queries")
     ap.add_argument("--test-n", type=int, default=4000, help="surrogate: test queries")
     ap.add_argument("--epochs", type=int, default=40, help="surrogate: training epochs")
-    ap.add_argument("--train-natoms", type=int, default=0,
-                    help="surrogate: one box size for the training MD (0: the config-2 mix)")
+    ap.add_argument("--train-natoms", type=int, default=4000,
+                    help="surrogate: box size of the training MD (default: the 4000 atoms of "
+                         "the MD fallback; 0: the config-2 size mix)")
     ap.add_argument("--queries", type=int, default=1 << 23, help="surrogate-infer: queries")
     ap.add_argument("--workload", choices=["uneven", "coupled", "serving", "surrogate",
                                            "surrogate-infer"],
