@@ -504,6 +504,12 @@ mdeos_status mdeos_debug_gemm_bf16(const uint16_t* A, const uint16_t* B, float* 
                                    int32_t N, int32_t K, int64_t sa_m, int64_t sa_k, int64_t sb_k,
                                    int64_t sb_n, int64_t sc_m, int64_t sc_n, void* stream);
 
+/* The surrogate's hidden-layer tanh on its own: y[i] = tanh(x[i]) for n device floats
+ * (relative error below 2e-6: an exp2 form, and an odd series below |x| = 1/4).
+ * Synchronous on `stream` (cudaStream_t).  Errors: MDEOS_EINVAL (NULL, n < 1),
+ * MDEOS_ECUDA. */
+mdeos_status mdeos_debug_tanh(const float* x, float* y, int32_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,7 +37,7 @@ EXPORTED = [
     "mdeos_surrogate_create", "mdeos_surrogate_set_params", "mdeos_surrogate_get_params",
     "mdeos_surrogate_grads", "mdeos_surrogate_train", "mdeos_surrogate_predict",
     "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_surrogate_set_infer_path",
-    "mdeos_surrogate_infer_device", "mdeos_debug_gemm_bf16",
+    "mdeos_surrogate_infer_device", "mdeos_debug_gemm_bf16", "mdeos_debug_tanh",
     "mdeos_autotune",
 ]
 SURROGATE_NPARAM = 33666
@@ -198,6 +198,7 @@ def lib():
         L.mdeos_surrogate_infer_device.argtypes = [vp, vp, i32, vp, vp, vp]
         L.mdeos_autotune.argtypes = [vp, vp, i32, i32, vp, i32, P(i32)]
         i64 = ctypes.c_int64
+        L.mdeos_debug_tanh.argtypes = [vp, vp, i32, vp]
         L.mdeos_debug_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i64, i64, i64, i64, i64,
                                             i64, vp]
         for name in EXPORTED:
@@ -629,6 +630,15 @@ def mdeos_debug_gemm_bf16(A_bits, B_bits, M, N, K, sa, sb, sc, stream=None):
     _check(lib().mdeos_debug_gemm_bf16(_dptr(A_bits), _dptr(B_bits), _dptr(C), M, N, K, sa[0],
                                        sa[1], sb[0], sb[1], sc[0], sc[1], _stream_ptr(stream)))
     return C
+
+
+def mdeos_debug_tanh(x, stream=None):
+    """The surrogate's hidden-layer tanh on a torch cuda float32 tensor."""
+    import torch
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(lib().mdeos_debug_tanh(_dptr(x), _dptr(y), x.numel(), _stream_ptr(stream)))
+    return y
 
 
 def e_from_temperature(T, natoms):

@@ -122,6 +122,26 @@ __global__ void __launch_bounds__(128) bf16_gemm_kernel(GemmArgs g) {
 // ---------------------------------------------------------------------------
 // elementwise parts; index layout [model][sample][unit]
 
+// tanh for the hidden layers, whose outputs are rounded to bf16 next (half an ulp:
+// 2^-9 relative).  |x| >= 1/4: tanh|x| = 1 - 2 / (1 + e^{2|x|}) with e^{2|x|} =
+// 2^{2|x| log2 e} from ex2.approx and the reciprocal from rcp.approx; |x| < 1/4, where
+// that form cancels: the odd series x (1 - x^2/3 + 2x^4/15 - 17x^6/315), whose first
+// omitted term is below 4e-7 relative there.  Relative error below 2e-6 everywhere
+// (3.8e-7 with exact exp2 and division; the approximate instructions add at most ~5e-7,
+// largest near |x| = 1/4), so a bf16 rounding differs from that of the exact tanh only
+// within 2e-6 of a rounding boundary.  Saturates to +-1 for large |x|; NaN stays NaN.
+__device__ __forceinline__ float tanh_act(float x) {
+  const float ax = fabsf(x);
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(ax * 2.885390081777927f));  // 2 log2(e)
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+  const float big = fmaf(-2.0f, r, 1.0f);
+  const float x2 = x * x;
+  const float small =
+      ax * fmaf(x2, fmaf(x2, fmaf(x2, -17.0f / 315.0f, 2.0f / 15.0f), -1.0f / 3.0f), 1.0f);
+  return copysignf(ax < 0.25f ? small : big, x);
+}
+
 // refresh the bf16 weight copies from the FP32 master parameters
 __global__ void mlp_cast_weights(const float* P, __nv_bfloat16* W1b, __nv_bfloat16* W2b,
                                  __nv_bfloat16* W3b, __nv_bfloat16* W4b, int E) {
@@ -147,7 +167,7 @@ __global__ void mlp_layer1(const float* X, const float* P, const __nv_bfloat16* 
   const float w0 = __bfloat162float(W1b[(long long)e * 2 * kH + 2 * j]);
   const float w1 = __bfloat162float(W1b[(long long)e * 2 * kH + 2 * j + 1]);
   const float z = X[2 * b] * w0 + X[2 * b + 1] * w1 + P[(long long)e * kNParam + kOffB1 + j];
-  H1[i] = __float2bfloat16_rn(tanhf(z));
+  H1[i] = __float2bfloat16_rn(tanh_act(z));
 }
 
 // h = bf16(tanh(Z + b)) for layers 2 and 3
@@ -156,7 +176,7 @@ __global__ void mlp_bias_tanh(const float* Z, const float* P, int off_b, __nv_bf
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= (long long)E * B * kH) return;
   const int j = (int)(i % kH), e = (int)(i / ((long long)B * kH));
-  Hout[i] = __float2bfloat16_rn(tanhf(Z[i] + P[(long long)e * kNParam + off_b + j]));
+  Hout[i] = __float2bfloat16_rn(tanh_act(Z[i] + P[(long long)e * kNParam + off_b + j]));
 }
 
 // y = W4 h3 + b4 (FP32 accumulation); with targets: dy = 2 (y - t) / (2 B) and the
@@ -319,7 +339,11 @@ constexpr int kTcRows = 128;                   // samples per tile (TMEM lanes)
 constexpr int kTcThreads = 256;                // two threads per row (column halves)
 constexpr uint32_t kLbo = 128, kSbo = 2048;    // bytes
 constexpr int kTcTile = kH * kH * 2;           // 32 KB per operand tile
-constexpr int kTcSmem = 3 * kTcTile + 1024 + 64;
+// FP32 copies of the small parameters behind the tiles and the mbarrier: W1 as
+// (w_c0, w_c1) pairs, b1, b2, b3, W4 (output-major), b4
+constexpr int kTcSW1 = 0, kTcSB1 = kTcSW1 + 2 * kH, kTcSB2 = kTcSB1 + kH, kTcSB3 = kTcSB2 + kH;
+constexpr int kTcSW4 = kTcSB3 + kH, kTcSB4 = kTcSW4 + 2 * kH, kTcSmall = kTcSB4 + 4;
+constexpr int kTcSmem = 3 * kTcTile + 1024 + 64 + kTcSmall * 4;
 
 __device__ __forceinline__ uint32_t tc_off(int r, int k) {
   return (uint32_t)((r >> 3) * kSbo + (k >> 3) * kLbo + (r & 7) * 16 + (k & 7) * 2);
@@ -392,7 +416,7 @@ __device__ __forceinline__ uint4 tanh_pack8(const float* z, const float* bias) {
   __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&pk);
 #pragma unroll
   for (int j = 0; j < 8; j += 2)
-    h[j >> 1] = __floats2bfloat162_rn(tanhf(z[j] + bias[j]), tanhf(z[j + 1] + bias[j + 1]));
+    h[j >> 1] = __floats2bfloat162_rn(tanh_act(z[j] + bias[j]), tanh_act(z[j + 1] + bias[j + 1]));
   return pk;
 }
 
@@ -416,8 +440,18 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* X
   const int m = tid & (kTcRows - 1), half = tid >> 7, c_lo = half * (kH / 2);
   const int ntiles = (B + kTcRows - 1) / kTcRows;
   const float* p = P + (long long)e * kNParam;
-  const __nv_bfloat16* w1 = W1b + (long long)e * 2 * kH;
-  const __nv_bfloat16* w4 = W4b + (long long)e * 2 * kH + half * kH;  // output unit = half
+  float* sp = reinterpret_cast<float*>(gbase + 3 * kTcTile + 64);  // small parameters
+  for (int k = tid; k < 2 * kH; k += kTcThreads) {  // the bf16-rounded weights, as FP32
+    sp[kTcSW1 + k] = __bfloat162float(W1b[(long long)e * 2 * kH + k]);
+    sp[kTcSW4 + k] = __bfloat162float(W4b[(long long)e * 2 * kH + k]);
+  }
+  for (int k = tid; k < kH; k += kTcThreads) {
+    sp[kTcSB1 + k] = p[kOffB1 + k];
+    sp[kTcSB2 + k] = p[kOffB2 + k];
+    sp[kTcSB3 + k] = p[kOffB3 + k];
+  }
+  if (tid < 2) sp[kTcSB4 + tid] = p[kOffB4 + tid];
+  const float* w4 = sp + kTcSW4 + half * kH;  // output unit = half
   // weights of this model into the canonical layout, 16 bytes at a time; consecutive
   // threads fill consecutive 16-byte rows of the core matrices (no bank conflicts)
   for (int q = tid; q < kH * kH / 8; q += kTcThreads) {
@@ -453,9 +487,11 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* X
     for (int c = c_lo; c < c_lo + kH / 2; c += 8) {
       float z[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        z[j] = x0 * __bfloat162float(w1[2 * (c + j)]) + x1 * __bfloat162float(w1[2 * (c + j) + 1]);
-      *reinterpret_cast<uint4*>(gA + tc_off(m, c)) = tanh_pack8(z, p + kOffB1 + c);
+      for (int j = 0; j < 8; ++j) {
+        const float2 w = *reinterpret_cast<const float2*>(sp + kTcSW1 + 2 * (c + j));
+        z[j] = x0 * w.x + x1 * w.y;
+      }
+      *reinterpret_cast<uint4*>(gA + tc_off(m, c)) = tanh_pack8(z, sp + kTcSB1 + c);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // h1 -> tensor core
     __syncthreads();
@@ -475,7 +511,7 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* X
       if (!ok) break;
       // epilogue: h = bf16(tanh(z + b)) of this row's 64 units -> tile A (the MMA that
       // read it has completed): h2 feeds layer 3, h3 the output layer
-      const float* bias = p + (layer == 0 ? kOffB2 : kOffB3) + c_lo;
+      const float* bias = sp + (layer == 0 ? kTcSB2 : kTcSB3) + c_lo;
 #pragma unroll 1
       for (int c0 = 0; c0 < kH / 2; c0 += 32) {
         float v[32];
@@ -500,11 +536,11 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* X
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float2 hf = __bfloat1622float2(h[j]);
-        y = fmaf(__bfloat162float(w4[c + 2 * j]), hf.x, y);
-        y = fmaf(__bfloat162float(w4[c + 2 * j + 1]), hf.y, y);
+        y = fmaf(w4[c + 2 * j], hf.x, y);
+        y = fmaf(w4[c + 2 * j + 1], hf.y, y);
       }
     }
-    if (b < B) Y[((long long)e * B + b) * 2 + half] = y + p[kOffB4 + half];
+    if (b < B) Y[((long long)e * B + b) * 2 + half] = y + sp[kTcSB4 + half];
     __syncthreads();  // tile A is rewritten by the next tile's layer 1
   }
   if (!ok) {  // NaN for this CTA's unfinished tiles; let MMAs in flight finish (bounded)
@@ -521,6 +557,11 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* X
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kH)
                  : "memory");
+}
+
+__global__ void debug_tanh_kernel(const float* x, float* y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = tanh_act(x[i]);
 }
 
 }  // namespace mdeos
@@ -973,6 +1014,15 @@ extern "C" mdeos_status mdeos_debug_gemm_bf16(const uint16_t* A, const uint16_t*
   SCK(gemm(st, reinterpret_cast<const __nv_bfloat16*>(A),
            reinterpret_cast<const __nv_bfloat16*>(B), C, M, N, K, sa_m, sa_k, 0, sb_k, sb_n, 0,
            sc_m, sc_n, 0, 1));
+  SCK(cudaStreamSynchronize(st));
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_debug_tanh(const float* x, float* y, int32_t n, void* stream) {
+  if (!x || !y || n < 1) return set_error(MDEOS_EINVAL, "bad tanh arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  debug_tanh_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, y, n);
+  SCK(cudaGetLastError());
   SCK(cudaStreamSynchronize(st));
   return MDEOS_OK;
 }

@@ -57,6 +57,26 @@ def test_tensor_core_gemm(m, M, N, K, ta, tb):
     assert (np.abs(C - ref) <= bound).all()
 
 
+def test_hidden_layer_tanh_error_bound(m):
+    """The kernels' own tanh (exp2 form, odd series below 1/4) against the exact tanh:
+    relative error below 2e-6 on a dense grid, across the branch point, for tiny and
+    huge arguments; saturation and NaN propagation."""
+    import torch
+    g = np.linspace(-12.0, 12.0, 400001)
+    tiny = 10.0 ** np.linspace(-30, -1, 2001)
+    edge = np.array([0.25, np.nextafter(np.float32(0.25), np.float32(0)), 0.2499, 0.2501,
+                     44.0, 88.0, 1e30, 0.0])
+    x = np.concatenate([g, tiny, -tiny, edge, -edge]).astype(np.float32)
+    y = m.mdeos_debug_tanh(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    ref = np.tanh(x.astype(np.float64))
+    nz = np.abs(ref) > 1e-36
+    rel = np.abs(y[nz] - ref[nz]) / np.abs(ref[nz])
+    assert rel.max() < 2e-6, float(rel.max())
+    assert (y[np.abs(x) >= 44.0] == np.sign(x[np.abs(x) >= 44.0])).all()
+    yn = m.mdeos_debug_tanh(torch.tensor([float("nan")], device="cuda")).cpu().numpy()
+    assert np.isnan(yn).all()
+
+
 def _params(seed, E=4):
     rng = np.random.default_rng(seed)
     p = S.init_params(seed, E)
