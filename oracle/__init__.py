@@ -101,6 +101,8 @@ def lib():
         _lib.orc_eos_eval_state.restype = i
         _lib.orc_eos_batch_state.argtypes = [p, i, ctypes.POINTER(Params), p, p, p, p, p, p, i]
         _lib.orc_eos_batch_state.restype = i
+        _lib.orc_block_se.argtypes = [p, i, i, p, p]
+        _lib.orc_block_se.restype = i
     return _lib
 
 
@@ -148,6 +150,16 @@ def lj_forces(x: np.ndarray, L: float, params: Params | None = None, mode: int =
     W = np.zeros(6, dtype=np.float64)
     E = lib().orc_lj_forces(n, _ptr(x), L, ctypes.byref(params), mode, _ptr(f), _ptr(W))
     return E, f, W
+
+
+def block_se(x, nblocks: int):
+    """Block-average (mean, standard error) of a series, the restriction's error bar."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    mean, se = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().orc_block_se(_ptr(x), x.shape[0], nblocks, ctypes.byref(mean), ctypes.byref(se))
+    if st != 0:
+        raise ValueError("orc_block_se: invalid series or block count")
+    return mean.value, se.value
 
 
 def count_pairs(x: np.ndarray, L: float, rc: float = 2.5) -> int:

@@ -409,9 +409,8 @@ static int eos_core(const orc_request* rq, const orc_params* p, const double* x_
   /* Production (NVT) with restriction (Eq. 11) and block averages. */
   if (status == ORC_OK) {
     int nb = p->se_blocks;
-    double* bP = (double*)calloc(nb, sizeof(double));
-    double* bT = (double*)calloc(nb, sizeof(double));
-    int* bn = (int*)calloc(nb, sizeof(int));
+    double* serP = (double*)calloc(rq->steps_avg, sizeof(double)); /* per-step samples */
+    double* serT = (double*)calloc(rq->steps_avg, sizeof(double));
     double sP = 0, sT = 0, sE = 0, sK = 0, sS[6] = {0, 0, 0, 0, 0, 0};
     for (int s = 0; s < rq->steps_avg; ++s) {
       double E = vv_step(n, x, v, f, L, p, W);
@@ -428,8 +427,8 @@ static int eos_core(const orc_request* rq, const orc_params* p, const double* x_
       if (!is_fin(E) || !is_fin(Ps) || !is_fin(Ts)) { status = ORC_EUNPHYS; break; }
       sP += Ps; sT += Ts; sE += E; sK += KE;
       for (int a = 0; a < 6; ++a) sS[a] += (K[a] + W[a]) / V;
-      int b = (int)((long long)s * nb / rq->steps_avg);
-      bP[b] += Ps; bT[b] += Ts; bn[b] += 1;
+      serP[s] = Ps;
+      serT[s] = Ts;
       if (p->rescale_every_avg > 0 && (s + 1) % p->rescale_every_avg == 0)
         rescale_to(n, v, p->mass, Tk);
     }
@@ -441,18 +440,10 @@ static int eos_core(const orc_request* rq, const orc_params* p, const double* x_
       out->epot = sE / m / n;
       out->ekin = sK / m / n;
       out->e_achieved = (sK / m + sE / m - E_ref) / n;
-      double mP = 0, mT = 0;
-      for (int b = 0; b < nb; ++b) { bP[b] /= bn[b]; bT[b] /= bn[b]; mP += bP[b]; mT += bT[b]; }
-      mP /= nb; mT /= nb;
-      double vP = 0, vT = 0;
-      for (int b = 0; b < nb; ++b) {
-        vP += (bP[b] - mP) * (bP[b] - mP);
-        vT += (bT[b] - mT) * (bT[b] - mT);
-      }
-      out->P_se = sqrt(vP / (nb - 1) / nb);
-      out->T_se = sqrt(vT / (nb - 1) / nb);
+      orc_block_se(serP, rq->steps_avg, nb, NULL, &out->P_se);
+      orc_block_se(serT, rq->steps_avg, nb, NULL, &out->T_se);
     }
-    free(bP); free(bT); free(bn);
+    free(serP); free(serT);
   }
   out->status = status;
   if (status == ORC_OK && x_out && v_out) {
@@ -461,6 +452,31 @@ static int eos_core(const orc_request* rq, const orc_params* p, const double* x_
   }
   free(x); free(v); free(f);
   return status;
+}
+
+/* Block-average standard error of the mean of a series x[0..m) (App. B averages
+ * over the production steps; the error bar is the standard error of the mean
+ * of nb equal-count blocks): block b holds steps s with floor(s nb / m) = b,
+ * mean = (1/nb) sum_b xbar_b, se = sqrt(sum_b (xbar_b - mean)^2 / ((nb - 1) nb)).
+ * For independent samples of variance s^2, E[se^2] = s^2 / m. */
+int orc_block_se(const double* x, int m, int nb, double* mean_out, double* se_out) {
+  if (x == NULL || m < 1 || nb < 2 || nb > m) return ORC_EINVAL;
+  double* bs = (double*)calloc(nb, sizeof(double));
+  int* bn = (int*)calloc(nb, sizeof(int));
+  for (int s = 0; s < m; ++s) {
+    int b = (int)((long long)s * nb / m);
+    bs[b] += x[s];
+    bn[b] += 1;
+  }
+  double mu = 0.0;
+  for (int b = 0; b < nb; ++b) { bs[b] /= bn[b]; mu += bs[b]; }
+  mu /= nb;
+  double v = 0.0;
+  for (int b = 0; b < nb; ++b) v += (bs[b] - mu) * (bs[b] - mu);
+  if (mean_out) *mean_out = mu;
+  if (se_out) *se_out = sqrt(v / (nb - 1) / nb);
+  free(bs); free(bn);
+  return ORC_OK;
 }
 
 int orc_eos_eval(const orc_request* rq, const orc_params* p, orc_result* out) {

@@ -89,6 +89,10 @@ int orc_md_steps(int n, double* x, double* v, double* f, double L, const orc_par
 /* Kinetic energy 1/2 m sum v^2. */
 double orc_kinetic(int n, const double* v, double mass);
 
+/* Block-average mean and standard error of a series of m samples in nb blocks of
+ * (near) equal count: the error bar of the restricted P and T (App. B). */
+int orc_block_se(const double* x, int m, int nb, double* mean_out, double* se_out);
+
 /* Full lifting -> MD -> restriction for one request (Sec. III, Eq. 6-11). */
 int orc_eos_eval(const orc_request* rq, const orc_params* p, orc_result* out);
 

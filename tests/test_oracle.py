@@ -322,3 +322,74 @@ def test_temperature_input_mode(orc):
     assert r["status"] == 0
     assert r["T_target"] == 1.4
     assert abs(r["T"] - 1.4) < 5 * r["T_se"] + 0.02
+
+
+# --------------------------------------------------------------------------
+# restriction error bar: block-average standard error (App. B averaging)
+
+def test_block_se_of_independent_samples_follows_chi_square(orc):
+    """For independent N(mu, s^2) samples, (nb - 1) m se^2 / s^2 is chi-square
+    with nb - 1 degrees of freedom: mean nb - 1, variance 2 (nb - 1).  A dropped
+    1/nb, a 1/nb in place of 1/(nb - 1), or block sums in place of block means
+    moves the mean of m se^2 / s^2 away from 1 by 10 % or more."""
+    rng = np.random.default_rng(2025)
+    m, nb, s, reps = 1000, 10, 2.0, 4000
+    z = np.empty(reps)
+    for k in range(reps):
+        x = rng.normal(3.0, s, m)
+        mean, se = orc.block_se(x, nb)
+        assert abs(mean - x.mean()) < 1e-12 * 3.0  # equal blocks: mean of block means
+        z[k] = m * se * se / (s * s)
+    # mean 1, sd of the mean sqrt(2 / 9) / sqrt(4000) = 0.0075
+    assert abs(z.mean() - 1.0) < 0.03
+    # variance of chi2(9) / 9 is 2 / 9
+    assert abs(z.var() / (2.0 / (nb - 1)) - 1.0) < 0.15
+
+
+def test_block_se_of_correlated_series_matches_closed_form(orc):
+    """AR(1) series x_t = phi x_(t-1) + eps_t: the variance of the mean of m
+    samples is s_x^2 (1 + phi) / ((1 - phi) m) for m >> 1/(1 - phi), with
+    s_x^2 = s_eps^2 / (1 - phi^2).  Blocks much longer than the correlation time
+    recover it; treating the samples as independent would miss by a factor 39."""
+    from scipy.signal import lfilter
+    rng = np.random.default_rng(7)
+    phi, m, nb, reps = 0.95, 200000, 20, 200
+    sx2 = 1.0 / (1.0 - phi * phi)
+    true_var = sx2 * (1.0 + phi) / ((1.0 - phi) * m)
+    ratios = []
+    for _ in range(reps):
+        eps = rng.normal(0.0, 1.0, m)
+        x0 = rng.normal(0.0, np.sqrt(sx2))
+        x = lfilter([1.0], [1.0, -phi], eps, zi=[phi * x0])[0]
+        _, se = orc.block_se(x, nb)
+        ratios.append(se * se / true_var)
+    # per-replicate relative sd sqrt(2/19) = 0.32; mean of 200: 0.023
+    assert abs(np.mean(ratios) - 1.0) < 0.1
+
+
+def test_block_se_rejects_bad_block_counts(orc):
+    with pytest.raises(ValueError):
+        orc.block_se(np.zeros(5), 1)
+    with pytest.raises(ValueError):
+        orc.block_se(np.zeros(5), 6)
+    # unequal blocks: floor(s nb / m) assigns 7 samples to 3 blocks as 3, 2, 2
+    mean, se = orc.block_se(np.array([0.0, 0.0, 0.0, 3.0, 3.0, 6.0, 6.0]), 3)
+    assert mean == pytest.approx(3.0, abs=1e-15)
+    assert se == pytest.approx(np.sqrt(18.0 / 2.0 / 3.0), rel=1e-15)
+
+
+def test_ensemble_spread_matches_reported_se(orc):
+    """32 independent seeds of one LJ state at fixed temperature: the spread of
+    the per-seed mean pressures must agree with the reported P_se.  The ratio
+    var(means) / mean(P_se^2) is chi-square(31)/31 distributed for a correct
+    error bar (widened for the noise of the 32 error estimates themselves)."""
+    from scipy.stats import chi2
+    reqs = [dict(rho=0.8, e=1.4, natoms=108, steps_equil=400, steps_avg=1000,
+                 seed=1000 + 17 * k, flags=orc.REQ_TEMPERATURE) for k in range(32)]
+    res = orc.eos_batch(reqs)
+    assert all(r["status"] == 0 for r in res)
+    P = np.array([r["P"] for r in res])
+    se2 = np.array([r["P_se"] for r in res]) ** 2
+    ratio = P.var(ddof=1) / se2.mean()
+    lo, hi = chi2.ppf([0.0005, 0.9995], 31) / 31
+    assert 0.75 * lo <= ratio <= 1.25 * hi, ratio
