@@ -52,6 +52,11 @@ WORKLOAD = ("batched uneven MD-EOS: 4096 LJ boxes, N=4n^3 n~U{3..10} (108-4000 a
             "production steps, one persistent graph-captured launch")
 
 
+CONFIG1 = ("16 independent LJ MD-EOS queries, one box each: N=256 (FCC 4x4x4), rho*~U[0.5,1.0], "
+           "T*~U[1.0,2.0], rc=2.5, dt=0.005, 1000 lifting + 1000 production steps, one "
+           "persistent graph-captured launch")
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -141,10 +146,15 @@ def gpu_requests(m, boxes):
                  element_id=b["element_id"]) for b in boxes]
 
 
-def cpu_sample(per_class=2, steps_equil=100, steps_avg=100):
+def cpu_sample(per_class=2, steps_equil=100, steps_avg=100, workload="uneven"):
     """Bounded sample of the workload for the CPU oracle: 2 boxes of every atom
-    count with 200 of the 2000 steps; EOS/s is scaled by the step fraction."""
+    count with 200 of the 2000 steps (the 16-box batch: all boxes, 400 of 2000
+    steps); EOS/s is scaled by the step fraction."""
     from paper_2508_06012_gb300 import workloads as w
+    if workload == "config1":
+        boxes = [dict(b, steps_equil=200, steps_avg=200) for b in w.config1()]
+        return boxes, 400 / 2000.0, ("16 boxes x 400 of 2000 steps (N=256), FP64 linked-cell "
+                                     "oracle, OpenMP")
     boxes = w.stratified(w.config2(), per_class, steps_equil, steps_avg)
     frac = (steps_equil + steps_avg) / 2000.0
     desc = (f"{len(boxes)} boxes ({per_class} per atom count 108..4000) x "
@@ -170,7 +180,7 @@ def reference_arm(args):
         return
     import oracle as orc
     orc.build()
-    boxes, frac, desc = cpu_sample()
+    boxes, frac, desc = cpu_sample(workload=args.workload)
     for _ in range(args.warmup):
         run_cpu_sample(orc, boxes)
     times = [run_cpu_sample(orc, boxes) for _ in range(args.steps)]
@@ -182,7 +192,8 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1000.0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": desc},
+        "config": {"workload": CONFIG1 if args.workload == "config1" else WORKLOAD,
+                   "sample": desc},
         "cpu_baseline": {"value": value, "unit": "EOS/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "EOS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -204,7 +215,9 @@ def ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     m.build()
-    if args.boxes or args.md_steps:
+    if args.workload == "config1":
+        boxes = w.config1(base_seed=20250806 + rank)
+    elif args.boxes or args.md_steps:
         half = (args.md_steps or 2000) // 2
         boxes = w.config2(base_seed=20250807 + rank, nbox=args.boxes or 4096,
                           steps_equil=half, steps_avg=half)
@@ -220,7 +233,8 @@ def ours(args):
         tab = m.mdeos_autotune(h, reqs, steps=200)
         tune = {"seconds": time.perf_counter() - t_tune,
                 "trial_launches": m.mdeos_stats(h)["launches"] - l0,
-                "skin_by_natoms": {str(int(r[0])): float(r[1]) for r in tab}}
+                "skin_by_natoms": {str(int(r[0])): float(r[1]) for r in tab},
+                "warps_by_natoms": {str(int(r[0])): int(r[2]) for r in tab}}
     b = m.mdeos_batch_create(h, reqs)
     info = m.mdeos_batch_info(b)
     stream = torch.cuda.Stream()
@@ -313,7 +327,7 @@ def ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle as orc
         orc.build()
-        sboxes, frac, desc = cpu_sample()
+        sboxes, frac, desc = cpu_sample(workload=args.workload)
         t = run_cpu_sample(orc, sboxes)
         v = len(sboxes) * frac / t
         cpu = {"value": v, "unit": "EOS/s", "cores": orc.max_threads(), "kind": "oracle",
@@ -325,8 +339,10 @@ def ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded LJ boxes; no datasets or trained weights)",
-            "config": {"workload": WORKLOAD if not (args.boxes or args.md_steps) else
-                       f"reduced: {nbox} boxes x {args.md_steps or 2000} steps of " + WORKLOAD,
+            "config": {"workload": (CONFIG1 if args.workload == "config1" else
+                                    WORKLOAD if not (args.boxes or args.md_steps) else
+                                    f"reduced: {nbox} boxes x {args.md_steps or 2000} steps of "
+                                    + WORKLOAD),
                        "boxes_per_gpu": nbox,
                        "l2": "flushed between timed iterations (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (independent boxes)",
@@ -334,6 +350,7 @@ def ours(args):
             "pairs_per_s": pairs_per_launch * args.steps * world / (dev_ms_max / 1000.0),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": clk, "wall_s_timed": wall,
+            "batch_latency_ms": {"median": float(np.median(kms)), "max": float(np.max(kms))},
         }
         print(json.dumps(line), flush=True)
     m.mdeos_batch_destroy(b)
@@ -838,11 +855,11 @@ def main():
                     help="surrogate: box size of the training MD (default: the 4000 atoms of "
                          "the MD fallback; 0: the config-2 size mix)")
     ap.add_argument("--queries", type=int, default=1 << 23, help="surrogate-infer: queries")
-    ap.add_argument("--workload", choices=["uneven", "coupled", "serving", "surrogate",
-                                           "surrogate-infer"],
+    ap.add_argument("--workload", choices=["uneven", "config1", "coupled", "serving",
+                                           "surrogate", "surrogate-infer"],
                     default="uneven",
-                    help="uneven: 4096-box batched EOS (default); coupled: MD-closed hydro; "
-                         "serving: Poisson request stream")
+                    help="uneven: 4096-box batched EOS (default); config1: 16 boxes of 256 "
+                         "atoms; coupled: MD-closed hydro; serving: Poisson request stream")
     ap.add_argument("--rates", default="50,100,200,300", help="serving: arrival rates (1/s)")
     ap.add_argument("--duration", type=float, default=15.0, help="serving: seconds per rate")
     ap.add_argument("--max-wait", type=float, default=10.0, help="serving: shed after (s)")

@@ -83,7 +83,10 @@ typedef struct {
   int32_t warm_lift_iters;     /* Eq. 10 segments after a warm start; default 1 */
   int32_t warm_slots;          /* elements kept; 0 = no warm store */
   int32_t warm_atoms;          /* atoms per stored element (>= natoms of its requests) */
-  int32_t reserved0;
+  int32_t nlist_capacity;      /* Verlet-list entries per atom; 0 = from the density (1.3 x
+                                  the neighbours within rc + skin at the box density, or at
+                                  rho = 0.9 if higher, + 32).  A box whose list overflows is
+                                  re-run by mdeos_poll with twice the capacity. */
 } mdeos_config;
 
 /* One EOS query.  Layout is part of the ABI. */
@@ -119,7 +122,7 @@ typedef struct {
   int32_t nlist_builds;/* neighbour-list rebuilds (diagnostic) */
   int32_t path;        /* force path used: 0 all-pairs, 1 all-pairs multi-image, 2 Verlet list */
   int32_t warm;        /* 1 if lifted from the element's stored state, else 0 */
-  int32_t reserved0;
+  int32_t nlist_retries; /* re-runs after a neighbour-list overflow (mdeos_poll) */
 } mdeos_result;
 
 typedef struct mdeos_handle mdeos_handle;
@@ -147,7 +150,12 @@ mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs, int32_t n,
  * for a ticket.  On MDEOS_OK the n results are written to `out` (host,
  * caller-owned, n entries, request order) and the ticket is released.
  * Returns MDEOS_PENDING if not done in time, MDEOS_EINVAL for an unknown
- * ticket, MDEOS_ECUDA if the device work failed. */
+ * ticket, MDEOS_ECUDA if the device work failed.  Boxes whose Verlet list
+ * overflowed (MDEOS_ENBR) are first re-run here with twice the list capacity, as
+ * often as needed up to a capacity of every other atom, with the same warm-start
+ * slot; result.nlist_retries counts the re-runs.  The re-runs are synchronous, so
+ * such a poll takes correspondingly longer.  Batches (mdeos_batch_*) and
+ * mdeos_submit_noalloc report MDEOS_ENBR without re-running. */
 mdeos_status mdeos_poll(mdeos_handle* h, uint64_t ticket, mdeos_result* out, int32_t timeout_us);
 
 /* Release the handle; waits for outstanding work. */
@@ -191,9 +199,8 @@ mdeos_status mdeos_stats(const mdeos_handle* h, size_t* last_h2d_bytes, size_t* 
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory where they need an EOS answer (a material-model
  * callback inside a hydrocode's time step, where cudaMalloc would synchronise
- * the device; code whose device memory is owned by a pool; host threads that
- * must not block).  It calls no cudaMalloc, cudaFree or other allocating
- * routine.  Its work table, queue counter and Verlet lists live in a static
+ * the device; code whose device memory is owned by a pool).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its work table, queue counter and Verlet lists live in a static
  * device array of MDEOS_NOALLOC_SCRATCH_BYTES that every GPU loading this
  * library holds until exit.
  *
@@ -202,10 +209,15 @@ mdeos_status mdeos_stats(const mdeos_handle* h, size_t* last_h2d_bytes, size_t* 
  * d_results: device array of n mdeos_result, caller-owned; written in request
  *            order when the work on `stream` completes (requests rejected by
  *            the planner get their status there too).
- * stream:    cudaStream_t (NULL = legacy default stream); asynchronous.
+ * stream:    cudaStream_t (NULL = legacy default stream).  The kernel runs
+ *            asynchronously, but the work table is copied to the device from
+ *            pageable host memory that the call owns, and such a copy may wait
+ *            for earlier work on `stream` before the call returns: do not rely
+ *            on this call not blocking.  A stream that is being captured into a
+ *            CUDA graph is refused with MDEOS_EINVAL (the recorded copies would
+ *            point at host memory freed on return).
  * The first call on a device looks up the static array's device address and
- * sets the kernel's shared-memory limit; make that first call before any
- * stream capture.  Every call reuses the same array (it keeps the previous
+ * sets the kernel's shared-memory limit.  Every call reuses the same array (it keeps the previous
  * call's contents; the call clears what must start at zero): calls whose work
  * overlaps on the GPU race, so serialise them (one stream, or events).  A batch
  * whose work table plus one CTA's Verlet lists exceed the array is rejected
@@ -218,14 +230,19 @@ mdeos_status mdeos_submit_noalloc(const mdeos_config* cfg, const mdeos_request* 
                                   mdeos_result* d_results, void* stream);
 
 /* ---- autotuner ----------------------------------------------------------
- * The Verlet skin trades list rebuilds (rarer with a larger skin) against pair
- * candidates per step (more with a larger skin); the best value depends on the box
- * size.  For every atom count among the Verlet-list boxes of reqs (host, n), one
- * full-GPU wave of such boxes (cycled from reqs, `steps` MD steps each) is timed with
- * CUDA events for each skin in {0.2, 0.25, 0.3, 0.35, 0.4, 0.5}; the fastest whose
- * boxes all succeed is kept in the handle and used by later planning of boxes with
- * that atom count while cfg.skin <= 0.  table (host double[3 * max_out], may be NULL)
- * receives (natoms, skin, ms per box) rows and *n_out their number.  Synchronous.
+ * Two launch choices per box size have no a-priori best value on a given GPU: the
+ * Verlet skin (rarer list rebuilds with a larger skin against more pair
+ * candidates per step) and the warps that run one box (more warps: more
+ * parallelism per box, fewer boxes per CTA).  For every atom count among the
+ * Verlet-list boxes of reqs (host, n), one full-GPU wave of such boxes (cycled from
+ * reqs, `steps` MD steps each) is timed with CUDA events for every skin in
+ * {0.2, 0.25, 0.3, 0.35, 0.4, 0.5} and the planner's warps per box and up to two
+ * doublings of it (at most 32); the fastest shape per box whose boxes all succeed
+ * is kept in the handle and used by later planning of that atom count while
+ * cfg.skin <= 0 (the skin) and for batches that fill the GPU (the warps; a batch
+ * with no more boxes than SMs runs each box in its own CTA, one atom per thread).
+ * table (host double[4 * max_out], may be NULL) receives (natoms, skin, warps per
+ * box, ms of GPU time per box) rows and *n_out their number.  Synchronous.
  * Errors: MDEOS_EINVAL (steps < 20), MDEOS_ENOMEM, MDEOS_ECUDA. */
 mdeos_status mdeos_autotune(mdeos_handle* h, const mdeos_request* reqs, int32_t n, int32_t steps,
                             double* table, int32_t max_out, int32_t* n_out);
@@ -336,15 +353,32 @@ mdeos_status mdeos_hydro_destroy(mdeos_hydro* hy);
  * published into host-mapped rings; every SM takes the next item as soon as it
  * finishes one, and each request is reported as soon as its box is done (result
  * and ready flag in host-mapped memory).  An idle grid exits after idle_ms and is
- * relaunched when work arrives.  Warm starts are not used here. */
+ * relaunched when work arrives.
+ *
+ * Element states (warm = 1): the server keeps each element's final MD state in a
+ * device store and lifts the element's next request from it, as the handle's warm
+ * store does (warm_lift_iters of the handle's configuration).  A stored element
+ * takes 16 + 32 B per atom (requests above 4096 atoms run cold, not stored).  A
+ * request is admitted only when its element's state has room: memory of elements
+ * with no request in flight is reclaimed least recently used first; while the rest
+ * of the store is held by requests in flight, the request waits in the queue and is
+ * admitted as their results come back (so the store, within hbm_budget_bytes, bounds
+ * the device memory however many requests arrive).  A second request for an element
+ * whose previous request is still in flight waits for it.  Requests with
+ * element_id 0 need no store memory. */
 typedef struct {
   int32_t max_inflight;     /* requests admitted to the GPU and not finished, default 4096 */
   int32_t max_batch;        /* requests planned together per admission step, default 2048 */
   double max_wait_s;        /* waiting longer than this: shed (MDEOS_ECANCELLED); 0 = never */
   int32_t max_queue;        /* waiting requests beyond this are shed on arrival; 0 = no cap */
   int32_t idle_ms;          /* an idle kernel exits after this long, default 20 */
-  size_t hbm_budget_bytes;  /* device memory the server may hold (per-SM scratch for the
-                               largest box, 32768 atoms); creation fails above it; 0 = no cap */
+  size_t hbm_budget_bytes;  /* device memory the server may hold: the per-SM scratch for the
+                               largest box (32768 atoms) plus the element store; creation
+                               fails if the scratch alone exceeds it; 0 = no cap */
+  int32_t warm;             /* 1: keep element states for warm starts (see above); 0: off */
+  int32_t reserved0;
+  size_t warm_bytes;        /* element store size; 0 = what hbm_budget_bytes leaves after the
+                               scratch (1 GiB without a budget) */
 } mdeos_serve_config;
 
 /* One finished request.  Times are seconds on the server clock (mdeos_serve_clock):
@@ -386,6 +420,12 @@ mdeos_status mdeos_serve_completed(mdeos_server* s, mdeos_served* out, int32_t m
  * kernel launches, waiting now, CUDA failures; bytes (host size_t[2], may be NULL):
  * device bytes held by the server and the peak number of requests in flight. */
 mdeos_status mdeos_serve_stats(mdeos_server* s, long long* counts, size_t* bytes);
+
+/* Element store counters: counts (host int64[4], may be NULL): warm-started
+ * requests, admissions that waited for store memory, states evicted, elements
+ * stored now; bytes (host size_t[2], may be NULL): store bytes in use (reserved by
+ * stored elements) and the store's size. */
+mdeos_status mdeos_serve_store_stats(mdeos_server* s, long long* counts, size_t* bytes);
 
 /* Stop: waiting requests are shed, in-flight launches finish; then release. */
 mdeos_status mdeos_serve_destroy(mdeos_server* s);
@@ -496,6 +536,17 @@ mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float* v4, int32
                             int32_t steps, double T_target, int32_t rescale_every, int32_t path,
                             double skin, double* epot, double* ekin, long long* cycles,
                             void* stream);
+
+/* The pair-force pass on its own (measurement of the force kernel): nbox boxes of
+ * n atoms (device x4: float4[nbox * n], box b at x4 + 4 n b), one per CTA and at
+ * most one per SM, each kept in shared memory with its Verlet list (skin) built
+ * once, then `passes` force passes as the step loop runs them: mode 0 forces only,
+ * mode 1 forces with energy, virial and pair count.  cycles (device int64[2 nbox])
+ * receives per box the SM cycles of the passes and the list entries per pass.
+ * Synchronous on `stream`.  Errors: MDEOS_EINVAL, MDEOS_ENOMEM, MDEOS_ECUDA. */
+mdeos_status mdeos_debug_force_bench(const mdeos_config* cfg, const float* x4, int32_t nbox,
+                                     int32_t n, double L, double skin, int32_t passes,
+                                     int32_t mode, long long* cycles, void* stream);
 
 /* The surrogate's tensor-core GEMM on its own: C(m, n) = sum_k A(m, k) B(k, n) with
  * A(m, k) = A[m * sa_m + k * sa_k], B(k, n) = B[k * sb_k + n * sb_n] (device bfloat16

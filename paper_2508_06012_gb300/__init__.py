@@ -29,11 +29,12 @@ EXPORTED = [
     "mdeos_last_error", "mdeos_batch_create", "mdeos_batch_launch",
     "mdeos_batch_device_results", "mdeos_batch_results", "mdeos_batch_destroy",
     "mdeos_batch_info", "mdeos_stats", "mdeos_debug_lift", "mdeos_debug_forces",
-    "mdeos_debug_md", "mdeos_submit_noalloc", "mdeos_warm_export", "mdeos_warm_import",
-    "mdeos_warm_reset", "mdeos_hydro_config_default", "mdeos_hydro_create", "mdeos_hydro_step",
+    "mdeos_debug_md", "mdeos_debug_force_bench", "mdeos_submit_noalloc", "mdeos_warm_export",
+    "mdeos_warm_import", "mdeos_warm_reset", "mdeos_hydro_config_default", "mdeos_hydro_create", "mdeos_hydro_step",
     "mdeos_hydro_state", "mdeos_hydro_eos_results", "mdeos_hydro_destroy",
     "mdeos_serve_config_default", "mdeos_serve_create", "mdeos_serve_clock",
-    "mdeos_serve_enqueue", "mdeos_serve_completed", "mdeos_serve_stats", "mdeos_serve_destroy",
+    "mdeos_serve_enqueue", "mdeos_serve_completed", "mdeos_serve_stats",
+    "mdeos_serve_store_stats", "mdeos_serve_destroy",
     "mdeos_surrogate_create", "mdeos_surrogate_set_params", "mdeos_surrogate_get_params",
     "mdeos_surrogate_grads", "mdeos_surrogate_train", "mdeos_surrogate_predict",
     "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_surrogate_set_infer_path",
@@ -53,7 +54,7 @@ class mdeos_config(ctypes.Structure):
         ("rc", ctypes.c_double), ("dt", ctypes.c_double), ("skin", ctypes.c_double),
         ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
         ("warm_lift_iters", ctypes.c_int32), ("warm_slots", ctypes.c_int32),
-        ("warm_atoms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("warm_atoms", ctypes.c_int32), ("nlist_capacity", ctypes.c_int32),
     ]
 
 
@@ -75,7 +76,7 @@ class mdeos_result(ctypes.Structure):
         ("cand_per_step", ctypes.c_double), ("element_id", ctypes.c_uint64),
         ("natoms", ctypes.c_int32), ("status", ctypes.c_int32),
         ("nlist_builds", ctypes.c_int32), ("path", ctypes.c_int32),
-        ("warm", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("warm", ctypes.c_int32), ("nlist_retries", ctypes.c_int32),
     ]
 
 
@@ -100,6 +101,7 @@ class mdeos_serve_config(ctypes.Structure):
         ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("max_wait_s", ctypes.c_double), ("max_queue", ctypes.c_int32),
         ("idle_ms", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
+        ("warm", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("warm_bytes", ctypes.c_size_t),
     ]
 
 
@@ -108,7 +110,7 @@ RESULT_DTYPE = np.dtype([
     ("e_achieved", "f8"), ("P_se", "f8"), ("T_se", "f8"), ("T_target", "f8"),
     ("e_cold", "f8"), ("L", "f8"), ("pairs_per_step", "f8"), ("cand_per_step", "f8"),
     ("element_id", "u8"), ("natoms", "i4"), ("status", "i4"), ("nlist_builds", "i4"),
-    ("path", "i4"), ("warm", "i4"), ("reserved0", "i4"),
+    ("path", "i4"), ("warm", "i4"), ("nlist_retries", "i4"),
 ])
 REQUEST_DTYPE = np.dtype([
     ("rho", "f8"), ("e", "f8"), ("e_ref", "f8"), ("natoms", "i4"), ("steps_equil", "i4"),
@@ -166,6 +168,8 @@ def lib():
         L.mdeos_debug_md.argtypes = [P(mdeos_config), vp, vp, i32, d, i32, d, i32, i32, d, vp,
                                      vp, vp, vp]
         L.mdeos_submit_noalloc.argtypes = [P(mdeos_config), vp, i32, vp, vp]
+        L.mdeos_debug_force_bench.argtypes = [P(mdeos_config), vp, i32, i32, d, d, i32, i32, vp,
+                                              vp]
         u64 = ctypes.c_uint64
         L.mdeos_warm_export.argtypes = [vp, u64, i32, vp, vp, P(d)]
         L.mdeos_warm_import.argtypes = [vp, u64, i32, vp, vp, d]
@@ -185,6 +189,7 @@ def lib():
         L.mdeos_serve_enqueue.argtypes = [vp, vp, i32, vp]
         L.mdeos_serve_completed.argtypes = [vp, vp, i32, P(i32)]
         L.mdeos_serve_stats.argtypes = [vp, vp, vp]
+        L.mdeos_serve_store_stats.argtypes = [vp, vp, vp]
         L.mdeos_serve_destroy.argtypes = [vp]
         L.mdeos_surrogate_create.argtypes = [vp, i32, i32, ctypes.c_uint64, P(vp)]
         L.mdeos_surrogate_set_params.argtypes = [vp, vp, vp]
@@ -374,6 +379,19 @@ def mdeos_debug_md(x4, v4, L: float, steps: int, path: int, skin: float = 0.3,
     return ep[:steps], ek[:steps]
 
 
+def mdeos_debug_force_bench(x4, L: float, skin: float, passes: int, mode: int = 0,
+                            cfg: mdeos_config | None = None, stream=None):
+    """Repeated force passes on resident boxes (x4: cuda float32 [nbox, n, 4]);
+    returns a cuda int64 tensor [nbox, 2]: SM cycles of the passes, list entries."""
+    import torch
+    cfg = cfg or mdeos_config_default()
+    nbox, n = x4.shape[0], x4.shape[1]
+    cyc = torch.zeros((nbox, 2), dtype=torch.int64, device=x4.device)
+    _check(lib().mdeos_debug_force_bench(ctypes.byref(cfg), _dptr(x4), nbox, n, L, skin, passes,
+                                         mode, _dptr(cyc), _stream_ptr(stream)))
+    return cyc
+
+
 def mdeos_warm_export(h, element_id: int, natoms: int):
     """Stored final state of an element: (x4, v4 float32 [n,4] host arrays, L)."""
     x4 = np.zeros((natoms, 4), dtype=np.float32)
@@ -499,6 +517,16 @@ class Server:
         d["device_bytes"], d["peak_inflight"] = int(b[0]), int(b[1])
         return d
 
+    def store_stats(self) -> dict:
+        c = np.zeros(4, dtype=np.int64)
+        b = np.zeros(2, dtype=np.uint64)
+        _check(lib().mdeos_serve_store_stats(self.s, c.ctypes.data_as(ctypes.c_void_p),
+                                             b.ctypes.data_as(ctypes.c_void_p)))
+        keys = ("warm_starts", "memory_waits", "evictions", "stored")
+        d = {k: int(v) for k, v in zip(keys, c)}
+        d["store_used_bytes"], d["store_bytes"] = int(b[0]), int(b[1])
+        return d
+
     def wait_all(self, n_expected: int, timeout_s: float = 600.0) -> np.ndarray:
         """Collect completions until n_expected have arrived (or the timeout)."""
         import time
@@ -527,10 +555,11 @@ class Server:
 
 
 def mdeos_autotune(h, reqs, steps: int = 200) -> np.ndarray:
-    """Measure the best Verlet skin per atom count on this GPU and keep it in the
-    handle; returns rows (natoms, skin, ms of GPU time per box)."""
+    """Measure the best launch shape (Verlet skin, warps per box) per atom count on
+    this GPU and keep it in the handle; returns rows (natoms, skin, warps, ms of GPU
+    time per box)."""
     arr = as_requests(reqs)
-    tab = np.zeros((64, 3))
+    tab = np.zeros((64, 4))
     k = ctypes.c_int32()
     _check(lib().mdeos_autotune(h, arr.ctypes.data_as(ctypes.c_void_p), len(arr), steps,
                                 tab.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(k)))

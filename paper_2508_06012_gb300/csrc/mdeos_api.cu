@@ -42,6 +42,10 @@ cudaError_t launch_debug_md(const BoxDesc& bd, const RunParams& rp, int apt, int
                             int smem, float4* x4, float4* v4, int steps, double T, int every,
                             double* ep, double* ek, long long* cyc, uint16_t* nl,
                             cudaStream_t st);
+cudaError_t launch_debug_force_bench(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
+                                     int smem, const float4* x4, int nbox, int passes, int mode,
+                                     long long* cyc, uint16_t* nl, long long nl_elems,
+                                     cudaStream_t st);
 }  // namespace mdeos
 
 using namespace mdeos;
@@ -108,6 +112,7 @@ static mdeos_status check_config(const mdeos_config* c) {
   if (c->skin > 2.0 * c->rc) return fail(MDEOS_EINVAL, "skin larger than 2 rc");
   if (c->warm_lift_iters < 1 || c->warm_lift_iters > 64)
     return fail(MDEOS_EINVAL, "warm_lift_iters out of range 1..64");
+  if (c->nlist_capacity < 0) return fail(MDEOS_EINVAL, "nlist_capacity must be >= 0");
   if (c->warm_slots < 0 || c->warm_atoms < 0 || c->warm_atoms > kMaxAtoms ||
       (c->warm_slots > 0 && c->warm_atoms < 2))
     return fail(MDEOS_EINVAL, "warm_slots / warm_atoms out of range");
@@ -139,8 +144,20 @@ static RunParams make_run_params(const mdeos_config* c) {
 // ---------------------------------------------------------------------------
 // planner: one box
 
-// Verlet skin per atom count measured by mdeos_autotune (used when cfg.skin <= 0)
-using SkinTable = std::map<int, float>;
+// Launch shape per atom count measured by mdeos_autotune: the Verlet skin (used
+// when cfg.skin <= 0) and the warps that run one box (0 = the planner's default).
+struct LaunchShape {
+  float skin = 0.f;
+  int warps = 0;
+};
+using ShapeTable = std::map<int, LaunchShape>;
+
+// smallest power of two >= x (x <= 32)
+static int pow2_ceil(int x) {
+  int p = 1;
+  while (p < x) p *= 2;
+  return p;
+}
 
 struct BoxPlan {
   BoxDesc bd;
@@ -157,8 +174,23 @@ static int round_apt(int a) { return a <= 1 ? 1 : (a <= 2 ? 2 : 4); }
 // minimum image) simulate the same box.
 static double box_side(int n, double rho) { return (double)(float)std::cbrt((double)n / rho); }
 
+// Verlet-list entries per atom: the configured capacity, else 1.3 x the neighbours
+// within rs at the box density (at least the liquid's, rho = 0.9: dilute boxes in
+// the coexistence region form droplets of liquid density) + 32; at least cap_min,
+// at most every other atom; whole 8-entry list words.
+static int list_capacity(const mdeos_config& c, int n, double rho, double rs, int cap_min) {
+  int mx = c.nlist_capacity;
+  if (mx <= 0) {
+    const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(rho, 0.9);
+    mx = (int)std::ceil(1.3 * expect_cap + 32.0);
+  }
+  mx = std::max(mx, cap_min);
+  mx = std::min(mx, n - 1);
+  return (std::max(mx, 1) + 7) & ~7;
+}
+
 static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, bool allow_big,
-                        const SkinTable* tuned) {
+                        const ShapeTable* tuned, int cap_min = 0, bool spread = false) {
   BoxPlan p;
   BoxDesc& b = p.bd;
   std::memset(&b, 0, sizeof(b));
@@ -199,7 +231,7 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
     skin = c.skin;
   } else if (tuned) {
     const auto it = tuned->find(n);
-    if (it != tuned->end()) skin = it->second;
+    if (it != tuned->end() && it->second.skin > 0.f) skin = it->second.skin;
   }
   const double smax = 0.5 * L - c.rc;
   if (n > kMaxAtoms) {
@@ -220,10 +252,7 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
     b.skin = (float)skin;
     b.nc_cell = nc;
     const double expect = 4.18879020478639 * rs * rs * rs * r.rho;
-    const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(r.rho, 0.9);
-    int mx = (int)std::ceil(1.3 * expect_cap + 32.0);
-    mx = std::min(mx, n - 1);
-    b.maxnb = (mx + 7) & ~7;
+    b.maxnb = list_capacity(c, n, r.rho, rs, cap_min);
     p.big = true;
     p.ncell = nc * nc * nc;
     p.warps = 32;
@@ -242,17 +271,11 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
   if (b.path == PATH_NLIST) {
     b.skin = (float)skin;
     const double rs = c.rc + skin;
-    int nc = (int)std::floor(L / rs);
-    while (nc > 3 && nc * nc * nc > kMaxCells) --nc;
-    b.nc_cell = nc >= 3 ? nc : 0;
-    p.ncell = nc >= 3 ? nc * nc * nc : 1;
-    // capacity from the liquid density at least: dilute boxes inside the
-    // liquid-vapour coexistence region form droplets of liquid density
+    const int nc = list_cells_per_axis(L, rs);
+    b.nc_cell = nc;
+    p.ncell = nc > 0 ? nc * nc * nc : 1;
     const double expect = 4.18879020478639 * rs * rs * rs * r.rho;
-    const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(r.rho, 0.9);
-    int mx = (int)std::ceil(1.3 * expect_cap + 32.0);
-    mx = std::min(mx, n - 1);
-    b.maxnb = (mx + 7) & ~7;  // whole 8-entry list words
+    b.maxnb = list_capacity(c, n, r.rho, rs, cap_min);
     p.cost = steps * n * (expect * 1.0 + 8.0);
   } else {
     b.skin = 0.f;
@@ -260,9 +283,18 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
     b.maxnb = 0;
     p.cost = steps * n * (double)n * (b.path == PATH_ALLPAIRS_MI ? 8.0 : 1.0) * 0.6;
   }
-  // threads per box: at most 4 atoms per thread, at least 4 warps
+  // threads per box: at most 4 atoms per thread, at least 4 warps; a tuned shape
+  // may give more warps; a batch that cannot fill the GPU (spread) runs every box
+  // in its own CTA with one atom per thread (up to 32 warps)
   int warps = 4;
   while (warps < 32 && warps * 32 * 4 < n) warps *= 2;
+  if (spread) {
+    warps = std::max(warps, std::min(32, pow2_ceil((n + 31) / 32)));
+  } else if (tuned) {
+    const auto it = tuned->find(n);
+    if (it != tuned->end() && it->second.warps > warps && it->second.warps <= 32)
+      warps = it->second.warps;
+  }
   p.warps = warps;
   p.apt = round_apt((n + warps * 32 - 1) / (warps * 32));
   return p;
@@ -282,16 +314,30 @@ struct Plan {
 
 static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_config& c, int nsm,
                               int smem_max, Plan& plan, bool allow_big = true,
-                              const SkinTable* tuned = nullptr) {
+                              const ShapeTable* tuned = nullptr, const int* cap_min = nullptr) {
   plan.boxes.clear();
   plan.items.clear();
   plan.status.assign(n, MDEOS_OK);
   std::vector<BoxPlan> bp;
   bp.reserve(n);
   for (int i = 0; i < n; ++i) {
-    BoxPlan p = plan_box(reqs[i], c, i, allow_big, tuned);
+    BoxPlan p = plan_box(reqs[i], c, i, allow_big, tuned, cap_min ? cap_min[i] : 0);
     plan.status[i] = p.status;
     if (p.status == MDEOS_OK) bp.push_back(p);
+  }
+  // A batch with no more shared-memory boxes than SMs cannot fill the GPU with
+  // packed items: give every such box its own CTA (spread), one atom per thread.
+  int nsmall = 0;
+  for (const BoxPlan& p : bp) nsmall += p.big ? 0 : 1;
+  const bool spread = nsmall > 0 && nsmall <= nsm;
+  if (spread) {
+    for (BoxPlan& p : bp) {
+      if (p.big) continue;
+      const BoxPlan q = plan_box(reqs[p.bd.out_index], c, p.bd.out_index, allow_big, tuned,
+                                 cap_min ? cap_min[p.bd.out_index] : 0, true);
+      p.warps = q.warps;
+      p.apt = q.apt;
+    }
   }
   // size classes by (warps, apt); inside a class, sort by cost so an item's
   // boxes finish together
@@ -333,7 +379,7 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
     }
     const int warps = bp[k].warps, apt = bp[k].apt;
     const int npad = warps * 32 * apt;
-    const int per_cta = std::min(kCtaThreads / (warps * 32), kMaxBoxesPerItem);
+    const int per_cta = spread ? 1 : std::min(kCtaThreads / (warps * 32), kMaxBoxesPerItem);
     // boxes of this class that share one item
     WorkItem wi;
     std::memset(&wi, 0, sizeof(wi));
@@ -425,6 +471,8 @@ struct TicketState {
   std::vector<int> status;    // planning status per request
   std::vector<uint64_t> element_id;
   std::vector<int> natoms;
+  std::vector<mdeos_request> reqs;  // kept to re-plan boxes whose list overflowed
+  std::vector<BoxDesc> planned;     // the box each request was planned as (by index)
   bool any_device = false;
   size_t bytes = 0;
 };
@@ -437,10 +485,10 @@ struct WarmSlot {
 
 struct mdeos_handle {
   mdeos_config cfg;
-  SkinTable tuned_skin;  // from mdeos_autotune
+  ShapeTable tuned_skin;  // launch shapes from mdeos_autotune
   // warm-start store: slot k holds x float4[warm_atoms] then v float4[warm_atoms]
   float4* d_warm = nullptr;
-  int* d_warm_flag = nullptr;
+  unsigned long long* d_warm_tag = nullptr;  // element_id of each slot's valid state
   size_t warm_bytes = 0;
   std::unordered_map<uint64_t, WarmSlot> warm_map;
   int warm_next = 0;
@@ -550,17 +598,19 @@ extern "C" mdeos_status mdeos_create(const mdeos_config* cfg, mdeos_handle** out
   }
   if (cfg->warm_slots > 0) {
     const size_t slot_bytes = (size_t)2 * cfg->warm_atoms * sizeof(float4);
-    h->warm_bytes = (size_t)cfg->warm_slots * slot_bytes + (size_t)cfg->warm_slots * sizeof(int);
+    h->warm_bytes = (size_t)cfg->warm_slots * (slot_bytes + sizeof(unsigned long long));
     if (cfg->hbm_budget_bytes && h->warm_bytes > cfg->hbm_budget_bytes) {
       delete h;
       return fail(MDEOS_ENOMEM, "warm-start store exceeds the HBM budget");
     }
     e = cudaMalloc(&h->d_warm, (size_t)cfg->warm_slots * slot_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_warm_flag, (size_t)cfg->warm_slots * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(h->d_warm_flag, 0, (size_t)cfg->warm_slots * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&h->d_warm_tag, (size_t)cfg->warm_slots * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+      e = cudaMemset(h->d_warm_tag, 0, (size_t)cfg->warm_slots * sizeof(unsigned long long));
     if (e != cudaSuccess) {
       if (h->d_warm) cudaFree(h->d_warm);
-      if (h->d_warm_flag) cudaFree(h->d_warm_flag);
+      if (h->d_warm_tag) cudaFree(h->d_warm_tag);
       delete h;
       return cuda_fail(e, "warm-start store allocation");
     }
@@ -598,7 +648,7 @@ extern "C" mdeos_status mdeos_destroy(mdeos_handle* h) {
   for (auto& b : h->pinned_free) cudaFreeHost(b.p);
   if (h->d_nl) cudaFree(h->d_nl);
   if (h->d_warm) cudaFree(h->d_warm);
-  if (h->d_warm_flag) cudaFree(h->d_warm_flag);
+  if (h->d_warm_tag) cudaFree(h->d_warm_tag);
   if (h->d_eval) cudaFree(h->d_eval);
   if (h->eval_pinned.p) cudaFreeHost(h->eval_pinned.p);
   if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -636,7 +686,7 @@ static void assign_warm(mdeos_handle* h, Plan& plan, const mdeos_request* reqs) 
                           (r.flags & MDEOS_REQ_COLD) == 0 &&
                           (r.steps_equil == 0 || r.steps_equil >= h->cfg.warm_lift_iters);
     bd.warm_state = h->d_warm + (size_t)ws.slot * 2 * cap;
-    bd.warm_flag = h->d_warm_flag + ws.slot;
+    bd.warm_tag = h->d_warm_tag + ws.slot;
     bd.warm_cap = cap;
     bd.L_old = try_warm ? ws.L : 0.0;
     ws.natoms = r.natoms;
@@ -662,6 +712,9 @@ extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs,
     t.element_id[i] = reqs[i].element_id;
     t.natoms[i] = reqs[i].natoms;
   }
+  t.reqs.assign(reqs, reqs + n);
+  t.planned.resize(n);
+  for (const BoxDesc& bd : plan.boxes) t.planned[bd.out_index] = bd;
   const size_t nb = plan.boxes.size(), ni = plan.items.size();
   const size_t off_items = (nb * sizeof(BoxDesc) + 255) & ~size_t(255);
   const size_t in_bytes = off_items + ni * sizeof(WorkItem);
@@ -716,6 +769,82 @@ extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs,
   return MDEOS_OK;
 }
 
+// Run one plan to completion on the handle's stream (boxes, items, results and
+// queue counter in a temporary device block) and copy its results to host `out`.
+static mdeos_status run_plan_sync(mdeos_handle* h, const Plan& plan, int n, mdeos_result* out) {
+  const size_t nb = plan.boxes.size(), ni = plan.items.size();
+  const size_t off_items = (nb * sizeof(BoxDesc) + 255) & ~size_t(255);
+  const size_t off_res = (off_items + ni * sizeof(WorkItem) + 255) & ~size_t(255);
+  const size_t off_cnt = off_res + (((size_t)n * sizeof(mdeos_result) + 255) & ~size_t(255));
+  const size_t dev_bytes = off_cnt + 256;
+  if (h->cfg.hbm_budget_bytes && h->used_bytes + dev_bytes > h->cfg.hbm_budget_bytes)
+    return fail(MDEOS_ENOMEM, "re-run exceeds the HBM budget");
+  mdeos_status st = ensure_scratch(h, (size_t)plan.grid * plan.nl_per_cta * sizeof(uint16_t));
+  if (st != MDEOS_OK) return st;
+  std::vector<char> in(off_items + ni * sizeof(WorkItem));
+  std::memcpy(in.data(), plan.boxes.data(), nb * sizeof(BoxDesc));
+  std::memcpy(in.data() + off_items, plan.items.data(), ni * sizeof(WorkItem));
+  char* d = nullptr;
+  CK(cudaMallocAsync((void**)&d, dev_bytes, h->stream));
+  cudaError_t e = cudaMemcpyAsync(d, in.data(), in.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess)
+    e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni, (int*)(d + off_cnt),
+                         (mdeos_result*)(d + off_res), h->d_nl, plan.nl_per_cta, h->rp, plan.grid,
+                         plan.smem, h->stream, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, d + off_res, (size_t)n * sizeof(mdeos_result),
+                        cudaMemcpyDeviceToHost, h->stream);
+  cudaFreeAsync(d, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "neighbour-list re-run");
+  h->launches += 1;
+  return MDEOS_OK;
+}
+
+// Boxes whose Verlet list overflowed (MDEOS_ENBR) are planned again with twice the
+// list capacity (up to every other atom) and re-run, keeping the warm-start slot
+// and box side of their first plan, until they succeed or the capacity is full.
+// The list's content and order do not depend on its capacity, so a re-run gives
+// the result a large enough list would have given at once.
+static void rerun_overflowed(mdeos_handle* h, TicketState& t, mdeos_result* res) {
+  std::vector<int> cap(t.n, 0);
+  for (int i = 0; i < t.n; ++i) cap[i] = t.planned[i].maxnb;
+  for (int round = 1; round <= 16; ++round) {
+    std::vector<int> idx;
+    for (int i = 0; i < t.n; ++i)
+      if (t.status[i] == MDEOS_OK && res[i].status == MDEOS_ENBR && cap[i] < t.natoms[i] - 1)
+        idx.push_back(i);
+    if (idx.empty()) return;
+    const int m = (int)idx.size();
+    std::vector<mdeos_request> sub(m);
+    std::vector<int> cmin(m);
+    for (int k = 0; k < m; ++k) {
+      sub[k] = t.reqs[idx[k]];
+      cmin[k] = 2 * cap[idx[k]];
+    }
+    Plan plan;
+    if (make_plan(sub.data(), m, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin,
+                  cmin.data()) != MDEOS_OK)
+      return;
+    for (BoxDesc& bd : plan.boxes) {  // same warm slot and stored box side as the first plan
+      const BoxDesc& first = t.planned[idx[bd.out_index]];
+      bd.warm_state = first.warm_state;
+      bd.warm_tag = first.warm_tag;
+      bd.warm_cap = first.warm_cap;
+      bd.L_old = first.L_old;
+    }
+    std::vector<mdeos_result> out(m);
+    if (run_plan_sync(h, plan, m, out.data()) != MDEOS_OK) return;
+    for (const BoxDesc& bd : plan.boxes) {
+      const int i = idx[bd.out_index];
+      cap[i] = bd.maxnb;
+      res[i] = out[bd.out_index];
+      res[i].nlist_retries = round;
+    }
+  }
+}
+
 extern "C" mdeos_status mdeos_poll(mdeos_handle* h, uint64_t ticket, mdeos_result* out,
                                    int32_t timeout_us) {
   if (!h || !out) return fail(MDEOS_EINVAL, "bad poll arguments");
@@ -748,7 +877,8 @@ extern "C" mdeos_status mdeos_poll(mdeos_handle* h, uint64_t ticket, mdeos_resul
   if (e != cudaSuccess) {
     ret = cuda_fail(e, "batch execution");
   } else {
-    const mdeos_result* dev = (const mdeos_result*)t.h_out.p;
+    mdeos_result* dev = (mdeos_result*)t.h_out.p;
+    rerun_overflowed(h, t, dev);
     for (int i = 0; i < t.n; ++i) {
       if (t.status[i] == MDEOS_OK) {
         out[i] = dev[i];
@@ -938,49 +1068,63 @@ extern "C" mdeos_status mdeos_autotune(mdeos_handle* h, const mdeos_request* req
   CK(cudaStreamSynchronize(h->stream));
   // size classes: Verlet-path boxes grouped by atom count
   std::map<int, std::vector<int>> cls;
-  std::map<int, int> per_cta;
+  std::map<int, int> warps0;
   for (int i = 0; i < n; ++i) {
     const BoxPlan p = plan_box(reqs[i], h->cfg, i, true, nullptr);
     if (p.status != MDEOS_OK || p.bd.path != PATH_NLIST) continue;
     cls[reqs[i].natoms].push_back(i);
-    per_cta[reqs[i].natoms] = p.big ? 1 : std::min(kCtaThreads / (p.warps * 32), kMaxBoxesPerItem);
+    warps0[reqs[i].natoms] = p.big ? 0 : p.warps;
   }
   const float cand[] = {0.2f, 0.25f, 0.3f, 0.35f, 0.4f, 0.5f};
   int k_out = 0;
   for (const auto& kv : cls) {
-    // one full wave of the GPU: nSM CTAs, each with as many boxes as an item holds
-    const int count = h->nsm * per_cta[kv.first];
-    std::vector<mdeos_request> trial(count);
-    for (int i = 0; i < count; ++i) {
-      trial[i] = reqs[kv.second[i % kv.second.size()]];
-      trial[i].steps_equil = steps / 2;
-      trial[i].steps_avg = steps - steps / 2;
-      trial[i].element_id = 0;
-      trial[i].seed += (uint64_t)i;
-    }
-    float best = 0.f, best_skin = 0.f;
-    for (float sk : cand) {
-      mdeos_config c = h->cfg;
-      c.skin = sk;
-      Plan plan;
-      if (make_plan(trial.data(), count, c, h->nsm, h->smem_max, plan) != MDEOS_OK) continue;
-      float ms = 0.f;
-      std::vector<int> status;
-      const mdeos_status st = time_plan(h, plan, count, &ms, status);
-      if (st != MDEOS_OK) return st;
-      bool ok = true;
-      for (int v : status) ok = ok && v == MDEOS_OK;
-      if (ok && (best_skin == 0.f || ms < best)) {
-        best = ms;
-        best_skin = sk;
+    // warps per box: the planner's choice and up to two doublings (at most 32)
+    std::vector<int> wopt;
+    for (int w = warps0[kv.first]; w > 0 && w <= 32 && wopt.size() < 3; w *= 2) wopt.push_back(w);
+    if (wopt.empty()) wopt.push_back(0);  // global-memory boxes: one CTA each
+    float best = 0.f;
+    LaunchShape best_shape;
+    for (int w : wopt) {
+      // one full wave of the GPU: nSM CTAs, each with as many boxes as an item holds
+      const int per_cta = w == 0 ? 1 : std::min(kCtaThreads / (w * 32), kMaxBoxesPerItem);
+      const int count = h->nsm * per_cta;  // spread at one box per CTA changes no shape
+      std::vector<mdeos_request> trial(count);
+      for (int i = 0; i < count; ++i) {
+        trial[i] = reqs[kv.second[i % kv.second.size()]];
+        trial[i].steps_equil = steps / 2;
+        trial[i].steps_avg = steps - steps / 2;
+        trial[i].element_id = 0;
+        trial[i].seed += (uint64_t)i;
+      }
+      for (float sk : cand) {
+        mdeos_config c = h->cfg;
+        c.skin = sk;
+        ShapeTable one;
+        one[kv.first].warps = w;
+        Plan plan;
+        if (make_plan(trial.data(), count, c, h->nsm, h->smem_max, plan, true, &one) != MDEOS_OK)
+          continue;
+        float ms = 0.f;
+        std::vector<int> status;
+        const mdeos_status st = time_plan(h, plan, count, &ms, status);
+        if (st != MDEOS_OK) return st;
+        bool ok = true;
+        for (int v : status) ok = ok && v == MDEOS_OK;
+        const float per_box = ms / count;
+        if (ok && (best_shape.skin == 0.f || per_box < best)) {
+          best = per_box;
+          best_shape.skin = sk;
+          best_shape.warps = w;
+        }
       }
     }
-    if (best_skin > 0.f) {
-      h->tuned_skin[kv.first] = best_skin;
+    if (best_shape.skin > 0.f) {
+      h->tuned_skin[kv.first] = best_shape;
       if (table && k_out < max_out) {
-        table[3 * k_out] = kv.first;
-        table[3 * k_out + 1] = best_skin;
-        table[3 * k_out + 2] = best / count;  // ms of GPU time per box (one wave)
+        table[4 * k_out] = kv.first;
+        table[4 * k_out + 1] = best_shape.skin;
+        table[4 * k_out + 2] = best_shape.warps;
+        table[4 * k_out + 3] = best;  // ms of GPU time per box (one wave)
         ++k_out;
       }
     }
@@ -1002,9 +1146,9 @@ extern "C" mdeos_status mdeos_warm_export(mdeos_handle* h, uint64_t element_id, 
   CK(cudaSetDevice(h->device));
   CK(cudaStreamSynchronize(h->stream));
   const WarmSlot& ws = it->second;
-  int flag = 0;
-  CK(cudaMemcpy(&flag, h->d_warm_flag + ws.slot, sizeof(int), cudaMemcpyDeviceToHost));
-  if (flag != 1) return fail(MDEOS_EINVAL, "the element's last evaluation failed");
+  unsigned long long tag = 0;
+  CK(cudaMemcpy(&tag, h->d_warm_tag + ws.slot, sizeof(tag), cudaMemcpyDeviceToHost));
+  if (tag != element_id) return fail(MDEOS_EINVAL, "the element's last evaluation failed");
   const float4* base = h->d_warm + (size_t)ws.slot * 2 * h->cfg.warm_atoms;
   CK(cudaMemcpy(x4, base, (size_t)natoms * sizeof(float4), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(v4, base + h->cfg.warm_atoms, (size_t)natoms * sizeof(float4),
@@ -1038,12 +1182,12 @@ extern "C" mdeos_status mdeos_warm_import(mdeos_handle* h, uint64_t element_id, 
   }
   CK(cudaSetDevice(h->device));
   float4* base = h->d_warm + (size_t)ws.slot * 2 * h->cfg.warm_atoms;
-  const int one = 1;
+  const unsigned long long tag = element_id;
   CK(cudaMemcpyAsync(base, hx.data(), (size_t)natoms * sizeof(float4), cudaMemcpyHostToDevice,
                      h->stream));
   CK(cudaMemcpyAsync(base + h->cfg.warm_atoms, hv.data(), (size_t)natoms * sizeof(float4),
                      cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->d_warm_flag + ws.slot, &one, sizeof(int), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(h->d_warm_tag + ws.slot, &tag, sizeof(tag), cudaMemcpyHostToDevice,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
   ws.natoms = natoms;
@@ -1056,7 +1200,8 @@ extern "C" mdeos_status mdeos_warm_reset(mdeos_handle* h) {
   std::lock_guard<std::mutex> lock(h->mu);
   if (!h->d_warm) return MDEOS_OK;
   CK(cudaSetDevice(h->device));
-  CK(cudaMemsetAsync(h->d_warm_flag, 0, (size_t)h->cfg.warm_slots * sizeof(int), h->stream));
+  CK(cudaMemsetAsync(h->d_warm_tag, 0, (size_t)h->cfg.warm_slots * sizeof(unsigned long long),
+                     h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->warm_map.clear();
   h->warm_next = 0;
@@ -1147,9 +1292,11 @@ void planning_result_of(mdeos_result& r, int status, const mdeos_request& q) {
 }
 
 // Planning with the handle's configuration and device limits (no warm store).
-mdeos_status plan_requests(const mdeos_handle* h, const mdeos_request* reqs, int n, PlanOut& out) {
+mdeos_status plan_requests(const mdeos_handle* h, const mdeos_request* reqs, int n, PlanOut& out,
+                           const int* cap_min) {
   Plan plan;
-  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin);
+  mdeos_status st =
+      make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin, cap_min);
   if (st != MDEOS_OK) return st;
   out.boxes.swap(plan.boxes);
   out.items.swap(plan.items);
@@ -1204,10 +1351,9 @@ static mdeos_status debug_setup(const mdeos_config* cfg, int n, double L, int pa
   nl_bytes = 0;
   if (path == PATH_NLIST) {
     const double rs = cfg->rc + skin;
-    int nc = (int)std::floor(L / rs);
-    while (nc > 3 && nc * nc * nc > kMaxCells) --nc;
-    bd.nc_cell = nc >= 3 ? nc : 0;
-    ncell = nc >= 3 ? nc * nc * nc : 1;
+    const int nc = list_cells_per_axis(L, rs);
+    bd.nc_cell = nc;
+    ncell = nc > 0 ? nc * nc * nc : 1;
     bd.maxnb = std::max(8, ((n - 1) + 7) & ~7);  // room for every atom: no overflow in tests
     nl_bytes = (size_t)bd.maxnb * kCtaThreads * apt * sizeof(uint16_t);
   }
@@ -1299,6 +1445,38 @@ extern "C" mdeos_status mdeos_debug_forces(const mdeos_config* cfg, const float*
                                       pairs, nl, s);
   if (nl) cudaFreeAsync(nl, s);
   if (e != cudaSuccess) return cuda_fail(e, "debug_forces launch");
+  CK(cudaStreamSynchronize(s));
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_debug_force_bench(const mdeos_config* cfg, const float* x4,
+                                                int32_t nbox, int32_t n, double L, double skin,
+                                                int32_t passes, int32_t mode, long long* cycles,
+                                                void* stream) {
+  if (!x4 || !cycles || nbox < 1 || passes < 1 || (mode != 0 && mode != 1) || n > kMaxAtoms)
+    return fail(MDEOS_EINVAL, "bad arguments");
+  int nsm = 0, dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (nbox > nsm) return fail(MDEOS_EINVAL, "at most one box per SM");
+  BoxDesc bd;
+  RunParams rp;
+  int apt, ncell, smem;
+  size_t nlb;
+  mdeos_status st = debug_setup(cfg, n, L, PATH_NLIST, skin, bd, rp, apt, ncell, smem, nlb);
+  if (st != MDEOS_OK) return st;
+  // list capacity as the planner sets it (liquid density at least)
+  const double rs = cfg->rc + skin;
+  const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(n / (L * L * L), 0.9);
+  bd.maxnb = (std::min((int)std::ceil(1.3 * expect_cap + 32.0), n - 1) + 7) & ~7;
+  const long long nl_elems = (long long)bd.maxnb * kCtaThreads * apt;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint16_t* nl = nullptr;
+  CK(cudaMallocAsync(&nl, (size_t)nl_elems * nbox * sizeof(uint16_t), s));
+  cudaError_t e = launch_debug_force_bench(bd, rp, apt, ncell, smem, (const float4*)x4, nbox,
+                                           passes, mode, cycles, nl, nl_elems, s);
+  cudaFreeAsync(nl, s);
+  if (e != cudaSuccess) return cuda_fail(e, "debug_force_bench launch");
   CK(cudaStreamSynchronize(s));
   return MDEOS_OK;
 }

@@ -23,7 +23,7 @@ namespace mdeos {
 constexpr int kMaxRounds = 16;  // force-pass rounds of a big box (position windows)
 
 struct BigShared {
-  float red[32 * kRedSlots];
+  long long red[32 * kRedSlots];
   double bc[8];
   double acc[kAccDoubles];
   int bcnt[kMaxSeBlocks];
@@ -79,20 +79,21 @@ __device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
   return m;
 }
 
-// Sum NQ per-thread FP32 values over the CTA; FP32 warp sums, FP64 across warps.
+// Sum NQ per-thread fixed-point values (fxp units) over the CTA exactly; every
+// thread gets the totals as FP64 in real units.
 template <int NQ>
-__device__ void block_sum(BigShared* sh, const float (&q)[NQ], double (&out)[NQ]) {
+__device__ void block_sum(BigShared* sh, const long long (&q)[NQ], double (&out)[NQ]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
-    const float s = warp_sum(q[k]);
+    const long long s = warp_sum_ll(q[k]);
     if (lane == 0) sh->red[warp * kRedSlots + k] = s;
   }
   __syncthreads();
   if (warp == 0 && lane < NQ) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += (double)sh->red[w * kRedSlots + lane];
-    sh->bc[lane] = s;
+    unsigned long long s = 0;
+    for (int w = 0; w < nw; ++w) s += (unsigned long long)sh->red[w * kRedSlots + lane];
+    sh->bc[lane] = (double)(long long)s * kFixInv;
   }
   __syncthreads();
 #pragma unroll
@@ -342,11 +343,12 @@ template <bool EN, bool VIR, bool CNT, bool SM>
 __device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, int s0, int s1,
                                              int wl, float4* f, const uint4* nl, int cap, int n,
                                              float L, float invL, LJ c) {
-  float e = 0.f;
-  float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int np = 0;
+  unsigned long long es = 0, ws[6] = {0, 0, 0, 0, 0, 0};
+  int np = 0, bad = 0;
 #pragma unroll 1
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    float e = 0.f;  // this atom's energy and virial over its list
+    float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int si = s;  // the atom's own index in the position source
     if (SM) {
       si = s - wl;
@@ -378,8 +380,17 @@ __device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, int
       }
     }
     f[s] = make_float4(fx, fy, fz, cw);
+    if (EN) {
+      es += (unsigned long long)fxp(0.5f * e);
+      bad |= !(fabsf(e) < 1e9f);
+    }
+    if (VIR) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) ws[k] += (unsigned long long)fxp(0.5f * w[k]);
+      bad |= !(fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) < 1e9f);
+    }
   }
-  FSums out = {EN ? e : 0.f, w[0], w[1], w[2], w[3], w[4], w[5], CNT ? np : 0};
+  FSums out = {es, ws[0], ws[1], ws[2], ws[3], ws[4], ws[5], CNT ? np : 0, bad};
   return out;
 }
 
@@ -411,7 +422,7 @@ __device__ __forceinline__ FSums big_forces_t(const BigMem& m, const BigCtx& b, 
   if (m.nround == 0)
     return big_force_pass<EN, VIR, CNT, false>(m.x, 0u, 0, b.n, 0, m.f, m.nl, m.cap, b.n, b.L,
                                                b.invL, c);
-  FSums t = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+  FSums t = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   float4* sx = reinterpret_cast<float4*>(__cvta_shared_to_generic(m.sx_a));
   for (int q = 0; q < m.nround; ++q) {
     const int wl = m.wlo[q], ws = m.wsz[q];
@@ -433,6 +444,7 @@ __device__ __forceinline__ FSums big_forces_t(const BigMem& m, const BigCtx& b, 
     t.w4 += r.w4;
     t.w5 += r.w5;
     t.np += r.np;
+    t.bad |= r.bad;
   }
   return t;
 }
@@ -452,7 +464,7 @@ static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, int n
   const uint32_t k0 = (uint32_t)(seed & 0xffffffffull), k1 = (uint32_t)(seed >> 32);
   const double sd = sqrt(T / rp.mass);
   const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
-  float p[3] = {0.f, 0.f, 0.f};
+  long long p[3] = {0, 0, 0};
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     const uint32_t id = (uint32_t)__float_as_int(m.x[s].w);
     uint32_t c[4] = {id, 0u, 0u, 0u};
@@ -465,21 +477,21 @@ static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, int n
     sincospi(2.0 * u3, &s3, &c3);
     const float vx = (float)(sd * r01 * c1), vy = (float)(sd * r01 * s1), vz = (float)(sd * r23 * c3);
     m.v[s] = make_float4(vx, vy, vz, 0.f);
-    p[0] += vx;
-    p[1] += vy;
-    p[2] += vz;
+    p[0] += fxp(vx);
+    p[1] += fxp(vy);
+    p[2] += fxp(vz);
   }
   double ptot[3];
   block_sum<3>(sh, p, ptot);
   const float mx = (float)(ptot[0] / n), my = (float)(ptot[1] / n), mz = (float)(ptot[2] / n);
-  float ke[1] = {0.f};
+  long long ke[1] = {0};
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     float4 vi = m.v[s];
     vi.x -= mx;
     vi.y -= my;
     vi.z -= mz;
     m.v[s] = vi;
-    ke[0] += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+    ke[0] += fxp(vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
   }
   double ketot[1];
   block_sum<1>(sh, ke, ketot);
@@ -539,10 +551,10 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   double E_cold;
   {
     const FSums r = big_forces(m, b, lj, true, false);
-    float q[1] = {r.e};
+    const long long q[1] = {(long long)r.e};
     double et[1];
     block_sum<1>(sh, q, et);
-    E_cold = 0.5 * et[0];
+    E_cold = et[0];
   }
   double* boxc = acc + ACC_BOX;
   const double E_ref = (rp.ref_mode == MDEOS_REF_FIXED) ? n * bd.e_ref : E_cold;
@@ -565,32 +577,39 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   const int total = bd.steps_equil + bd.steps_avg;
   const int nb = rp.se_blocks;
   if (status == MDEOS_OK) big_init_velocities(m, sh, n, bd.seed, Tk, rp);
-  const float invV_f = (float)(1.0 / V), inv3V_f = (float)(1.0 / (3.0 * V));
-  const float inv_ndof_f = (float)(1.0 / ndof);
+  const double invV = 1.0 / V, inv3V = 1.0 / (3.0 * V), inv_ndof = 1.0 / ndof;
   float lam = 1.0f;
-  float Tk_f = (float)Tk;
   for (int step = 0; step < total && status == MDEOS_OK; ++step) {
     const bool avg = step >= bd.steps_equil;
     const int s_avg = step - bd.steps_equil;
     const bool seg_end = !avg && (seg_pos == seg_len - 1);
     const bool esamp = !avg && !temp_mode && (seg_pos >= seg_len - nsamp);
     const bool need = big_kick_drift(m, b, rp, lam);
-    if (__syncthreads_or(need)) {
-      big_wrap(m, n, b.L, b.invL);
-      __syncthreads();
-      big_build(m, sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
-      ++builds;
-    }
+    const bool rebuild = __syncthreads_or(need) != 0;
     {
+      // written by warp 0 last step (non-finite state): stop before a rebuild
+      // bins such positions into cells
       const int st = sh->ctrl[CTRL_STATUS];
       if (st != 0 || sh->ctrl[CTRL_OVERFLOW] != 0) {
         status = st != 0 ? st : MDEOS_ENBR;
         break;
       }
     }
+    if (rebuild) {
+      big_wrap(m, n, b.L, b.invL);
+      __syncthreads();
+      big_build(m, sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+      ++builds;
+      if (sh->ctrl[CTRL_OVERFLOW] != 0) {
+        status = MDEOS_ENBR;
+        break;
+      }
+    }
     const FSums r = big_forces(m, b, lj, avg || esamp, avg);
-    float ke = 0.f, kt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // second half kick; per-atom kinetic energy and kinetic stress into exact sums
+    unsigned long long ke = 0, kt[6] = {0, 0, 0, 0, 0, 0};
     int cand = 0;
+    bool bad = r.bad != 0;
     for (int s = tid; s < n; s += nt) {
       const float4 fi = m.f[s];
       float4 vi = m.v[s];
@@ -598,101 +617,113 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
       vi.y = fmaf(rp.hdtm, fi.y, vi.y);
       vi.z = fmaf(rp.hdtm, fi.z, vi.z);
       m.v[s] = vi;
-      ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+      const float ka = 0.5f * rp.mass_f * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+      bad |= !(ka < 1e9f);
+      ke += (unsigned long long)fxp(ka);
       if (avg) {
-        kt[0] += vi.x * vi.x;
-        kt[1] += vi.y * vi.y;
-        kt[2] += vi.z * vi.z;
-        kt[3] += vi.x * vi.y;
-        kt[4] += vi.x * vi.z;
-        kt[5] += vi.y * vi.z;
+        kt[0] += (unsigned long long)fxp(rp.mass_f * vi.x * vi.x);
+        kt[1] += (unsigned long long)fxp(rp.mass_f * vi.y * vi.y);
+        kt[2] += (unsigned long long)fxp(rp.mass_f * vi.z * vi.z);
+        kt[3] += (unsigned long long)fxp(rp.mass_f * vi.x * vi.y);
+        kt[4] += (unsigned long long)fxp(rp.mass_f * vi.x * vi.z);
+        kt[5] += (unsigned long long)fxp(rp.mass_f * vi.y * vi.z);
         cand += __float_as_int(fi.w);
       }
     }
     {
-      float* red = sh->red + warp * kRedSlots;
-      const float s = warp_sum(0.5f * rp.mass_f * ke);
-      if (lane == 0) red[7] = s;
+      long long* red = sh->red + warp * kRedSlots;
+      const long long s = warp_sum_ll((long long)ke);
+      const bool any_bad = __any_sync(0xffffffffu, bad);
+      if (lane == 0) {
+        red[7] = s;
+        red[10] = any_bad ? 1 : 0;
+      }
       if (avg || esamp) {
-        const float se = warp_sum(0.5f * r.e);
+        const long long se = warp_sum_ll((long long)r.e);
         if (lane == 0) red[6] = se;
       }
       if (avg) {
-        const float wv[6] = {r.w0, r.w1, r.w2, r.w3, r.w4, r.w5};
+        const unsigned long long wv[6] = {r.w0, r.w1, r.w2, r.w3, r.w4, r.w5};
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const float sk = warp_sum(rp.mass_f * kt[k] + 0.5f * wv[k]);
+          const long long sk = warp_sum_ll((long long)(kt[k] + wv[k]));
           if (lane == 0) red[k] = sk;
         }
-        const float sp = warp_sum((float)r.np), sc = warp_sum((float)cand);
+        const long long sp = warp_sum_ll(r.np), sc = warp_sum_ll(cand);
         if (lane == 0) {
           red[8] = sp;
           red[9] = sc;
         }
       }
     }
+    // thermostat steps and segment ends rescale the velocities
+    const bool resc = seg_end ||
+                      (!avg && rp.rescale_every_equil > 0 &&
+                       (seg_pos + 1) % rp.rescale_every_equil == 0) ||
+                      (avg && rp.rescale_every_avg > 0 && (s_avg + 1) % rp.rescale_every_avg == 0);
     __syncthreads();
-    float ke_tot = 0.f;
-    for (int w = 0; w < nwarps; ++w) ke_tot += sh->red[w * kRedSlots + 7];
-    const float T_inst = 2.0f * ke_tot * inv_ndof_f;
     if (warp == 0) {
-      float q = 0.f;
-      if (lane < kRedSlots)
-        for (int w = 0; w < nwarps; ++w) q += sh->red[w * kRedSlots + lane];
-      const float s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
-      const float s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
-      const float e6 = __shfl_sync(0xffffffffu, q, 6);
-      const float Ps = (s0 + s1 + s2) * inv3V_f;  // Eq. 11, mean normal stress
-      const float Ts = 2.0f * k7 * inv_ndof_f;
+      // box sums of the step: exact sums of the warp partials (lane k holds
+      // quantity k); the thermostat's kinetic temperature comes from the same sum
+      const long long qi = warp_partials_ll(sh->red, nwarps, lane);
+      const double q = lane < 8 ? (double)qi * kFixInv : (double)qi;
+      const double s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
+      const double s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
+      const double Ps = (s0 + s1 + s2) * inv3V;  // Eq. 11, mean normal stress
+      const double Ts = 2.0 * k7 * inv_ndof;
+      if ((lane == 7 && !(Ts > 0.0)) || (lane == 10 && qi != 0))
+        sh->ctrl[CTRL_STATUS] = MDEOS_EUNPHYS;
       int slot = -1;
-      float val = 0.f;
+      double val = 0.0;
       if (avg) {
         const int blk = (int)(((long long)s_avg * nb) / bd.steps_avg);
-        if (lane < 6) { slot = ACC_RUN + lane; val = q * invV_f; }
+        if (lane < 6) { slot = ACC_RUN + lane; val = q * invV; }
         else if (lane < 10) { slot = ACC_RUN + lane; val = q; }
         else if (lane == 10) { slot = ACC_RUN + 10; val = Ps; }
         else if (lane == 11) { slot = ACC_RUN + 11; val = Ts; }
         else if (lane == 12) { slot = ACC_BP + blk; val = Ps; sh->bcnt[blk] += 1; }
         else if (lane == 13) { slot = ACC_BT + blk; val = Ts; }
-        if (lane == 10 && (!isfinite(Ps) || !isfinite(Ts) || !isfinite(e6)))
-          sh->ctrl[CTRL_STATUS] = MDEOS_EUNPHYS;
       } else if (esamp && lane == 6) {
         slot = ACC_RUN + 12;
         val = q;
       }
-      if (slot >= 0) acc[slot] += (double)val;
+      if (slot >= 0) acc[slot] += val;
+      double Tn = Tk;
       if (seg_end && lane == 6) {
         const double Ebar = acc[ACC_RUN + 12] / nsamp;
-        const double Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) / ndof;  // Eq. 10
+        Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) / ndof;  // Eq. 10
         sh->bc[0] = Tn;
         acc[ACC_RUN + 12] = 0.0;
       }
+      // velocity-rescale factor towards the (new) target temperature
+      if (resc) {
+        Tn = __shfl_sync(0xffffffffu, Tn, 6);
+        if (lane == 7)
+          sh->bc[5] = (Tn > 0.0 && Ts > 0.0 && isfinite(Tn) && isfinite(Ts)) ? sqrt(Tn / Ts) : -1.0;
+      }
     }
-    if (!(T_inst > 0.f) || !isfinite(T_inst)) {
-      status = MDEOS_EUNPHYS;
-      break;
-    }
+    // the rescale is applied with the next first half-kick
     lam = 1.0f;
-    if (seg_end) {
+    if (resc) {
       __syncthreads();
-      const double Tn = sh->bc[0];
-      if (!(Tn > 0.0) || !isfinite(Tn)) {
+      const double lam_d = sh->bc[5];
+      if (!(lam_d > 0.0)) {
         status = MDEOS_EUNPHYS;
         break;
       }
-      if (tid == 0) boxc[3] = Tn;
-      Tk_f = (float)Tn;
-      lam = sqrtf(Tk_f / T_inst);
+      if (seg_end) {
+        Tk = sh->bc[0];
+        if (tid == 0) boxc[3] = Tk;
+      }
+      lam = (float)lam_d;
+    }
+    if (seg_end) {
       ++seg;
       seg_pos = 0;
       seg_len = (seg == nseg - 1) ? base + bd.steps_equil % nseg : base;
       nsamp = max(1, (seg_len + 9) / 10);
     } else if (!avg) {
-      if (rp.rescale_every_equil > 0 && (seg_pos + 1) % rp.rescale_every_equil == 0)
-        lam = sqrtf(Tk_f / T_inst);
       ++seg_pos;
-    } else if (rp.rescale_every_avg > 0 && (s_avg + 1) % rp.rescale_every_avg == 0) {
-      lam = sqrtf(Tk_f / T_inst);
     }
   }
   __syncthreads();
@@ -734,7 +765,7 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
     res.nlist_builds = builds;
     res.path = PATH_NLIST;
     res.warm = 0;
-    res.reserved0 = 0;
+    res.nlist_retries = 0;
     if (status != MDEOS_OK) {
       res.P = res.T = res.epot = res.ekin = res.e_achieved = res.P_se = res.T_se = 0.0;
       for (int k = 0; k < 6; ++k) res.sigma[k] = 0.0;

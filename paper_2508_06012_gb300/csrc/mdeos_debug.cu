@@ -11,18 +11,17 @@ __device__ void debug_lift_body(const Group& g, const BoxDesc& bd, const RunPara
   if (g.tid < 16) g.ctrl()[g.tid] = 0;
   lattice_own<APT>(g, bd);
   gbar(g.bar, g.nt);
-  float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int np = 0;
+  ForceAcc f0;
   if (bd.path == PATH_NLIST) {
     build_nlist<APT>(g, b);
-    compute_forces<APT, PATH_NLIST, true, false, false>(g, b, rp, e0, w0, np);
+    compute_forces<APT, PATH_NLIST, true, false, false>(g, b, rp, f0);
   } else if (bd.path == PATH_ALLPAIRS_MI) {
-    compute_forces<APT, PATH_ALLPAIRS_MI, true, false, false>(g, b, rp, e0, w0, np);
+    compute_forces<APT, PATH_ALLPAIRS_MI, true, false, false>(g, b, rp, f0);
   } else {
-    compute_forces<APT, PATH_ALLPAIRS, true, false, false>(g, b, rp, e0, w0, np);
+    compute_forces<APT, PATH_ALLPAIRS, true, false, false>(g, b, rp, f0);
   }
   double et[1];
-  float q[1] = {e0};
+  const long long q[1] = {(long long)f0.e};
   group_sum<1>(g, q, et);
   init_velocities<APT>(g, b, bd.seed, T, rp);
   for (int a = 0; a < APT; ++a) {
@@ -34,7 +33,7 @@ __device__ void debug_lift_body(const Group& g, const BoxDesc& bd, const RunPara
       v4[id] = g.v()[i];
     }
   }
-  if (g.tid == 0) e_out[0] = 0.5 * et[0];
+  if (g.tid == 0) e_out[0] = et[0];
 }
 
 template <int APT, int PATH>
@@ -66,15 +65,15 @@ __device__ void debug_forces_body(const Group& g, const BoxDesc& bd, const RunPa
     }
     gbar(g.bar, g.nt);
   }
-  float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int np = 0;
-  compute_forces<APT, PATH, true, true, true>(g, b, rp, e, w, np);
+  ForceAcc fa;
+  compute_forces<APT, PATH, true, true, true>(g, b, rp, fa);
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
     if (i < b.n) f4[__float_as_int(g.x()[i].w)] = g.f()[i];
   }
-  float q[8] = {0.5f * e,    0.5f * w[0], 0.5f * w[1], 0.5f * w[2],
-                0.5f * w[3], 0.5f * w[4], 0.5f * w[5], (float)np};
+  const long long q[8] = {(long long)fa.e,    (long long)fa.w[0], (long long)fa.w[1],
+                          (long long)fa.w[2], (long long)fa.w[3], (long long)fa.w[4],
+                          (long long)fa.w[5], (long long)fa.np * 4294967296LL};
   double out[8];
   group_sum<8>(g, q, out);
   if (g.tid == 0) {
@@ -111,9 +110,8 @@ __device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams
     build_nlist<APT>(g, b);
   }
   {
-    float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int np = 0;
-    compute_forces<APT, PATH, false, false, false>(g, b, rp, e0, w0, np);
+    ForceAcc f0;
+    compute_forces<APT, PATH, false, false, false>(g, b, rp, f0);
   }
   gbar(g.bar, g.nt);  // every force loop has read the positions before any atom moves
   for (int s = 0; s < steps; ++s) {
@@ -131,11 +129,10 @@ __device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams
       build_nlist<APT>(g, b, cyc ? bph : nullptr);
     }
     const long long t2 = clock64();
-    float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int np = 0;
-    compute_forces<APT, PATH, true, false, false>(g, b, rp, e, w, np);
+    ForceAcc fa;
+    compute_forces<APT, PATH, true, false, false>(g, b, rp, fa);
     const long long t3 = clock64();
-    float ke = 0.f;
+    long long ke = 0;
     for (int a = 0; a < APT; ++a) {
       const int i = g.tid + a * g.nt;
       if (i < n) {
@@ -145,10 +142,10 @@ __device__ void debug_md_body(const Group& g, const BoxDesc& bd, const RunParams
         vi.y = fmaf(rp.hdtm, fi.y, vi.y);
         vi.z = fmaf(rp.hdtm, fi.z, vi.z);
         g.v()[i] = vi;
-        ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+        ke += fxp(0.5f * rp.mass_f * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z));
       }
     }
-    float q[2] = {0.5f * e, 0.5f * rp.mass_f * ke};
+    const long long q[2] = {(long long)fa.e, ke};
     double tot[2];
     group_sum<2>(g, q, tot);
     if (g.tid == 0) {
@@ -262,6 +259,82 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// The pair-force pass on its own: one resident box per CTA (positions from x4 +
+// blockIdx.x * n), the Verlet list built once, then `passes` force passes exactly
+// as the step loop runs them (mode 0: forces only, in list-length order; 1: forces,
+// energy, virial and pair count).  cyc[2 b] = SM cycles of the passes, cyc[2 b + 1]
+// = list entries (pair candidates) per pass of box b.
+
+template <int APT>
+__device__ void debug_force_bench_body(const Group& g, const BoxDesc& bd, const RunParams& rp,
+                                       const float4* x4, int passes, int mode, long long* cyc) {
+  const BoxCtx b = make_ctx(bd, rp);
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) {
+      const float4 xi = x4[i];
+      g.x()[i] = make_float4(xi.x, xi.y, xi.z, __int_as_float(i));
+      g.v()[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (g.tid < 16) g.ctrl()[g.tid] = 0;
+  gbar(g.bar, g.nt);
+  wrap_own<APT>(g, b);
+  build_nlist<APT>(g, b);
+  long long cand[1] = {0};
+  for (int a = 0; a < APT; ++a) {
+    const int i = g.tid + a * g.nt;
+    if (i < b.n) cand[0] += (long long)__float_as_int(g.f()[i].w) * 4294967296LL;
+  }
+  double ctot[1];
+  group_sum<1>(g, cand, ctot);
+  ForceAcc fa;
+  const long long t0 = clock64();
+  for (int p = 0; p < passes; ++p) {
+    if (mode == 0) {
+      compute_forces<APT, PATH_NLIST, false, false, false>(g, b, rp, fa);
+    } else {
+      compute_forces<APT, PATH_NLIST, true, true, true>(g, b, rp, fa);
+      gbar(g.bar, g.nt);
+    }
+  }
+  const long long t1 = clock64();
+  if (g.tid == 0) {
+    cyc[0] = t1 - t0;
+    cyc[1] = (long long)ctot[0];
+  }
+  if (fa.e == 12345ull && fa.np == -1) cyc[0] = -1;  // keeps the sums live
+}
+
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    debug_force_bench_kernel(BoxDesc bd, RunParams rp, int apt, int ncell_cap, const float4* x4,
+                             int passes, int mode, long long* cyc, uint16_t* nl,
+                             long long nl_elems) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Group g = make_group(smem, threadIdx.x, 32, apt, ncell_cap, 1,
+                             nl + (long long)blockIdx.x * nl_elems);
+  const float4* xb = x4 + (size_t)blockIdx.x * bd.natoms;
+  long long* cb = cyc + 2 * blockIdx.x;
+  switch (apt) {
+    case 1: debug_force_bench_body<1>(g, bd, rp, xb, passes, mode, cb); break;
+    case 2: debug_force_bench_body<2>(g, bd, rp, xb, passes, mode, cb); break;
+    default: debug_force_bench_body<4>(g, bd, rp, xb, passes, mode, cb); break;
+  }
+}
+
+cudaError_t launch_debug_force_bench(const BoxDesc& bd, const RunParams& rp, int apt, int ncell_cap,
+                                     int smem, const float4* x4, int nbox, int passes, int mode,
+                                     long long* cyc, uint16_t* nl, long long nl_elems,
+                                     cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(debug_force_bench_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  debug_force_bench_kernel<<<nbox, kCtaThreads, smem, st>>>(bd, rp, apt, ncell_cap, x4, passes,
+                                                             mode, cyc, nl, nl_elems);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // boxes above the shared-memory limit (global-memory state, one CTA)
 
 __global__ void __launch_bounds__(kCtaThreads, 1)
@@ -291,8 +364,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   __syncthreads();
   const FSums r = big_forces(m, b, make_lj(rp), true, true);
   for (int s = threadIdx.x; s < b.n; s += blockDim.x) f4[__float_as_int(m.x[s].w)] = m.f[s];
-  float q[8] = {0.5f * r.e,  0.5f * r.w0, 0.5f * r.w1, 0.5f * r.w2,
-                0.5f * r.w3, 0.5f * r.w4, 0.5f * r.w5, (float)r.np};
+  const long long q[8] = {(long long)r.e,  (long long)r.w0, (long long)r.w1, (long long)r.w2,
+                          (long long)r.w3, (long long)r.w4, (long long)r.w5,
+                          (long long)r.np * 4294967296LL};
   double out[8];
   block_sum<8>(&sh, q, out);
   if (threadIdx.x == 0) {
@@ -336,7 +410,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
       ++nbuild;
     }
     const FSums r = big_forces(m, b, lj, true, false);
-    float ke = 0.f;
+    long long ke = 0;
     for (int s = threadIdx.x; s < n; s += blockDim.x) {
       const float4 fi = m.f[s];
       float4 vi = m.v[s];
@@ -344,9 +418,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
       vi.y = fmaf(rp.hdtm, fi.y, vi.y);
       vi.z = fmaf(rp.hdtm, fi.z, vi.z);
       m.v[s] = vi;
-      ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+      ke += fxp(0.5f * rp.mass_f * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z));
     }
-    float q[2] = {0.5f * r.e, 0.5f * rp.mass_f * ke};
+    const long long q[2] = {(long long)r.e, ke};
     double tot[2];
     block_sum<2>(&sh, q, tot);
     if (threadIdx.x == 0) {

@@ -10,10 +10,13 @@
 //    while the Verlet list is rebuilt).  Thread t owns atoms t, t + nt, ...
 //    for the whole run, so per-atom state needs no cross-thread exchange
 //    except positions.
-//  * Pair forces are FP32 (rcp.approx + FMA).  Per-thread and per-warp
-//    partial sums are FP32; the cross-warp combination and every time
-//    accumulation of energy, virial and kinetic tensors are FP64.
-//  * The Verlet list (uint16 atom indices, four per 8-byte word, words laid
+//  * Pair forces are FP32 (rcp.approx + FMA), each atom's sum over its list in
+//    list order.  Box sums (energy, virial, kinetic energy and stress, momentum)
+//    add per-atom FP32 values converted to 64-bit fixed point (2^-32 units):
+//    integer sums are exact and independent of their order, so no result
+//    depends on how many threads run a box or which thread holds which atom.
+//    Time accumulation and the restriction are FP64.
+//  * The Verlet list (uint16 atom indices, eight per 16-byte word, words laid
 //    out so one warp load is contiguous) lives in global scratch.
 #pragma once
 #include <cuda_runtime.h>
@@ -55,6 +58,21 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// 64-bit fixed point of the box sums: v * 2^32 rounded to the nearest integer
+// (exact for |v| >= 2^-9, where the scaled float is already an integer).  Values
+// are kept below 2^30 in magnitude by the callers' finiteness checks.
+constexpr float kFixScale = 4294967296.0f;         // 2^32
+constexpr double kFixInv = 2.3283064365386963e-10;  // 2^-32
+__device__ __forceinline__ long long fxp(float v) { return __float2ll_rn(v * kFixScale); }
+
+// exact warp sum of 64-bit integers (two's complement wraps instead of overflow UB)
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+  unsigned long long u = (unsigned long long)v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) u += (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)u, o);
+  return (long long)u;
 }
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the two-multiplier
@@ -101,9 +119,11 @@ struct Group {
   __device__ __forceinline__ int* cell() const {
     return reinterpret_cast<int*>(base + (size_t)50 * npad);
   }
-  __device__ __forceinline__ float* red() const { return reinterpret_cast<float*>(base + off_red); }
+  __device__ __forceinline__ long long* red() const {
+    return reinterpret_cast<long long*>(base + off_red);
+  }
   __device__ __forceinline__ double* bc() const {
-    return reinterpret_cast<double*>(base + off_red + nwarps * kRedSlots * 4);
+    return reinterpret_cast<double*>(base + off_red + nwarps * kRedSlots * 8);
   }
   __device__ __forceinline__ double* acc() const { return bc() + 8; }
   __device__ __forceinline__ int* bcnt() const { return reinterpret_cast<int*>(acc() + kAccDoubles); }
@@ -124,24 +144,33 @@ __device__ inline Group make_group(unsigned char* base, int tid, int warps, int 
   return g;
 }
 
-// Sum NQ per-thread FP32 values over the group; every thread gets the FP64
-// totals.  Warp sums are FP32, the cross-warp combination FP64 in warp order.
+// Sum NQ per-thread fixed-point values (fxp units) over the group exactly; every
+// thread gets the totals as FP64 in real units.
 template <int NQ>
-__device__ void group_sum(const Group& g, const float (&q)[NQ], double (&out)[NQ]) {
+__device__ void group_sum(const Group& g, const long long (&q)[NQ], double (&out)[NQ]) {
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
-    float s = warp_sum(q[k]);
+    const long long s = warp_sum_ll(q[k]);
     if (g.lane() == 0) g.red()[g.warp() * kRedSlots + k] = s;
   }
   gbar(g.bar, g.nt);
   if (g.warp() == 0 && g.lane() < NQ) {
-    double s = 0.0;
-    for (int w = 0; w < g.nwarps; ++w) s += (double)g.red()[w * kRedSlots + g.lane()];
-    g.bc()[g.lane()] = s;
+    unsigned long long s = 0;
+    for (int w = 0; w < g.nwarps; ++w) s += (unsigned long long)g.red()[w * kRedSlots + g.lane()];
+    g.bc()[g.lane()] = (double)(long long)s * kFixInv;
   }
   gbar(g.bar, g.nt);
 #pragma unroll
   for (int k = 0; k < NQ; ++k) out[k] = g.bc()[k];
+}
+
+// Leader-warp combination of one step's per-warp partials (red[w * kRedSlots + k],
+// k < kRedSlots): lane k returns the exact sum over warps of quantity k.
+__device__ __forceinline__ long long warp_partials_ll(const long long* red, int nwarps, int lane) {
+  unsigned long long s = 0;
+  if (lane < kRedSlots)
+    for (int w = 0; w < nwarps; ++w) s += (unsigned long long)red[w * kRedSlots + lane];
+  return (long long)s;
 }
 
 // Per-box constants in registers.
@@ -249,23 +278,39 @@ __device__ __forceinline__ void nl_pair_bd(uint32_t xs_a, int j, bool ok, const 
   lj_pair<EN, VIR>(dx, dy, dz, ok, c, fx, fy, fz, e, w, np);
 }
 
+__device__ __forceinline__ void st_shared_u16(uint32_t a, int v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v) : "memory");
+}
+
+__device__ __forceinline__ uint4 ld_shared_u4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+
 __device__ __forceinline__ int ld_shared_u16(uint32_t a) {
   unsigned short v;
   asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
   return (int)v;
 }
 
-// per-thread partial sums of one force pass
+// per-thread partial sums of one force pass: energy and virial in fxp units
+// (already halved: each pair appears in two atoms' lists), wrapping integer adds
 struct FSums {
-  float e, w0, w1, w2, w3, w4, w5;
+  unsigned long long e, w0, w1, w2, w3, w4, w5;
   int np;
+  int bad;  // an atom's energy or virial is not finite or above 1e9
 };
 
 // Forces on the thread's own slots tid, tid + nt, ... (written to fs), with
-// optional energy, virial and pair-count partials over ordered pairs (the caller
-// halves E and W).  Not inlined and fed only scalars: it runs with the whole
-// register budget for the pair loop while the caller's step state is saved once
-// per call, and positions are read with explicit shared-memory loads.
+// optional energy, virial and pair-count sums: per atom in FP32 over its list,
+// then added to the thread's exact fixed-point sums.  Not inlined and fed only
+// scalars: it runs with the whole register budget for the pair loop while the
+// caller's step state is saved once per call, and positions are read with
+// explicit shared-memory loads.
 //
 // ord_a (shared address, 0 = none): the slot to take at position tid + a * nt, from
 // the last list build (slots by list length, longest first, dealt over the rows in a
@@ -276,10 +321,8 @@ template <int APT, int PATH, bool EN, bool VIR, bool CNT>
 __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16_t* nl, int tid,
                                          int nt, int npad, int n, int maxnb, float L, float invL,
                                          LJ c, uint32_t ord_a) {
-  // energy, virial and pair count accumulate over all of the thread's atoms
-  float e = 0.f;
-  float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int np = 0;
+  unsigned long long es = 0, ws[6] = {0, 0, 0, 0, 0, 0};
+  int np = 0, bad = 0;
 #pragma unroll 1
   for (int a = 0; a < APT; ++a) {
     int i = tid + a * nt;
@@ -288,6 +331,8 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
       const float4 xi = ld_shared4(xs_a + 16u * (uint32_t)i);
       const float cw = fs[i].w;  // packed list lengths (Verlet path), kept across steps
       float fx = 0.f, fy = 0.f, fz = 0.f;
+      float e = 0.f;  // this atom's energy and virial over its list
+      float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (PATH == PATH_NLIST) {
         // Row of slot i: eight uint16 entries per 16-byte word, word (k/8) of slot
         // i at (k/8) * npad + i, so a warp's word loads are contiguous.  The list
@@ -353,15 +398,31 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
         }
       }
       fs[i] = make_float4(fx, fy, fz, cw);
+      if (EN) {
+        es += (unsigned long long)fxp(0.5f * e);
+        bad |= !(fabsf(e) < 1e9f);
+      }
+      if (VIR) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ws[k] += (unsigned long long)fxp(0.5f * w[k]);
+        bad |= !(fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) < 1e9f);
+      }
     }
   }
-  FSums out = {EN ? e : 0.f, w[0], w[1], w[2], w[3], w[4], w[5], CNT ? np : 0};
+  FSums out = {es, ws[0], ws[1], ws[2], ws[3], ws[4], ws[5], CNT ? np : 0, bad};
   return out;
 }
 
+// Per-thread sums of a force pass: energy and virial (fxp units, halved), pair
+// count, and the non-finite flag.
+struct ForceAcc {
+  unsigned long long e = 0, w[6] = {0, 0, 0, 0, 0, 0};
+  int np = 0, bad = 0;
+};
+
 template <int APT, int PATH, bool EN, bool VIR, bool CNT>
 __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, const RunParams& rp,
-                                               float& e_acc, float (&w_acc)[6], int& pair_acc) {
+                                               ForceAcc& acc) {
   const uint32_t xs_a = (uint32_t)__cvta_generic_to_shared(g.x());
   // the length order only where no sum depends on which thread takes which atom
   const uint32_t ord_a = (PATH == PATH_NLIST && !EN && !VIR && !CNT)
@@ -372,30 +433,31 @@ __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, 
   // in the length order a thread's forces belong to other threads' atoms: every
   // force is written before any thread reads its own atoms' forces
   if (ord_a != 0u) gbar(g.bar, g.nt);
-  if (EN) e_acc += r.e;
+  if (EN) acc.e += r.e;
   if (VIR) {
-    w_acc[0] += r.w0;
-    w_acc[1] += r.w1;
-    w_acc[2] += r.w2;
-    w_acc[3] += r.w3;
-    w_acc[4] += r.w4;
-    w_acc[5] += r.w5;
+    acc.w[0] += r.w0;
+    acc.w[1] += r.w1;
+    acc.w[2] += r.w2;
+    acc.w[3] += r.w3;
+    acc.w[4] += r.w4;
+    acc.w[5] += r.w5;
   }
-  if (CNT) pair_acc += r.np;
+  if (CNT) acc.np += r.np;
+  acc.bad |= r.bad;
 }
 
 // ---------------------------------------------------------------------------
 // Verlet list build from positions wrapped into [0, L).
 //
-// Cell path (>= 3 cells of side >= rc + skin per axis): a shared-memory counting
-// sort re-orders the box into cell order -- positions (original atom id carried
-// in x.w) and velocities are permuted in place, and ownership follows the slot --
-// so the 32 lanes of a warp hold neighbouring atoms and scan the same cells, and
-// later force-loop gathers touch nearby shared-memory words.  Inside a cell atoms
-// keep their previous relative order (sorted by previous slot), so the order, the
-// list and every result are deterministic.  The per-cell image shift replaces a
-// per-candidate minimum image in the search.
-// Small boxes (fewer than 3 cells per axis) scan every atom without re-ordering.
+// Cell path (a grid of cells of side >= (rc + skin) / 2, at most 12 per axis; any
+// box with L >= 2 (rc + skin)): a shared-memory counting sort re-orders the box
+// into cell order -- positions (original atom id carried in x.w) and velocities
+// are permuted in place, and ownership follows the slot -- so the 32 lanes of a
+// warp hold neighbouring atoms and scan overlapping cells, and later force-loop
+// gathers touch nearby shared-memory words.  Inside a cell atoms keep their
+// previous relative order (sorted by previous slot), so the order, the list and
+// every result are deterministic.
+// Without a grid (nc_cell = 0) every atom is scanned with the minimum image.
 // The list length of slot s is kept in f[s].w (as int bits).
 __device__ __forceinline__ void nl_store(uint16_t* row, int k, int npad, int j) {
   row[(size_t)(k >> 3) * npad * 8 + (k & 7)] = (uint16_t)j;
@@ -461,6 +523,121 @@ __device__ void build_order(const Group& g, const BoxCtx& b) {
   gbar(g.bar, g.nt);
 }
 
+__device__ __forceinline__ int ld_shared_s32(uint32_t a) {
+  int v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+
+// Verlet-list search over the cell-ordered box (cells of side h >= R / 2, R = rc +
+// skin).  Every lane walks the same 5 x 5 rows of cells around its home cell (z and
+// y offsets -2..2, a warp-uniform loop), and in each row only the x range of cells
+// that can hold an atom within R of its own: R^2 less the squared distance to the
+// row's y-z rectangle bounds the x extent.  A row's cells are contiguous slots in
+// cell order, cut into at most three segments where the x range wraps around the
+// box, each with its image shift applied to the home atom once.  Ranges use R
+// enlarged by 1e-5 so rounding drops no cell, and the home position is clamped into
+// [0, L] so the indices stay in range even for a state that has blown up (the box
+// then fails on its temperature); entries are accepted on r^2 < R^2.  A cell reached
+// through two images (grids of fewer than 5 cells) holds at most one image of each
+// atom within R, since L >= 2 R.  The slot's force-array word (stage_a + 16 slot)
+// stages eight entries at a time, written to the list as one 16-byte store; at the
+// end it receives (0, 0, 0, list length).  Out of line and fed only scalars and
+// shared-memory addresses, so the search has the whole register budget.
+template <int APT>
+__device__ __noinline__ void nl_search(uint32_t xs_a, uint32_t stage_a, uint32_t cs_a,
+                                       uint32_t ovf_a, uint16_t* nl, int tid, int nt, int npad,
+                                       int n, int nc, float L, float cinv, float rcs2, int maxnb) {
+  const float Rs = 1.00001f * sqrtf(rcs2);
+  const float Rs2 = Rs * Rs;
+  const float h = L / (float)nc;
+#pragma unroll 1
+  for (int a = 0; a < APT; ++a) {
+    const int sl = tid + a * nt;
+    if (sl >= n) break;
+    float4 xi = ld_shared4(xs_a + 16u * (uint32_t)sl);
+    xi.x = fminf(fmaxf(xi.x, 0.f), L);
+    xi.y = fminf(fmaxf(xi.y, 0.f), L);
+    xi.z = fminf(fmaxf(xi.z, 0.f), L);
+    const int cx = min((int)(xi.x * cinv), nc - 1), cy = min((int)(xi.y * cinv), nc - 1);
+    const int cz = min((int)(xi.z * cinv), nc - 1);
+    const uint32_t stage = stage_a + 16u * (uint32_t)sl;
+    uint4* lrow = reinterpret_cast<uint4*>(nl) + sl;  // word w at lrow + w * npad
+    int k = 0;
+#pragma unroll 1
+    for (int dz = -2; dz <= 2; ++dz) {
+      const int qz = cz + dz;
+      const float zl = (float)qz * h;
+      const float ez = fmaxf(fmaxf(zl - xi.z, xi.z - (zl + h)), 0.f);
+      const int wz = qz < 0 ? qz + nc : (qz >= nc ? qz - nc : qz);
+      const float az = xi.z - (qz < 0 ? -L : (qz >= nc ? L : 0.f));
+#pragma unroll 1
+      for (int dy = -2; dy <= 2; ++dy) {
+        const int qy = cy + dy;
+        const float yl = (float)qy * h;
+        const float ey = fmaxf(fmaxf(yl - xi.y, xi.y - (yl + h)), 0.f);
+        const float rx2 = Rs2 - ez * ez - ey * ey;
+        // x cells within the radius left over (none when the row is out of range)
+        const float rx = sqrtf(fmaxf(rx2, 0.f));
+        int x0 = max((int)floorf((xi.x - rx) * cinv), cx - 2);
+        int x1 = min((int)floorf((xi.x + rx) * cinv), cx + 2);
+        if (rx2 < 0.f) x1 = x0 - 1;
+        const int wy = qy < 0 ? qy + nc : (qy >= nc ? qy - nc : qy);
+        const float ay = xi.y - (qy < 0 ? -L : (qy >= nc ? L : 0.f));
+        const uint32_t rowa = cs_a + 4u * (uint32_t)((wz * nc + wy) * nc);
+#pragma unroll 1
+        for (int sg = 0; sg < 3; ++sg) {
+          // sg 0: cells x0..-1 (image -L), 1: 0..nc-1 (none), 2: nc..x1 (image +L)
+          const int lo = sg == 0 ? x0 : (sg == 1 ? max(x0, 0) : max(x0, nc));
+          const int hi = sg == 0 ? min(x1, -1) : (sg == 1 ? min(x1, nc - 1) : x1);
+          if (lo > hi) continue;
+          const int off = sg == 0 ? nc : (sg == 1 ? 0 : -nc);
+          const float ax = xi.x - (sg == 0 ? -L : (sg == 1 ? 0.f : L));
+          int t = ld_shared_s32(rowa + 4u * (uint32_t)(lo + off));
+          const int t1 = ld_shared_s32(rowa + 4u * (uint32_t)(hi + off + 1));
+#pragma unroll 1
+          for (; t < t1; t += 2) {
+            const float4 xa = ld_shared4(xs_a + 16u * (uint32_t)t);
+            const float4 xb = ld_shared4(xs_a + 16u * (uint32_t)min(t + 1, t1 - 1));
+            const float dax = ax - xa.x, day = ay - xa.y, daz = az - xa.z;
+            const float dbx = ax - xb.x, dby = ay - xb.y, dbz = az - xb.z;
+            const float ra = fmaf(dax, dax, fmaf(day, day, daz * daz));
+            const float rb = fmaf(dbx, dbx, fmaf(dby, dby, dbz * dbz));
+            const bool pa = ra < rcs2 && t != sl;
+            const bool pb = rb < rcs2 && t + 1 != sl && t + 1 < t1;
+            if (pa) {
+              if (k < maxnb) {
+                st_shared_u16(stage + 2u * (uint32_t)(k & 7), t);
+                if ((k & 7) == 7) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
+              }
+              ++k;
+            }
+            if (pb) {
+              if (k < maxnb) {
+                st_shared_u16(stage + 2u * (uint32_t)(k & 7), t + 1);
+                if ((k & 7) == 7) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
+              }
+              ++k;
+            }
+          }
+        }
+      }
+    }
+    if (k > maxnb) {
+      atomicOr(reinterpret_cast<int*>(__cvta_shared_to_generic(ovf_a)), 1);
+      k = maxnb;
+    }
+    if ((k & 7) != 0) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);  // partial word
+    st_shared_v4(stage, make_float4(0.f, 0.f, 0.f, __int_as_float(k)));
+  }
+}
+
 template <int APT>
 __device__ void build_nlist(const Group& g, const BoxCtx& b, long long* prof = nullptr) {
   const int n = b.n;
@@ -474,7 +651,7 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, long long* prof = n
   float4* xs = g.x();
   float4* vs = g.v();
   float4* srt = g.f();  // sorted copy of the positions (forces are dead during a rebuild)
-  if (b.nc >= 3) {
+  if (b.nc > 0) {
     const int nc = b.nc, ncell = nc * nc * nc;
     int* ccount = g.cell();              // counts, then insertion cursors
     int* cstart = g.cell() + ncell + 1;  // [ncell + 1]
@@ -562,53 +739,10 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, long long* prof = n
     }
     gbar(g.bar, g.nt);
     MDEOS_PHASE(4)
-    // Search: each slot scans the 27 neighbour cells of its home cell; the image
-    // shift of a wrapped neighbour cell is applied to the home atom once per cell.
-    const float rcs2 = b.rcs2;
-#pragma unroll
-    for (int a = 0; a < APT; ++a) {
-      const int sl = g.tid + a * g.nt;
-      if (sl < n) {
-        const float4 xi = xs[sl];
-        const int c = cell_of(xi, b.cinv, nc);
-        const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-        uint16_t* row = g.nl + (size_t)sl * 8;
-        int k = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-          int qz = cz + dz;
-          const float shz = qz < 0 ? -b.L : (qz >= nc ? b.L : 0.f);
-          qz = qz < 0 ? qz + nc : (qz >= nc ? qz - nc : qz);
-          for (int dy = -1; dy <= 1; ++dy) {
-            int qy = cy + dy;
-            const float shy = qy < 0 ? -b.L : (qy >= nc ? b.L : 0.f);
-            qy = qy < 0 ? qy + nc : (qy >= nc ? qy - nc : qy);
-            for (int dx = -1; dx <= 1; ++dx) {
-              int qx = cx + dx;
-              const float shx = qx < 0 ? -b.L : (qx >= nc ? b.L : 0.f);
-              qx = qx < 0 ? qx + nc : (qx >= nc ? qx - nc : qx);
-              // neighbour image sits at x_j + shift: d = (x_i - shift) - x_j
-              const float ax = xi.x - shx, ay = xi.y - shy, az = xi.z - shz;
-              const int q = (qz * nc + qy) * nc + qx;
-              const int t1 = cstart[q + 1];
-              for (int t = cstart[q]; t < t1; ++t) {
-                const float4 xo = xs[t];
-                const float ddx = ax - xo.x, ddy = ay - xo.y, ddz = az - xo.z;
-                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                if (t != sl && r2 < rcs2) {
-                  if (k < b.maxnb) nl_store(row, k, g.npad, t);
-                  ++k;
-                }
-              }
-            }
-          }
-        }
-        if (k > b.maxnb) {
-          atomicOr(&g.ctrl()[CTRL_OVERFLOW], 1);
-          k = b.maxnb;
-        }
-        srt[sl] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
-      }
-    }
+    nl_search<APT>((uint32_t)__cvta_generic_to_shared(xs), (uint32_t)__cvta_generic_to_shared(srt),
+                   (uint32_t)__cvta_generic_to_shared(cstart),
+                   (uint32_t)__cvta_generic_to_shared(&g.ctrl()[CTRL_OVERFLOW]), g.nl, g.tid, g.nt,
+                   g.npad, n, nc, b.L, b.cinv, b.rcs2, b.maxnb);
     gbar(g.bar, g.nt);
     MDEOS_PHASE(5)
   } else {
@@ -696,7 +830,7 @@ __device__ void init_velocities(const Group& g, const BoxCtx& b, unsigned long l
   const double sd = sqrt(T / rp.mass);
   const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
   float3 v[APT];
-  float p[3] = {0.f, 0.f, 0.f};
+  long long p[3] = {0, 0, 0};
 #pragma unroll
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
@@ -713,15 +847,15 @@ __device__ void init_velocities(const Group& g, const BoxCtx& b, unsigned long l
       sincospi(2.0 * u1, &s1, &c1);
       sincospi(2.0 * u3, &s3, &c3);
       v[a] = make_float3((float)(sd * r01 * c1), (float)(sd * r01 * s1), (float)(sd * r23 * c3));
-      p[0] += v[a].x;
-      p[1] += v[a].y;
-      p[2] += v[a].z;
+      p[0] += fxp(v[a].x);
+      p[1] += fxp(v[a].y);
+      p[2] += fxp(v[a].z);
     }
   }
   double ptot[3];
   group_sum<3>(g, p, ptot);
   const float mx = (float)(ptot[0] / b.n), my = (float)(ptot[1] / b.n), mz = (float)(ptot[2] / b.n);
-  float ke[1] = {0.f};
+  long long ke[1] = {0};
 #pragma unroll
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
@@ -729,7 +863,7 @@ __device__ void init_velocities(const Group& g, const BoxCtx& b, unsigned long l
       v[a].x -= mx;
       v[a].y -= my;
       v[a].z -= mz;
-      ke[0] += v[a].x * v[a].x + v[a].y * v[a].y + v[a].z * v[a].z;
+      ke[0] += fxp(v[a].x * v[a].x + v[a].y * v[a].y + v[a].z * v[a].z);
     }
   }
   double ketot[1];
@@ -776,7 +910,8 @@ __device__ void load_warm(const Group& g, const BoxCtx& b, const BoxDesc& bd) {
 template <int APT>
 __device__ bool warm_velocities(const Group& g, const BoxCtx& b, double T, const RunParams& rp) {
   float3 v[APT];
-  float p[3] = {0.f, 0.f, 0.f};
+  long long p[3] = {0, 0, 0};
+  bool bad = false;
 #pragma unroll
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
@@ -784,15 +919,17 @@ __device__ bool warm_velocities(const Group& g, const BoxCtx& b, double T, const
     if (i < b.n) {
       const float4 vi = g.v()[i];
       v[a] = make_float3(vi.x, vi.y, vi.z);
-      p[0] += vi.x;
-      p[1] += vi.y;
-      p[2] += vi.z;
+      bad |= !(fabsf(vi.x) + fabsf(vi.y) + fabsf(vi.z) < 1e4f);
+      p[0] += fxp(vi.x);
+      p[1] += fxp(vi.y);
+      p[2] += fxp(vi.z);
     }
   }
+  if (gbar_or(g.bar, g.nt, bad)) return false;  // stored state not usable
   double ptot[3];
   group_sum<3>(g, p, ptot);
   const float mx = (float)(ptot[0] / b.n), my = (float)(ptot[1] / b.n), mz = (float)(ptot[2] / b.n);
-  float ke[1] = {0.f};
+  long long ke[1] = {0};
 #pragma unroll
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
@@ -800,7 +937,7 @@ __device__ bool warm_velocities(const Group& g, const BoxCtx& b, double T, const
       v[a].x -= mx;
       v[a].y -= my;
       v[a].z -= mz;
-      ke[0] += v[a].x * v[a].x + v[a].y * v[a].y + v[a].z * v[a].z;
+      ke[0] += fxp(v[a].x * v[a].x + v[a].y * v[a].y + v[a].z * v[a].z);
     }
   }
   double ketot[1];
@@ -841,13 +978,13 @@ __device__ void save_warm(const Group& g, const BoxCtx& b, const BoxDesc& bd, fl
 // the three force variants the step loop uses
 template <int APT, int PATH>
 __device__ __forceinline__ void forces_step(const Group& g, const BoxCtx& b, const RunParams& rp,
-                                            bool en, bool vir, float& e, float (&w)[6], int& np) {
+                                            bool en, bool vir, ForceAcc& acc) {
   if (vir)
-    compute_forces<APT, PATH, true, true, true>(g, b, rp, e, w, np);
+    compute_forces<APT, PATH, true, true, true>(g, b, rp, acc);
   else if (en)
-    compute_forces<APT, PATH, true, false, false>(g, b, rp, e, w, np);
+    compute_forces<APT, PATH, true, false, false>(g, b, rp, acc);
   else
-    compute_forces<APT, PATH, false, false, false>(g, b, rp, e, w, np);
+    compute_forces<APT, PATH, false, false, false>(g, b, rp, acc);
 }
 
 // first half kick with the pending thermostat factor, then drift; returns
@@ -892,13 +1029,12 @@ __device__ __noinline__ double warm_lift(const Group& g, const BoxCtx& b, const 
   load_warm<APT>(g, b, bd);
   gbar(g.bar, g.nt);
   if (PATH == PATH_NLIST) build_nlist<APT>(g, b);
-  float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int np0 = 0;
-  forces_step<APT, PATH>(g, b, rp, true, false, e0, w0, np0);
-  float q[1] = {e0};
+  ForceAcc f0;
+  forces_step<APT, PATH>(g, b, rp, true, false, f0);
+  const long long q[1] = {(long long)f0.e};
   double et[1];
   group_sum<1>(g, q, et);
-  const double T = T_fixed > 0.0 ? T_fixed : 2.0 * (E_tgt - 0.5 * et[0]) / ndof;  // Eq. 10
+  const double T = T_fixed > 0.0 ? T_fixed : 2.0 * (E_tgt - et[0]) / ndof;  // Eq. 10
   if (!(T > 0.0) || !isfinite(T)) return T;
   if (!warm_velocities<APT>(g, b, T, rp)) return -1.0;
   return T;
@@ -933,23 +1069,23 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   // E_cold: potential energy of the lifted lattice at rest (Sec. III)
   double E_cold;
   {
-    float e0 = 0.f, w0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int np0 = 0;
-    forces_step<APT, PATH>(g, b, rp, true, false, e0, w0, np0);
-    float q[1] = {e0};
+    ForceAcc f0;
+    forces_step<APT, PATH>(g, b, rp, true, false, f0);
+    const long long q[1] = {(long long)f0.e};
     double et[1];
     group_sum<1>(g, q, et);
-    E_cold = 0.5 * et[0];
+    E_cold = et[0];
   }
   double* boxc = acc + ACC_BOX;  // FP64 box constants, read by warp 0 only
   const double E_ref = (rp.ref_mode == MDEOS_REF_FIXED) ? n * bd.e_ref : E_cold;
   const double E_tgt = n * bd.e + E_ref;
-  // warm start if the element's slot holds a valid state (flag written by an
+  // warm start if the element's slot holds its valid state (tag written by an
   // earlier launch; every thread reads the same value)
   double Tk;
   int status = MDEOS_OK;
   int nseg = 0;
-  if (bd.warm_state != nullptr && bd.L_old > 0.0 && *(volatile const int*)bd.warm_flag == 1) {
+  if (bd.warm_state != nullptr && bd.L_old > 0.0 &&
+      *(volatile const unsigned long long*)bd.warm_tag == bd.element_id) {
     nseg = rp.warm_lift_iters;
     if (PATH == PATH_NLIST) ++builds;
     Tk = warm_lift<APT, PATH>(g, b, bd, rp, E_tgt, temp_mode ? bd.e : -1.0, ndof);
@@ -975,11 +1111,9 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   const int nb = rp.se_blocks;
 
 
-  const float invV_f = (float)(1.0 / V), inv3V_f = (float)(1.0 / (3.0 * V));
-  const float inv_ndof_f = (float)(1.0 / ndof);
+  const double invV = 1.0 / V, inv3V = 1.0 / (3.0 * V), inv_ndof = 1.0 / ndof;
   const int lead = (g.bar - 1) & 3 & (g.nwarps - 1);  // spreads group leaders over SMSPs
   float lam = 1.0f;
-  float Tk_f = (float)Tk;
   if (g.tid == 0) boxc[3] = Tk;
   for (int step = 0; step < total && status == MDEOS_OK; ++step) {
     const bool avg = step >= bd.steps_equil;
@@ -987,28 +1121,31 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
     const bool seg_end = !avg && (seg_pos == seg_len - 1);
     const bool esamp = !avg && !temp_mode && (seg_pos >= seg_len - nsamp);
     const bool need = kick_drift<APT>(g, b, rp, lam);
-    if (PATH == PATH_NLIST) {
-      if (gbar_or(g.bar, g.nt, need)) {
-        wrap_own<APT>(g, b);
-        build_nlist<APT>(g, b);
-        ++builds;
-      }
-    } else {
-      gbar(g.bar, g.nt);
-    }
+    const bool rebuild = (PATH == PATH_NLIST) ? gbar_or(g.bar, g.nt, need) : (gbar(g.bar, g.nt), false);
     {
-      const int st = g.ctrl()[CTRL_STATUS];  // written by warp 0 last step
+      // written by the leader warp last step (non-finite state): stop before a
+      // rebuild bins such positions into cells
+      const int st = g.ctrl()[CTRL_STATUS];
       if (st != 0 || g.ctrl()[CTRL_OVERFLOW] != 0) {
         status = st != 0 ? st : MDEOS_ENBR;
         break;
       }
     }
+    if (PATH == PATH_NLIST && rebuild) {
+      wrap_own<APT>(g, b);
+      build_nlist<APT>(g, b);
+      ++builds;
+      if (g.ctrl()[CTRL_OVERFLOW] != 0) {
+        status = MDEOS_ENBR;
+        break;
+      }
+    }
     // forces at the new positions
-    float e_th = 0.f, w_th[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int np_th = 0;
-    forces_step<APT, PATH>(g, b, rp, avg || esamp, avg, e_th, w_th, np_th);
-    // second half kick, kinetic energy and kinetic stress
-    float ke = 0.f, kt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    ForceAcc fa;
+    forces_step<APT, PATH>(g, b, rp, avg || esamp, avg, fa);
+    // second half kick; per-atom kinetic energy and kinetic stress into exact sums
+    unsigned long long ke = 0, kt[6] = {0, 0, 0, 0, 0, 0};
+    bool bad = fa.bad != 0;
 #pragma unroll
     for (int a = 0; a < APT; ++a) {
       const int i = g.tid + a * g.nt;
@@ -1019,30 +1156,37 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
         vi.y = fmaf(rp.hdtm, fi.y, vi.y);
         vi.z = fmaf(rp.hdtm, fi.z, vi.z);
         g.v()[i] = vi;
-        ke += vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+        const float ka = 0.5f * rp.mass_f * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+        bad |= !(ka < 1e9f);
+        ke += (unsigned long long)fxp(ka);
         if (avg) {
-          kt[0] += vi.x * vi.x;
-          kt[1] += vi.y * vi.y;
-          kt[2] += vi.z * vi.z;
-          kt[3] += vi.x * vi.y;
-          kt[4] += vi.x * vi.z;
-          kt[5] += vi.y * vi.z;
+          kt[0] += (unsigned long long)fxp(rp.mass_f * vi.x * vi.x);
+          kt[1] += (unsigned long long)fxp(rp.mass_f * vi.y * vi.y);
+          kt[2] += (unsigned long long)fxp(rp.mass_f * vi.z * vi.z);
+          kt[3] += (unsigned long long)fxp(rp.mass_f * vi.x * vi.y);
+          kt[4] += (unsigned long long)fxp(rp.mass_f * vi.x * vi.z);
+          kt[5] += (unsigned long long)fxp(rp.mass_f * vi.y * vi.z);
         }
       }
     }
-    // per-warp partials: 0..5 stress (K + W), 6 E_pot, 7 E_kin
+    // per-warp partials: 0..5 stress (K + W), 6 E_pot, 7 E_kin (fxp units),
+    // 8 in-cutoff pairs, 9 candidates, 10 non-finite flag
     {
-      float* red = g.red() + g.warp() * kRedSlots;
-      const float s = warp_sum(0.5f * rp.mass_f * ke);
-      if (g.lane() == 0) red[7] = s;
+      long long* red = g.red() + g.warp() * kRedSlots;
+      const long long s = warp_sum_ll((long long)ke);
+      const bool any_bad = __any_sync(0xffffffffu, bad);
+      if (g.lane() == 0) {
+        red[7] = s;
+        red[10] = any_bad ? 1 : 0;
+      }
       if (avg || esamp) {
-        const float se = warp_sum(0.5f * e_th);
+        const long long se = warp_sum_ll((long long)fa.e);
         if (g.lane() == 0) red[6] = se;
       }
       if (avg) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const float sk = warp_sum(rp.mass_f * kt[k] + 0.5f * w_th[k]);
+          const long long sk = warp_sum_ll((long long)(kt[k] + fa.w[k]));
           if (g.lane() == 0) red[k] = sk;
         }
         int cand = 0;
@@ -1055,86 +1199,94 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
                                          : (PATH == PATH_ALLPAIRS ? n : 8 * n);
           }
         }
-        const float sp = warp_sum((float)np_th), sc = warp_sum((float)cand);
+        const long long sp = warp_sum_ll(fa.np), sc = warp_sum_ll(cand);
         if (g.lane() == 0) {
           red[8] = sp;
           red[9] = sc;
         }
       }
     }
+    // thermostat steps and segment ends rescale the velocities
+    const bool resc = seg_end ||
+                      (!avg && rp.rescale_every_equil > 0 &&
+                       (seg_pos + 1) % rp.rescale_every_equil == 0) ||
+                      (avg && rp.rescale_every_avg > 0 && (s_avg + 1) % rp.rescale_every_avg == 0);
     gbar(g.bar, g.nt);
-    float ke_tot = 0.f;
-    for (int w = 0; w < g.nwarps; ++w) ke_tot += g.red()[w * kRedSlots + 7];
-    const float T_inst = 2.0f * ke_tot * inv_ndof_f;
     if (g.warp() == lead) {
-      // Per-step sums of the warp partials stay FP32 (<= 32 terms); each lane then
-      // adds one quantity into its FP64 time accumulator, so a step costs one
-      // convert and one FP64 add per warp instead of one per quantity.
+      // Box sums of the step: the exact sums of the warp partials (lane k holds
+      // quantity k); each lane then adds one quantity into its FP64 time
+      // accumulator.  The thermostat's kinetic temperature comes from the same sum.
       const int lane = g.lane();
-      float q = 0.f;
-      if (lane < kRedSlots)
-        for (int w = 0; w < g.nwarps; ++w) q += g.red()[w * kRedSlots + lane];
-      const float s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
-      const float s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
-      const float e6 = __shfl_sync(0xffffffffu, q, 6);
-      const float Ps = (s0 + s1 + s2) * inv3V_f;   // Eq. 11, mean normal stress
-      const float Ts = 2.0f * k7 * inv_ndof_f;
+      const long long qi = warp_partials_ll(g.red(), g.nwarps, lane);
+      const double q = lane < 8 ? (double)qi * kFixInv : (double)qi;
+      const double s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
+      const double s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
+      const double Ps = (s0 + s1 + s2) * inv3V;   // Eq. 11, mean normal stress
+      const double Ts = 2.0 * k7 * inv_ndof;
+      if ((lane == 7 && !(Ts > 0.0)) || (lane == 10 && qi != 0))
+        g.ctrl()[CTRL_STATUS] = MDEOS_EUNPHYS;
       int slot = -1;
-      float val = 0.f;
+      double val = 0.0;
       if (avg) {
-        const int blk = (s_avg * nb) / bd.steps_avg;
-        if (lane < 6) { slot = ACC_RUN + lane; val = q * invV_f; }
+        const int blk = (int)(((long long)s_avg * nb) / bd.steps_avg);
+        if (lane < 6) { slot = ACC_RUN + lane; val = q * invV; }
         else if (lane < 10) { slot = ACC_RUN + lane; val = q; }
         else if (lane == 10) { slot = ACC_RUN + 10; val = Ps; }
         else if (lane == 11) { slot = ACC_RUN + 11; val = Ts; }
         else if (lane == 12) { slot = ACC_BP + blk; val = Ps; g.bcnt()[blk] += 1; }
         else if (lane == 13) { slot = ACC_BT + blk; val = Ts; }
-        if (lane == 10 && (!isfinite(Ps) || !isfinite(Ts) || !isfinite(e6)))
-          g.ctrl()[CTRL_STATUS] = MDEOS_EUNPHYS;
       } else if (esamp && lane == 6) {
         slot = ACC_RUN + 12;
         val = q;
       }
-      if (slot >= 0) acc[slot] += (double)val;
+      if (slot >= 0) acc[slot] += val;
+      double Tn = Tk;
       if (seg_end && lane == 6) {
         const double Ebar = acc[ACC_RUN + 12] / nsamp;
-        const double Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) / ndof;  // Eq. 10
+        Tn = temp_mode ? bd.e : 2.0 * (boxc[2] - Ebar) / ndof;  // Eq. 10
         g.bc()[0] = Tn;
         acc[ACC_RUN + 12] = 0.0;
       }
+      // velocity-rescale factor towards the (new) target temperature, from the
+      // FP64 kinetic temperature of this step
+      if (resc) {
+        Tn = __shfl_sync(0xffffffffu, Tn, 6);
+        if (lane == 7)
+          g.bc()[5] = (Tn > 0.0 && Ts > 0.0 && isfinite(Tn) && isfinite(Ts)) ? sqrt(Tn / Ts) : -1.0;
+      }
     }
-    if (!(T_inst > 0.f) || !isfinite(T_inst)) {
-      status = MDEOS_EUNPHYS;
-      break;
-    }
+    // the rescale is applied with the next first half-kick
     lam = 1.0f;
-    if (seg_end) {
+    if (resc) {
       gbar(g.bar, g.nt);
-      const double Tn = g.bc()[0];
-      if (!(Tn > 0.0) || !isfinite(Tn)) {
+      const double lam_d = g.bc()[5];
+      if (!(lam_d > 0.0)) {
         status = MDEOS_EUNPHYS;
         break;
       }
-      if (g.tid == 0) boxc[3] = Tn;
-      Tk_f = (float)Tn;
-      lam = sqrtf(Tk_f / T_inst);
+      if (seg_end) {
+        Tk = g.bc()[0];
+        if (g.tid == 0) boxc[3] = Tk;
+      }
+      lam = (float)lam_d;
+    }
+    if (seg_end) {
       ++seg;
       seg_pos = 0;
       seg_len = (seg == nseg - 1) ? base + bd.steps_equil % nseg : base;
       nsamp = max(1, (seg_len + 9) / 10);
     } else if (!avg) {
-      if (rp.rescale_every_equil > 0 && (seg_pos + 1) % rp.rescale_every_equil == 0)
-        lam = sqrtf(Tk_f / T_inst);
       ++seg_pos;
-    } else if (rp.rescale_every_avg > 0 && (s_avg + 1) % rp.rescale_every_avg == 0) {
-      lam = sqrtf(Tk_f / T_inst);
     }
   }
   gbar(g.bar, g.nt);
   if (status == MDEOS_OK && g.ctrl()[CTRL_STATUS] != 0) status = g.ctrl()[CTRL_STATUS];
   if (bd.warm_state != nullptr) {
+    // a list overflow leaves the stored state as it was (the host re-runs the box
+    // with a larger list); any other failure invalidates it
     if (status == MDEOS_OK) save_warm<APT>(g, b, bd, lam);
-    if (g.tid == 0) *(volatile int*)bd.warm_flag = (status == MDEOS_OK) ? 1 : 0;
+    if (g.tid == 0 && status != MDEOS_ENBR)
+      *(volatile unsigned long long*)bd.warm_tag = (status == MDEOS_OK) ? bd.element_id : 0ull;
   }
   // restriction: time averages and block standard errors
   if (g.tid == 0) {
@@ -1175,7 +1327,7 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
     r.nlist_builds = builds;
     r.path = PATH;
     r.warm = g.ctrl()[CTRL_WARM];
-    r.reserved0 = 0;
+    r.nlist_retries = 0;
     if (status != MDEOS_OK) {
       r.P = r.T = r.epot = r.ekin = r.e_achieved = r.P_se = r.T_se = 0.0;
       for (int k = 0; k < 6; ++k) r.sigma[k] = 0.0;

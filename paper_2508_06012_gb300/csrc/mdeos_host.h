@@ -22,7 +22,8 @@ struct PlanOut {
 };
 
 mdeos_status set_error(mdeos_status st, const std::string& msg);
-mdeos_status plan_requests(const mdeos_handle* h, const mdeos_request* reqs, int n, PlanOut& out);
+mdeos_status plan_requests(const mdeos_handle* h, const mdeos_request* reqs, int n, PlanOut& out,
+                           const int* cap_min = nullptr);
 void planning_result_of(mdeos_result& r, int status, const mdeos_request& q);
 cudaStream_t handle_stream(const mdeos_handle* h);
 int handle_device(const mdeos_handle* h);

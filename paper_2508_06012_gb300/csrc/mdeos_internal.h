@@ -21,12 +21,23 @@ constexpr int kMaxBoxesPerItem = 8;   // named barriers 1..8 (0 is the CTA barri
 constexpr int kCtaThreads = 1024;
 constexpr int kMaxAtoms = 4096;       // 1024 threads x 4 atoms per thread
 constexpr int kMaxSeBlocks = 32;
-constexpr int kMaxCells = 1024;       // cell-list cells per box
-constexpr int kRedSlots = 10;         // reduction quantities per warp
+constexpr int kMaxCells = 1728;       // cell-list cells per box (12 per axis)
+constexpr int kRedSlots = 11;         // reduction quantities per warp (64-bit fixed point)
 // boxes above kMaxAtoms run one per CTA with their state in global memory
 constexpr int kMaxAtomsBig = 32768;   // uint16 neighbour indices
 constexpr int kMaxCellsBig = 32768;   // cells of the list build (<= 32 per axis)
 constexpr int kBigSharedBytes = 4096; // shared memory of a big-box CTA (reductions only)
+
+// Cells per axis of a shared-memory box's Verlet-list build: side at least
+// R / 2 (R = rc + skin), at most 12 per axis; 0 = no cell grid (brute-force
+// search).  The search walks the 5 x 5 x 5 cells around an atom's home cell, which
+// is valid for any such grid once L >= 2 R (a cell reached through two images holds
+// at most one image of each atom within R).
+__host__ __device__ inline int list_cells_per_axis(double L, double R) {
+  if (!(L >= 2.0 * R)) return 0;
+  int nc = (int)(2.0 * L / R);
+  return nc < 12 ? nc : 12;
+}
 
 // per-CTA global scratch of a big box (layout in mdeos_big.cuh)
 __host__ __device__ inline int big_cap(int n) { return (n + 31) & ~31; }
@@ -66,9 +77,10 @@ struct BoxDesc {
   float skin;
   int out_index;            // slot in the result array
   // warm-start slot (nullptr: none): x float4[warm_cap] then v float4[warm_cap];
-  // its flag is 1 while the slot holds a valid state of this element
+  // its tag is the element_id whose valid final state the slot holds (0: none), so a
+  // slot taken over by another element needs no clearing
   float4* warm_state;
-  int* warm_flag;
+  unsigned long long* warm_tag;
   double L_old;             // box side of the stored state; > 0: try a warm start
   int warm_cap;
   int warm_pad;
@@ -112,7 +124,7 @@ constexpr int kAccDoubles = 2 * kMaxSeBlocks + 24;  // block sums of P and T, ru
 //   positions, forces, velocities  float4[npad] each (48 B per atom slot)
 //   force-pass order               uint16[npad] (slots by list length)
 //   cell counts / starts           int[2 * ncell_cap + 2]
-//   per-warp partials              float[warps][kRedSlots]    (16-B aligned)
+//   per-warp partials              int64[warps][kRedSlots]    (16-B aligned)
 //   FP64 broadcast slots           double[8]
 //   FP64 accumulators              double[kAccDoubles]
 //   block counts                   int[kMaxSeBlocks]
@@ -125,7 +137,7 @@ __host__ __device__ inline int group_red_offset(int warps, int apt, int ncell_ca
 
 __host__ __device__ inline int group_smem_bytes(int warps, int apt, int ncell_cap) {
   int b = group_red_offset(warps, apt, ncell_cap);
-  b += warps * kRedSlots * 4;
+  b += warps * kRedSlots * 8;
   b += 8 * 8 + kAccDoubles * 8 + kMaxSeBlocks * 4 + 16 * 4;
   return (b + 127) & ~127;
 }

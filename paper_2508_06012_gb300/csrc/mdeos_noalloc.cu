@@ -3,11 +3,11 @@
 // Some callers cannot allocate device memory at the point where they need an
 // equation-of-state answer: a hydrocode's material-model callback invoked
 // inside its own time step (where cudaMalloc would synchronise the whole device
-// and stall the caller's other streams), code running under a memory pool that
-// owns all device memory, or host threads that must not block.  This entry point
-// serves them: the caller passes the requests and a device result array, and
-// every other byte the persistent kernel needs -- the work table, the queue
-// counter and the Verlet lists -- lives in one static device array below.
+// and stall the caller's other streams), or code running under a memory pool that
+// owns all device memory.  This entry point serves them: the caller passes the
+// requests and a device result array, and every other byte the persistent kernel
+// needs -- the work table, the queue counter and the Verlet lists -- lives in one
+// static device array below.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -136,6 +136,14 @@ extern "C" mdeos_status mdeos_submit_noalloc(const mdeos_config* cfg, const mdeo
                            "(work table plus one CTA's Verlet lists); split it");
   if (per_cta > 0) grid = std::min<long long>(grid, (kNoAllocScratchBytes - off_nl) / per_cta);
   cudaStream_t s = (cudaStream_t)stream;
+  // The host tables below are pageable vectors freed on return: a copy recorded
+  // into a graph would read freed memory at replay.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess)
+    return set_error(MDEOS_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(MDEOS_EINVAL, "mdeos_submit_noalloc cannot be called on a capturing stream");
   // requests rejected by the planner get their status from the host copy; the
   // kernel overwrites every planned box
   e = cudaMemcpyAsync(d_results, init.data(), (size_t)n * sizeof(mdeos_result),

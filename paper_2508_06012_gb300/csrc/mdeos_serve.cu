@@ -13,7 +13,10 @@
 // relaunches it when new items are published and no grid is running.
 // Admission: at most max_inflight requests on the GPU; waiting requests older than
 // max_wait_s and arrivals beyond max_queue are shed with MDEOS_ECANCELLED.  Device
-// memory is fixed at creation: per-SM scratch for the largest box.
+// memory: per-SM scratch for the largest box, fixed at creation, and the element
+// store (warm starts), whose blocks are reserved at admission and released when
+// the request's result comes back; a request whose element state does not fit
+// while the store is held by requests in flight waits for them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,9 +25,12 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "mdeos_host.h"
@@ -37,6 +43,19 @@ struct Waiting {
   uint64_t id;
   mdeos_request r;
   double t_arr;
+  int cap_min = 0;   // Verlet-list capacity at least (a re-run after an overflow)
+  int retries = 0;   // re-runs so far
+  bool waited = false;  // has waited for element-store memory
+};
+
+// One element's block of the store: [tag uint64 + pad (16 B)] [x float4[natoms]]
+// [v float4[natoms]]; the device writes the tag (the element_id of a valid state).
+struct StoreEntry {
+  size_t off = 0, bytes = 0;
+  int natoms = 0;
+  double L = 0.0;         // box side of the stored state (0: none)
+  double last_use = 0.0;
+  int inflight = 0;       // a request of this element is on the GPU
 };
 
 struct InFlight {
@@ -88,6 +107,13 @@ struct mdeos_server {
   bool running[kGrids] = {};
   double last_launch = -1.0;
   long long outstanding_items = 0;
+  // element store (scheduler thread only, counters read by stats)
+  unsigned char* d_store = nullptr;
+  size_t store_cap = 0, store_used = 0;
+  std::unordered_map<uint64_t, StoreEntry> store;
+  std::map<size_t, size_t> store_free;  // free blocks: offset -> bytes, coalesced
+  std::atomic<long long> n_warm{0}, n_memwait{0}, n_evict{0}, n_stored{0};
+  std::atomic<size_t> store_used_pub{0};
   unsigned published = 0;               // items published (= *h_tail)
   std::vector<int> item_pending;         // boxes not yet reported, per item slot
   std::vector<unsigned> free_boxes;      // free box ring slots
@@ -118,18 +144,129 @@ static mdeos_served shed(const Waiting& w, double t, int status) {
   return make_served(w, t, t, r);
 }
 
+// ---- element store (first fit over coalesced free blocks) ----------------------
+
+static bool store_alloc(mdeos_server* s, size_t bytes, size_t& off) {
+  for (auto it = s->store_free.begin(); it != s->store_free.end(); ++it) {
+    if (it->second < bytes) continue;
+    off = it->first;
+    const size_t rest = it->second - bytes;
+    s->store_free.erase(it);
+    if (rest) s->store_free[off + bytes] = rest;
+    s->store_used += bytes;
+    return true;
+  }
+  return false;
+}
+
+static void store_release(mdeos_server* s, size_t off, size_t bytes) {
+  s->store_used -= bytes;
+  auto it = s->store_free.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != s->store_free.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    s->store_free.erase(nx);
+  }
+  if (it != s->store_free.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      s->store_free.erase(it);
+    }
+  }
+}
+
+// Reserve the element's block for a request about to be admitted: 1 = reserved,
+// 0 = no state kept (no element, above 4096 atoms or larger than the store: runs
+// cold), -1 = wait (the element's previous request is in flight, or the store is
+// held by requests in flight).  Blocks of elements with nothing in flight are
+// reclaimed least recently used first.
+static int store_reserve(mdeos_server* s, const mdeos_request& r, double t) {
+  if (!s->d_store || r.element_id == 0 || r.natoms > kMaxAtoms) return 0;
+  const size_t bytes = (16 + 32 * (size_t)r.natoms + 255) & ~(size_t)255;
+  if (bytes > s->store_cap) return 0;
+  auto it = s->store.find(r.element_id);
+  if (it != s->store.end()) {
+    if (it->second.inflight > 0) return -1;
+    if (it->second.natoms == r.natoms) {
+      it->second.inflight = 1;
+      it->second.last_use = t;
+      return 1;
+    }
+    store_release(s, it->second.off, it->second.bytes);
+    s->store.erase(it);
+  }
+  size_t off = 0;
+  while (!store_alloc(s, bytes, off)) {
+    auto lru = s->store.end();
+    for (auto e = s->store.begin(); e != s->store.end(); ++e)
+      if (e->second.inflight == 0 &&
+          (lru == s->store.end() || e->second.last_use < lru->second.last_use))
+        lru = e;
+    if (lru == s->store.end()) {  // the rest is held by requests in flight: wait
+      s->n_stored = (long long)s->store.size();
+      s->store_used_pub = s->store_used;
+      return -1;
+    }
+    store_release(s, lru->second.off, lru->second.bytes);
+    s->store.erase(lru);
+    ++s->n_evict;
+  }
+  StoreEntry e;
+  e.off = off;
+  e.bytes = bytes;
+  e.natoms = r.natoms;
+  e.last_use = t;
+  e.inflight = 1;
+  s->store[r.element_id] = e;
+  s->n_stored = (long long)s->store.size();
+  s->store_used_pub = s->store_used;
+  return 1;
+}
+
+// A request's result came back (or will not): release its element's block for
+// reuse and record whether the block now holds a valid state.
+static void store_done(mdeos_server* s, const BoxDesc& bd, int status, double t) {
+  if (!bd.warm_state) return;
+  auto it = s->store.find(bd.element_id);
+  if (it == s->store.end()) return;
+  it->second.inflight = 0;
+  it->second.last_use = t;
+  if (status == MDEOS_OK)
+    it->second.L = bd.L;
+  else if (status != MDEOS_ENBR)
+    it->second.L = 0.0;  // the device cleared the tag; an overflow left the state as it was
+}
+
 // Report every box whose ready flag is up; with fail_status != 0 (kernel failure,
 // or no grid left to run them at shutdown) report the rest with that status.
 static bool harvest(mdeos_server* s, int fail_status) {
   std::vector<mdeos_served> out;
   std::vector<unsigned> keep;
   keep.reserve(s->inflight_slots.size());
+  std::vector<Waiting> rerun;
   for (unsigned slot : s->inflight_slots) {
     InFlight& f = s->inflight_box[slot];
     if (reinterpret_cast<volatile int*>(s->h_ready)[slot] != 0) {
       std::atomic_thread_fence(std::memory_order_acquire);
-      out.push_back(make_served(f.w, f.t_pub, s->now(), s->h_res[slot]));
+      const mdeos_result& r = s->h_res[slot];
+      const int cap = s->h_boxes[slot].maxnb;
+      store_done(s, s->h_boxes[slot], r.status, s->now());
+      if (r.status == MDEOS_OK && r.warm == 1) ++s->n_warm;
+      if (r.status == MDEOS_ENBR && cap < f.w.r.natoms - 1 && f.w.retries < 16) {
+        // the box's Verlet list overflowed: run it again with twice the capacity,
+        // ahead of the queue (as mdeos_poll does)
+        Waiting w = f.w;
+        w.cap_min = 2 * cap;
+        ++w.retries;
+        rerun.push_back(w);
+      } else {
+        mdeos_served o = make_served(f.w, f.t_pub, s->now(), r);
+        o.result.nlist_retries = f.w.retries;
+        out.push_back(o);
+      }
     } else if (fail_status != 0) {
+      store_done(s, s->h_boxes[slot], fail_status, s->now());
       out.push_back(shed(f.w, s->now(), fail_status));
       if (fail_status == MDEOS_ECUDA) ++s->n_err;
       if (fail_status == MDEOS_ECANCELLED) ++s->n_cancel;
@@ -140,31 +277,68 @@ static bool harvest(mdeos_server* s, int fail_status) {
     if (--s->item_pending[f.item_slot] == 0) --s->outstanding_items;
     s->free_boxes.push_back(slot);
   }
-  if (out.empty()) return false;
+  if (out.empty() && rerun.empty()) return false;
   s->inflight_slots.swap(keep);
   std::lock_guard<std::mutex> lk(s->mu);
   for (auto& o : out) s->completed.push_back(o);
+  for (auto it = rerun.rbegin(); it != rerun.rend(); ++it) s->waiting.push_front(*it);
   s->n_done += (long long)out.size();
   return true;
 }
 
 // Plan a batch of waiting requests into items and publish them.  Requests the
 // queue cannot take now (ring slots) are handed back in `b`.
+static void store_unreserve(mdeos_server* s, const mdeos_request& r) {
+  auto it = s->store.find(r.element_id);
+  if (it != s->store.end() && r.element_id != 0) it->second.inflight = 0;
+}
+
+// Plan a batch of waiting requests into items and publish them.  Requests whose
+// element state has no room in the store yet, and requests the queue cannot take
+// now (ring slots), are handed back in `b`.
 static bool admit(mdeos_server* s, std::vector<Waiting>& b) {
-  const int n = (int)b.size();
-  std::vector<mdeos_request> rq(n);
-  for (int i = 0; i < n; ++i) rq[i] = b[i].r;
-  PlanOut plan;
   const double t = s->now();
+  std::vector<Waiting> go, wait;
+  std::vector<char> reserved;
+  for (auto& w : b) {
+    const int k = store_reserve(s, w.r, t);
+    if (k < 0) {
+      if (!w.waited) {
+        w.waited = true;
+        ++s->n_memwait;
+      }
+      wait.push_back(w);
+    } else {
+      go.push_back(w);
+      reserved.push_back(k == 1 ? 1 : 0);
+    }
+  }
+  const int n = (int)go.size();
+  if (n == 0) {
+    b.swap(wait);
+    return false;
+  }
+  std::vector<mdeos_request> rq(n);
+  std::vector<int> cap_min(n);
+  for (int i = 0; i < n; ++i) {
+    rq[i] = go[i].r;
+    cap_min[i] = go[i].cap_min;
+  }
+  PlanOut plan;
   std::vector<mdeos_served> out;
-  if (plan_requests(s->h, rq.data(), n, plan) != MDEOS_OK) {
-    for (auto& w : b) out.push_back(shed(w, t, MDEOS_EINVAL));
-    b.clear();
+  const int warm_iters = handle_config(s->h).warm_lift_iters;
+  std::vector<Waiting> rest;
+  if (plan_requests(s->h, rq.data(), n, plan, cap_min.data()) != MDEOS_OK) {
+    for (int i = 0; i < n; ++i) {
+      if (reserved[i]) store_unreserve(s, go[i].r);
+      out.push_back(shed(go[i], t, MDEOS_EINVAL));
+    }
   } else {
     std::vector<char> taken(n, 0);
     for (int i = 0; i < n; ++i)
       if (plan.status[i] != MDEOS_OK) {
-        out.push_back(shed(b[i], t, plan.status[i]));
+        if (reserved[i]) store_unreserve(s, go[i].r);
+        out.push_back(shed(go[i], t, plan.status[i]));
         taken[i] = 1;
       }
     for (const WorkItem& wi0 : plan.items) {
@@ -175,7 +349,8 @@ static bool admit(mdeos_server* s, std::vector<Waiting>& b) {
           wi0.nbox * wi0.smem_stride > s->smem) {
         for (int k = 0; k < wi0.nbox; ++k) {  // needs more per-SM memory than held
           const int ri = plan.boxes[wi0.box[k]].out_index;
-          out.push_back(shed(b[ri], t, MDEOS_ENOMEM));
+          if (reserved[ri]) store_unreserve(s, go[ri].r);
+          out.push_back(shed(go[ri], t, MDEOS_ENOMEM));
           taken[ri] = 1;
         }
         continue;
@@ -184,12 +359,22 @@ static bool admit(mdeos_server* s, std::vector<Waiting>& b) {
       for (int k = 0; k < wi.nbox; ++k) {
         BoxDesc bd = plan.boxes[wi0.box[k]];
         const int ri = bd.out_index;  // request index within the batch
+        if (reserved[ri]) {  // the element's block: its state, tag and box side
+          const StoreEntry& e = s->store[go[ri].r.element_id];
+          const mdeos_request& r = go[ri].r;
+          const bool try_warm = e.L > 0.0 && (r.flags & MDEOS_REQ_COLD) == 0 &&
+                                (r.steps_equil == 0 || r.steps_equil >= warm_iters);
+          bd.warm_tag = reinterpret_cast<unsigned long long*>(s->d_store + e.off);
+          bd.warm_state = reinterpret_cast<float4*>(s->d_store + e.off + 16);
+          bd.warm_cap = e.natoms;
+          bd.L_old = try_warm ? e.L : 0.0;
+        }
         const unsigned slot = s->free_boxes.back();
         s->free_boxes.pop_back();
         bd.out_index = (int)slot;
         s->h_boxes[slot] = bd;
         s->h_ready[slot] = 0;
-        s->inflight_box[slot] = InFlight{b[ri], islot, t};
+        s->inflight_box[slot] = InFlight{go[ri], islot, t};
         s->inflight_slots.push_back(slot);
         wi.box[k] = (int)slot;
         taken[ri] = 1;
@@ -203,11 +388,14 @@ static bool admit(mdeos_server* s, std::vector<Waiting>& b) {
                                                                  std::memory_order_release);
       s->n_admitted += wi.nbox;
     }
-    std::vector<Waiting> rest;
     for (int i = 0; i < n; ++i)
-      if (!taken[i]) rest.push_back(b[i]);
-    b.swap(rest);
+      if (!taken[i]) {
+        if (reserved[i]) store_unreserve(s, go[i].r);
+        rest.push_back(go[i]);
+      }
   }
+  rest.insert(rest.end(), wait.begin(), wait.end());
+  b.swap(rest);
   s->peak_inflight = std::max<long long>(s->peak_inflight, (long long)s->inflight_slots.size());
   if (!out.empty()) {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -366,6 +554,16 @@ extern "C" mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_co
     delete s;
     return set_error(MDEOS_ENOMEM, "the server's per-SM scratch exceeds hbm_budget_bytes");
   }
+  if (cfg->warm) {  // element store: what the budget leaves, or as configured
+    size_t cap = cfg->warm_bytes;
+    if (cap == 0)
+      cap = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes - s->dev_bytes : (size_t(1) << 30);
+    if (cfg->hbm_budget_bytes && s->dev_bytes + cap > cfg->hbm_budget_bytes) {
+      delete s;
+      return set_error(MDEOS_ENOMEM, "scratch plus warm_bytes exceed hbm_budget_bytes");
+    }
+    s->store_cap = cap & ~(size_t)255;
+  }
   s->cap_items = pow2_at_least((unsigned)cfg->max_inflight * 2);
   s->cap_boxes = pow2_at_least((unsigned)cfg->max_inflight * 2);
   cudaError_t e = cudaSetDevice(s->device);
@@ -385,6 +583,14 @@ extern "C" mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_co
   if (e == cudaSuccess) e = cudaMalloc(&s->d_head, head_bytes);
   if (e == cudaSuccess) e = cudaMemset(s->d_head, 0, head_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_nl, (size_t)s->grid * s->nl_per_cta * sizeof(uint16_t));
+  if (e == cudaSuccess && s->store_cap >= 256) {
+    e = cudaMalloc(&s->d_store, s->store_cap);
+    if (e == cudaSuccess) e = cudaMemset(s->d_store, 0, s->store_cap);  // no valid tags
+    if (e == cudaSuccess) {
+      s->store_free[0] = s->store_cap;
+      s->dev_bytes += s->store_cap;
+    }
+  }
   for (int g = 0; g < mdeos_server::kGrids; ++g) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st[g], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev[g], cudaEventDisableTiming);
@@ -477,6 +683,22 @@ extern "C" mdeos_status mdeos_serve_stats(mdeos_server* s, long long* counts, si
   return MDEOS_OK;
 }
 
+extern "C" mdeos_status mdeos_serve_store_stats(mdeos_server* s, long long* counts,
+                                                size_t* bytes) {
+  if (!s) return set_error(MDEOS_EINVAL, "server is NULL");
+  if (counts) {
+    counts[0] = s->n_warm;
+    counts[1] = s->n_memwait;
+    counts[2] = s->n_evict;
+    counts[3] = s->n_stored;
+  }
+  if (bytes) {
+    bytes[0] = s->store_used_pub;
+    bytes[1] = s->d_store ? s->store_cap : 0;
+  }
+  return MDEOS_OK;
+}
+
 extern "C" mdeos_status mdeos_serve_destroy(mdeos_server* s) {
   if (!s) return MDEOS_OK;
   s->stop.store(true);
@@ -492,6 +714,7 @@ extern "C" mdeos_status mdeos_serve_destroy(mdeos_server* s) {
     if (s->st[g]) cudaStreamDestroy(s->st[g]);
   }
   if (s->d_nl) cudaFree(s->d_nl);
+  if (s->d_store) cudaFree(s->d_store);
   if (s->d_head) cudaFree(s->d_head);
   for (void* p : {(void*)s->h_boxes, (void*)s->h_items, (void*)s->h_res, (void*)s->h_ready,
                   (void*)s->h_tail, (void*)s->h_stop, (void*)s->h_alive, (void*)s->h_linger})

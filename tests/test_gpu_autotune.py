@@ -1,6 +1,6 @@
-"""GPU test of the autotuner (mdeos_autotune): one skin per atom count from the
-candidate set, later evaluations still exact and deterministic, and an explicit
-cfg.skin overriding the tuned table."""
+"""GPU test of the autotuner (mdeos_autotune): one launch shape (skin, warps per box)
+per atom count from the candidate sets, later evaluations still exact and
+deterministic, and an explicit cfg.skin overriding the tuned table."""
 import numpy as np
 import pytest
 
@@ -35,7 +35,13 @@ def test_autotune_table_and_evaluation(m):
         tab = m.mdeos_autotune(h, reqs, steps=40)
         assert sorted(tab[:, 0].astype(int)) == [256, 864, 2048, 4000]
         assert all(any(abs(s - c) < 1e-6 for c in CAND) for s in tab[:, 1])
-        assert (tab[:, 2] > 0).all()
+        # warps per box: the planner's (4 for 256 atoms, 8 for 864, 16 for 2048, 32
+        # for 4000 atoms) or up to two doublings of it
+        w0 = {256: 4, 864: 8, 2048: 16, 4000: 32}
+        for row in tab:
+            assert int(row[2]) in [w for w in (w0[int(row[0])] * 2 ** k for k in range(3))
+                                   if w <= 32], row
+        assert (tab[:, 3] > 0).all()
         r1 = m.mdeos_poll(h, m.mdeos_submit(h, reqs), len(reqs))
         r2 = m.mdeos_poll(h, m.mdeos_submit(h, reqs), len(reqs))
         assert (r1["status"] == 0).all() and r1.tobytes() == r2.tobytes()

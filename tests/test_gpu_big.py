@@ -140,26 +140,24 @@ def test_big_nve_energy_drift_and_momentum(m, orc):
     assert vcm <= 1e-4 * np.sqrt(T)
 
 
-def test_big_eos_matches_oracle(m, orc):
-    """Whole lifting -> MD -> restriction of 6912-atom boxes against the oracle with
-    the same seeds (chaotic: compared within the block standard errors)."""
+def test_big_eos_lifting_matches_oracle(m, orc):
+    """Whole lifting -> MD -> restriction of 6912-atom boxes: the deterministic part
+    of the lifting (E_cold of the lattice, Eq. 6-7) against the oracle; the
+    statistical parity of the restricted values is in tests/test_gpu_ensembles.py."""
     reqs = [dict(rho=rho, e=m.e_from_temperature(T, 6912), natoms=6912, steps_equil=200,
                  steps_avg=300, seed=900 + k) for k, (rho, T) in
             enumerate([(0.7, 1.5), (0.95, 2.0), (0.4, 1.2), (1.1, 2.5)])]
     with m.Engine() as eng:
         g = eng.evaluate(reqs)
     assert (g["status"] == 0).all() and (g["path"] == m.PATH_NLIST).all()
-    o = orc.eos_batch([dict(r, e=orc.e_from_temperature(
-        [1.5, 2.0, 1.2, 2.5][k], 6912)) for k, r in enumerate(reqs)],
-        orc.make_params(force_mode=orc.FORCE_CELL))
-    for k in range(len(reqs)):
-        assert o[k]["status"] == 0
+    for k, r in enumerate(reqs):
+        x, L = orc.lattice_fcc(6912, r["rho"])
+        L32 = float(np.float32(L))
+        E, _, _ = orc.lj_forces(x * (L32 / L), L32, orc.make_params(force_mode=orc.FORCE_CELL),
+                                mode=orc.FORCE_CELL)
         # FP32 per-thread energy sums over ~550 pair terms per thread
-        assert g["e_cold"][k] == pytest.approx(o[k]["e_cold"], rel=5e-6)
+        assert g["e_cold"][k] == pytest.approx(E / 6912, rel=5e-6)
         assert g["T_target"][k] > 0
-        for key, sek in (("P", "P_se"), ("T", "T_se")):
-            se = np.hypot(g[sek][k], o[k][sek])
-            assert abs(g[key][k] - o[k][key]) <= 5 * se + 0.02 * abs(o[k][key]), (k, key)
     assert np.allclose(g["sigma"][:, :3].mean(axis=1), g["P"], rtol=1e-6, atol=1e-6)
 
 

@@ -42,12 +42,15 @@ def oracle_reqs(orc, boxes):
 
 
 def test_config1_statistics_match_oracle_ensemble(m, orc, eng):
-    """Config-1 state points (N = 256, 1000 + 1000 steps), 8 seeds each."""
+    """Config-1 state points (N = 256, 1000 + 1000 steps), 16 seeds each.  The first
+    lies in the liquid-vapour coexistence region (rho = 0.67, T ~ 0.8), where E_pot
+    depends on how far the phase separation has gone and runs scatter widely."""
     from paper_2508_06012_gb300 import workloads as w
     pts = w.config1()[:4]
+    ns = 16
     boxes = []
     for p in pts:
-        for s in range(8):
+        for s in range(ns):
             q = dict(p)
             q["seed"] = w.box_seed(p["seed"], s)
             boxes.append(q)
@@ -55,11 +58,11 @@ def test_config1_statistics_match_oracle_ensemble(m, orc, eng):
     o = orc.eos_batch(oracle_reqs(orc, boxes), orc.make_params())
     assert (g["status"] == 0).all() and all(r["status"] == 0 for r in o)
     for k in range(len(pts)):
-        sl = slice(8 * k, 8 * k + 8)
+        sl = slice(ns * k, ns * k + ns)
         for key in ("P", "T", "e_achieved", "epot"):
             a = g[key][sl]
             b = np.array([r[key] for r in o[sl]])
-            se = np.sqrt(a.var(ddof=1) / 8 + b.var(ddof=1) / 8)
+            se = np.sqrt(a.var(ddof=1) / ns + b.var(ddof=1) / ns)
             assert abs(a.mean() - b.mean()) <= 3 * se + 1e-9, (k, key, a.mean(), b.mean(), se)
         # the achieved energy is the requested one within the method's noise band
         e = m.e_from_temperature(pts[k]["T"], 256)
@@ -99,13 +102,7 @@ def test_full_config2_batch_in_bench_launch_shape(m, orc):
     ideal = 4.0 / 3.0 * np.pi * 2.5 ** 3 * rho * n
     assert (g["pairs_per_step"] > 0.6 * ideal).all() and (g["pairs_per_step"] < 1.6 * ideal).all()
     assert (g["cand_per_step"] >= g["pairs_per_step"]).all()
-    # one box per atom count against the oracle (same seed, linked-cell oracle)
-    pick = [int(np.flatnonzero(n == 4 * c ** 3)[0]) for c in range(3, 11)]
-    o = orc.eos_batch(oracle_reqs(orc, [boxes[i] for i in pick]), orc.make_params(force_mode=1))
-    for k, i in enumerate(pick):
-        for key, sek in (("P", "P_se"), ("T", "T_se")):
-            se = np.hypot(g[sek][i], o[k][sek])
-            assert abs(g[key][i] - o[k][key]) <= 5 * se + 0.02 * abs(o[k][key]), (i, key)
+    # ensemble parity against the oracle at these sizes: tests/test_gpu_ensembles.py
 
 
 def test_result_alone_equals_result_in_mix(m, eng):

@@ -3,7 +3,9 @@ on identical inputs, through the C ABI.
 
 Tolerances (FP32 pair arithmetic against FP64; the largest forces and the
 per-thread FP32 partial sums set the scale):
-  forces     max_i |F_gpu - F_ref| / max(|F_ref,i|, F_rms) <= 1e-5
+  forces     ||F_gpu - F_ref||_2 / ||F_ref||_2 <= 1e-5; per atom
+             |dF_i| <= 1e-5 max(|F_ref,i|, F_rms) + 16 u sum_j |f_ij|
+                       + 2 u L sum_j |df_ij/dr|   (u = 2^-24)
   energy     |E_gpu - E_ref| <= 1e-6 |E_ref| + 1e-5 N
   virial     |W_gpu - W_ref| <= 2e-5 max|W_ref| + 1e-4 N
   trajectory max |r_gpu - r_ref| <= 1e-4 sigma after 100 steps from one state
@@ -57,6 +59,41 @@ def _force_err_atom(f_gpu, f_ref):
     return (np.linalg.norm(f_gpu - f_ref, axis=1) / np.maximum(fnorm, frms)).max()
 
 
+def _pair_force_sums(x, L):
+    """Per atom, sum_j |f_ij| and sum_j |df_ij/dr| (minimum image, r < rc): the
+    scales of the FP32 rounding in an atom's force."""
+    x = np.asarray(x, dtype=np.float64)
+    sf, sd = np.zeros(len(x)), np.zeros(len(x))
+    for i0 in range(0, len(x), 512):
+        d = x[i0:i0 + 512, None, :] - x[None, :, :]
+        d -= L * np.round(d / L)
+        r2 = (d ** 2).sum(-1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ir = 1.0 / np.sqrt(r2)
+            f = np.abs(24.0 * (2.0 * ir ** 13 - ir ** 7))
+            df = np.abs(24.0 * (-26.0 * ir ** 14 + 7.0 * ir ** 8))
+        out = (r2 >= RC * RC) | (r2 == 0.0)
+        f[out] = 0.0
+        df[out] = 0.0
+        sf[i0:i0 + 512] = f.sum(1)
+        sd[i0:i0 + 512] = df.sum(1)
+    return sf, sd
+
+
+def _fp32_atom_bound(x, L, f_ref):
+    """Per-atom bound on the FP32 force error: 1e-5 max(|F_i|, F_rms), plus 16 unit
+    roundoffs u = 2^-24 of sum_j |f_ij| (each pair term carries ~10 roundings -- r^2,
+    the reciprocal, r^-6, the force factor -- and the list sum one more per term),
+    plus the rounding of the position difference itself, u L per axis for a pair
+    across the periodic boundary, times sum_j |df_ij/dr|.  Where the pair forces
+    cancel to a small net force the last two terms dominate."""
+    fnorm = np.linalg.norm(f_ref, axis=1)
+    frms = np.sqrt((fnorm ** 2).mean())
+    sf, sd = _pair_force_sums(x, L)
+    u = 2.0 ** -24
+    return 1e-5 * np.maximum(fnorm, frms) + 16.0 * u * sf + 2.0 * u * L * sd
+
+
 def _ambiguous_pairs(x, L, rel=2e-6):
     d = x[:, None, :] - x[None, :, :]
     d -= L * np.round(d / L)
@@ -89,7 +126,12 @@ def test_forces_energy_virial_match_oracle(m, orc, n, rho, path, seed):
     ew = ew.cpu().numpy()
     assert np.isfinite(ew).all()
     assert _force_err(fg, f) <= 1e-5
-    assert _force_err_atom(fg, f) <= 1e-4
+    ea = _force_err_atom(fg, f)
+    err = np.linalg.norm(fg - f, axis=1)
+    bound = _fp32_atom_bound(x32, L, f)
+    print(f"per-atom force error n={n} rho={rho} path={path}: {ea:.3e} of max(|F_i|, F_rms), "
+          f"{(err / bound).max():.3f} of the FP32 bound")
+    assert (err <= bound).all(), (err / bound).max()
     assert abs(ew[0] - E) <= 1e-6 * abs(E) + 1e-5 * n
     assert np.abs(ew[1:] - W).max() <= 2e-5 * np.abs(W).max() + 1e-4 * n
     # in-cutoff ordered pair count: exact except pairs within FP32 rounding of rc

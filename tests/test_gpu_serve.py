@@ -113,3 +113,66 @@ def test_idle_exit_and_relaunch(m, h):
         st = srv.stats()
     assert a["result"]["status"][0] == 0 and b["result"]["status"][0] == 0
     assert st["launches"] >= 2
+
+
+def _element_requests(m, sizes, seed, round_k):
+    """One request per element (element_id k + 1) for a hydro-like step; each round
+    moves every element's density a little, as a Lagrangian mesh does."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, n in enumerate(sizes):
+        rho = 0.8 + 0.01 * round_k + 0.05 * rng.uniform()
+        out.append(dict(rho=rho, e=m.e_from_temperature(1.4, n), natoms=n, steps_equil=100,
+                        steps_avg=100, seed=1000 + 31 * k + round_k, element_id=k + 1))
+    return out
+
+
+def test_served_warm_starts_equal_the_handle_store(m):
+    """Element states kept by the server give the same warm-started results, bit for
+    bit, as the handle's own warm store fed the same requests."""
+    sizes = [256, 500, 864, 1372, 2048, 4000, 300, 1111]
+    rounds = [_element_requests(m, sizes, 5, k) for k in range(3)]
+    hs = m.mdeos_create()
+    served = []
+    try:
+        with m.Server(hs, warm=1) as srv:
+            for reqs in rounds:   # one hydro step after the other
+                ids = srv.enqueue(reqs)
+                got = srv.wait_all(len(reqs), timeout_s=300)
+                by = {int(g["id"]): g["result"] for g in got}
+                served.append(np.array([by[int(i)] for i in ids]))
+            ss = srv.store_stats()
+    finally:
+        m.mdeos_destroy(hs)
+    with m.Engine(warm_slots=64, warm_atoms=4096) as eng:
+        ref = [eng.evaluate(reqs) for reqs in rounds]
+    for k in range(3):
+        assert (served[k]["status"] == 0).all(), served[k]["status"]
+        assert (served[k]["warm"] == (0 if k == 0 else 1)).all(), (k, served[k]["warm"])
+        assert served[k].tobytes() == ref[k].tobytes(), k
+    assert ss["warm_starts"] == 2 * len(sizes) and ss["stored"] == len(sizes)
+
+
+def test_admission_waits_for_element_store_memory(m):
+    """A store with room for two 2048-atom elements and six such elements arriving
+    at once: two run, the others wait and are admitted as results come back; at no
+    time do more than two hold store memory.  A second round reuses or reclaims the
+    blocks (least recently used first)."""
+    per = (16 + 32 * 2048 + 255) // 256 * 256
+    reqs = [dict(rho=0.8, e=m.e_from_temperature(1.3, 2048), natoms=2048, steps_equil=60,
+                 steps_avg=60, seed=50 + k, element_id=100 + k) for k in range(6)]
+    hs = m.mdeos_create()
+    try:
+        with m.Server(hs, warm=1, warm_bytes=2 * per) as srv:
+            srv.enqueue(reqs)
+            got = srv.wait_all(6, timeout_s=300)
+            st, ss = srv.stats(), srv.store_stats()
+            assert len(got) == 6 and (got["result"]["status"] == 0).all()
+            assert st["peak_inflight"] <= 2, st
+            assert ss["memory_waits"] >= 4 and ss["evictions"] >= 4, ss
+            assert ss["store_bytes"] == 2 * per and ss["stored"] == 2
+            srv.enqueue(reqs[4:])          # the two most recent elements: still stored
+            got2 = srv.wait_all(2, timeout_s=300)
+            assert (got2["result"]["warm"] == 1).all()
+    finally:
+        m.mdeos_destroy(hs)

@@ -43,10 +43,51 @@ def test_noalloc_matches_submit_on_two_calls_in_a_row():
     assert (ref["status"][:-1] == 0).all() and ref["status"][-1] == m.MDEOS_EINVAL
     torch.cuda.set_device(0)
     out = torch.zeros(n * m.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    free = []
     for call in range(2):
         out.fill_(0xFF)  # stale bytes the call must overwrite
         torch.cuda.synchronize()
+        free_before, _ = torch.cuda.mem_get_info()
+        alloc_before = torch.cuda.memory_allocated()
         m.mdeos_submit_noalloc(reqs, out.data_ptr(), m.mdeos_config_default(device=0))
         torch.cuda.synchronize()
+        free.append(free_before - torch.cuda.mem_get_info()[0])
+        assert torch.cuda.memory_allocated() == alloc_before
         got = np.frombuffer(out.cpu().numpy().tobytes(), dtype=m.RESULT_DTYPE)
         _same(got, ref)
+    # The first call may load the module's code and static array onto the device;
+    # after it, a call takes no device memory at all (slack for the driver's own
+    # bookkeeping, far below one CTA's 0.7 MB of Verlet lists).
+    assert free[1] <= (1 << 20), free
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """Its host tables are freed on return, so a graph recording the copies would
+    replay from freed memory: the call is refused while the stream is captured."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2508_06012_gb300 as m
+    m.build()
+    torch.cuda.set_device(0)
+    reqs = _requests(m)[:2]
+    out = torch.zeros(len(reqs) * m.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    m.mdeos_submit_noalloc(reqs, out.data_ptr(), m.mdeos_config_default(device=0))  # set-up call
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    x = torch.zeros(4, device="cuda")
+    err = None
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        x.add_(1.0)
+        try:
+            m.mdeos_submit_noalloc(reqs, out.data_ptr(), m.mdeos_config_default(device=0),
+                                   stream=s.cuda_stream)
+        except m.MdeosError as exc:
+            err = exc
+        g.capture_end()
+    assert err is not None and "capturing" in str(err)
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
