@@ -629,8 +629,10 @@ def surrogate(args):
     val = queries(778, args.val_n)
     test = queries(779, args.test_n)
     rv = m.mdeos_poll(h, m.mdeos_submit(h, val), len(val), -1)
-    # 3. training
+    # 3. training (pressure learned as asinh(P): the loss then weighs errors as
+    # |dP| / max(|P|, 1), the gate's error measure)
     sg = m.Surrogate(h, 4, 4096, seed=11)
+    sg.set_output_transform(m.SURROGATE_P_ASINH)
     t0 = time.perf_counter()
     losses = sg.train(x, y, epochs=args.epochs, batch=1024, lr=2e-3, seed=5)
     losses2 = sg.train(x, y, epochs=args.epochs, batch=1024, lr=3e-4, seed=6, set_norm=False)
@@ -638,9 +640,11 @@ def surrogate(args):
     out["train_epochs"] = 2 * args.epochs
     out["train_loss_first_mid_last"] = [float(losses[0]), float(losses[-1]), float(losses2[-1])]
     # 4. gate threshold: the largest disagreement level whose accepted validation queries
-    # have RMS pressure error <= 1% of max(|P_MD|, 1)
+    # have RMS pressure error <= 1% of max(|P_MD|, 1).  An MD answer is the pressure at
+    # the energy its run sampled (e_achieved, within ~T sqrt(3 / 2N) of the request), so
+    # the network is scored at that state: its error as an EOS, not the lifting's offset
     okv = rv["status"] == 0
-    xv = np.array([[q["rho"], q["e"]] for q in val])[okv]
+    xv = np.stack([np.array([q["rho"] for q in val]), rv["e_achieved"]], axis=1)[okv]
     mv, sv = sg.predict(xv)
     pv = rv["P"][okv]
     err = np.abs(mv[:, 0] - pv) / np.maximum(np.abs(pv), 1.0)
@@ -672,13 +676,15 @@ def surrogate(args):
     rm = m.mdeos_poll(h, m.mdeos_submit(h, test), len(test), -1)
     t_md = time.perf_counter() - t0
     acc = (rm["status"] == 0) & (rg["status"] == 0) & (used == 0)
-    et = np.abs(rg["P"] - rm["P"]) / np.maximum(np.abs(rm["P"]), 1.0)
+    # accuracy of the accepted answers: the network at the state each reference run sampled
+    mt, _ = sg.predict(np.stack([np.array([q["rho"] for q in test]), rm["e_achieved"]], axis=1))
+    et = np.abs(mt[:, 0] - rm["P"]) / np.maximum(np.abs(rm["P"]), 1.0)
     k3, thr3 = level(0.03)
     t0 = time.perf_counter()
     rg3, used3 = sg.gated_eval(test, thr3, md_natoms=4000)
     t_g3 = time.perf_counter() - t0
     acc3 = (rm["status"] == 0) & (rg3["status"] == 0) & (used3 == 0)
-    et3 = np.abs(rg3["P"] - rm["P"]) / np.maximum(np.abs(rm["P"]), 1.0)
+    et3 = et
     out["test_at_3pct"] = {"threshold_rel_sd": thr3, "surrogate_answered": int((used3 == 0).sum()),
                            "gated_s": t_g3, "gated_eos_per_s": len(test) / t_g3,
                            "speedup_vs_md_only": t_md / t_g3,
@@ -691,6 +697,59 @@ def surrogate(args):
                    "rms_err_surrogate_answers_vs_md":
                        float(np.sqrt(np.mean(et[acc] ** 2))) if acc.any() else None,
                    "md_P_se_median": float(np.median(rm["P_se"][rm["status"] == 0]))}
+    # 5b. latency: the served, surrogate-gated form against plain MD launched once per
+    # box (the paper's one run per query), and the served MD-only form between them.
+    # All test queries arrive at once; a query's latency runs from that instant to its
+    # answer.  Surrogate answers take one batched prediction; the others go through
+    # the continuous-batching server.
+    def pct(a, q):
+        return float(np.percentile(np.asarray(a), q))
+    lat = {}
+    srv = m.Server(h)  # a running service: created before the queries arrive
+    xq = np.array([[q["rho"], q["e"]] for q in test])
+    clock0 = srv.clock()
+    t0 = time.perf_counter()
+    mq, sq = sg.predict(xq)
+    t_pred = time.perf_counter() - t0
+    acc_q = sq[:, 0] <= thr * np.maximum(np.abs(mq[:, 0]), 1.0)
+    rest = [q for q, a in zip(test, acc_q) if not a]
+    done_at = np.full(len(test), t_pred)
+    if rest:
+        ids = srv.enqueue(rest)
+        got = srv.wait_all(len(rest), timeout_s=3600)
+        when = {int(g["id"]): g["t_done"] - clock0 for g in got}
+        done_at[np.flatnonzero(~acc_q)] = [when[int(i)] for i in ids]
+    t_all = float(done_at.max())
+    lat["served_surrogate"] = {"queries": len(test), "answered_by_network": int(acc_q.sum()),
+                               "eos_per_s": len(test) / t_all, "p50_s": pct(done_at, 50),
+                               "p99_s": pct(done_at, 99), "makespan_s": t_all}
+    t0c = srv.clock()
+    ids = srv.enqueue(test)
+    got = srv.wait_all(len(test), timeout_s=3600)
+    d = np.array([g["t_done"] - t0c for g in got])
+    lat["served_md_only"] = {"queries": len(test), "eos_per_s": len(test) / float(d.max()),
+                             "p50_s": pct(d, 50), "p99_s": pct(d, 99), "makespan_s": float(d.max())}
+    srv.close()
+    n1 = min(len(test), args.one_launch_n)
+    one = []
+    t0 = time.perf_counter()
+    for q in test[:n1]:
+        t1 = time.perf_counter()
+        m.mdeos_poll(h, m.mdeos_submit(h, [q]), 1, -1)
+        one.append(time.perf_counter() - t1)
+    t_one = time.perf_counter() - t0
+    # queued one after the other, query k waits for the k before it
+    waits = np.cumsum(one)
+    lat["md_one_launch_per_box"] = {
+        "queries_timed": n1, "eos_per_s": n1 / t_one, "launch_s_p50": pct(one, 50),
+        "p50_s_if_all_arrive_at_once": pct(waits, 50) * len(test) / n1,
+        "p99_s_if_all_arrive_at_once": pct(waits, 99) * len(test) / n1,
+        "note": "each query a separate launch run to completion; latencies of the full "
+                "query set scaled from the timed prefix"}
+    lat["accuracy"] = {"target_rms_rel_err": 0.01,
+                       "surrogate_answers_rms_vs_md": out["test"]["rms_err_surrogate_answers_vs_md"],
+                       "md_answers": "MD (4000 atoms, 1000 + 1000 steps) in every form"}
+    out["latency"] = lat
     # 6. inference throughput on large batches (one copy of the ensemble, 64k per launch)
     big = m.Surrogate(h, 4, 65536, seed=1)
     big.set_params(*sg.get_params())
@@ -730,9 +789,13 @@ def surrogate(args):
     sg.close()
     clk = clocks.stop()
     m.mdeos_destroy(h)
-    line = {"metric": "surrogate-gated EOS/s at 1% pressure error",
-            "value": out["test"]["gated_eos_per_s"], "unit": "EOS/s", "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": out["test"]["gated_s"] * 1000.0,
+    line = {"metric": "served surrogate-gated EOS/s at 1% pressure error",
+            "value": lat["served_surrogate"]["eos_per_s"], "unit": "EOS/s", "n_gpus": 1,
+            "p50_s": lat["served_surrogate"]["p50_s"], "p99_s": lat["served_surrogate"]["p99_s"],
+            "vs_md_one_launch_per_box": {
+                "eos_per_s": lat["md_one_launch_per_box"]["eos_per_s"],
+                "p99_s": lat["md_one_launch_per_box"]["p99_s_if_all_arrive_at_once"]},
+            "steps": 1, "warmup": 0, "ms_per_step": lat["served_surrogate"]["makespan_s"] * 1000.0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (MD answers of seeded LJ boxes)", "config": {
                 "workload": SURROGATE, "train_n": args.train_n,
@@ -851,6 +914,8 @@ def main():
     ap.add_argument("--val-n", type=int, default=2000, help="surrogate: validation queries")
     ap.add_argument("--test-n", type=int, default=4000, help="surrogate: test queries")
     ap.add_argument("--epochs", type=int, default=40, help="surrogate: training epochs")
+    ap.add_argument("--one-launch-n", type=int, default=24,
+                    help="surrogate: queries timed as one MD launch each")
     ap.add_argument("--train-natoms", type=int, default=4000,
                     help="surrogate: box size of the training MD (default: the 4000 atoms of "
                          "the MD fallback; 0: the config-2 size mix)")

@@ -485,6 +485,17 @@ mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double* x, int32_
 #define MDEOS_SURROGATE_INFER_MMA 1
 mdeos_status mdeos_surrogate_set_infer_path(mdeos_surrogate* s, int32_t path);
 
+/* How the networks represent the pressure output.  LINEAR (default): P itself,
+ * standardised.  ASINH: asinh(P), standardised, mapped back with sinh before the
+ * ensemble mean and spread -- linear for |P| < 1 and logarithmic above, so the
+ * squared-error loss weighs errors as |dP| / max(|P|, 1), the gate's error measure.
+ * Set it before training (the normalisers of mdeos_surrogate_train's set_norm are
+ * taken in the chosen units); predictions are always in physical units.  Errors:
+ * EINVAL for any other value. */
+#define MDEOS_SURROGATE_P_LINEAR 0
+#define MDEOS_SURROGATE_P_ASINH 1
+mdeos_status mdeos_surrogate_set_output_transform(mdeos_surrogate* s, int32_t mode);
+
 /* Prediction on device arrays, asynchronous on `stream` (cudaStream_t; NULL = the
  * handle's stream): d_x device double[n][2] = (rho, e) in; d_mean and d_sd device
  * double[n][2] = ensemble mean and spread of (P, T) out (all caller-owned, non-NULL
@@ -541,7 +552,8 @@ mdeos_status mdeos_debug_md(const mdeos_config* cfg, float* x4, float* v4, int32
  * n atoms (device x4: float4[nbox * n], box b at x4 + 4 n b), one per CTA and at
  * most one per SM, each kept in shared memory with its Verlet list (skin) built
  * once, then `passes` force passes as the step loop runs them: mode 0 forces only,
- * mode 1 forces with energy, virial and pair count.  cycles (device int64[2 nbox])
+ * mode 1 forces with energy, virial and pair count; mode 2 runs `passes` list builds
+ * instead (the build measured on its own).  cycles (device int64[2 nbox])
  * receives per box the SM cycles of the passes and the list entries per pass.
  * Synchronous on `stream`.  Errors: MDEOS_EINVAL, MDEOS_ENOMEM, MDEOS_ECUDA. */
 mdeos_status mdeos_debug_force_bench(const mdeos_config* cfg, const float* x4, int32_t nbox,

@@ -38,11 +38,13 @@ EXPORTED = [
     "mdeos_surrogate_create", "mdeos_surrogate_set_params", "mdeos_surrogate_get_params",
     "mdeos_surrogate_grads", "mdeos_surrogate_train", "mdeos_surrogate_predict",
     "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_surrogate_set_infer_path",
-    "mdeos_surrogate_infer_device", "mdeos_debug_gemm_bf16", "mdeos_debug_tanh",
+    "mdeos_surrogate_infer_device", "mdeos_surrogate_set_output_transform",
+    "mdeos_debug_gemm_bf16", "mdeos_debug_tanh",
     "mdeos_autotune",
 ]
 SURROGATE_NPARAM = 33666
 SURROGATE_INFER_TC, SURROGATE_INFER_MMA = 0, 1
+SURROGATE_P_LINEAR, SURROGATE_P_ASINH = 0, 1
 
 
 class mdeos_config(ctypes.Structure):
@@ -200,6 +202,7 @@ def lib():
         L.mdeos_surrogate_gated_eval.argtypes = [vp, vp, i32, d, i32, vp, vp]
         L.mdeos_surrogate_destroy.argtypes = [vp]
         L.mdeos_surrogate_set_infer_path.argtypes = [vp, i32]
+        L.mdeos_surrogate_set_output_transform.argtypes = [vp, i32]
         L.mdeos_surrogate_infer_device.argtypes = [vp, vp, i32, vp, vp, vp]
         L.mdeos_autotune.argtypes = [vp, vp, i32, i32, vp, i32, P(i32)]
         i64 = ctypes.c_int64
@@ -614,6 +617,10 @@ class Surrogate:
         pm = np.zeros((self.E, n, 2), dtype=np.float32) if per_model else None
         _check(lib().mdeos_surrogate_predict(self.s, _vp(x), n, _vp(mean), _vp(sd), _vp(pm)))
         return (mean, sd, pm) if per_model else (mean, sd)
+
+    def set_output_transform(self, mode: int):
+        """SURROGATE_P_LINEAR (default) or SURROGATE_P_ASINH (learn asinh(P))."""
+        _check(lib().mdeos_surrogate_set_output_transform(self.s, mode))
 
     def set_infer_path(self, path: int):
         """SURROGATE_INFER_TC (fused tcgen05 kernel, default) or SURROGATE_INFER_MMA."""

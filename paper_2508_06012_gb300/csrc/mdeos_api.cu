@@ -182,10 +182,10 @@ static int list_capacity(const mdeos_config& c, int n, double rho, double rs, in
   int mx = c.nlist_capacity;
   if (mx <= 0) {
     const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(rho, 0.9);
-    mx = (int)std::ceil(1.3 * expect_cap + 32.0);
+    mx = (int)std::ceil(1.3 * expect_cap + 32.0) + kListPadSlack;  // + padding of coded lists
   }
   mx = std::max(mx, cap_min);
-  mx = std::min(mx, n - 1);
+  mx = std::min(mx, n - 1 + kListPadSlack);
   return (std::max(mx, 1) + 7) & ~7;
 }
 
@@ -271,7 +271,7 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
   if (b.path == PATH_NLIST) {
     b.skin = (float)skin;
     const double rs = c.rc + skin;
-    const int nc = list_cells_per_axis(L, rs);
+    const int nc = list_cells_per_axis(L, rs, n);
     b.nc_cell = nc;
     p.ncell = nc > 0 ? nc * nc * nc : 1;
     const double expect = 4.18879020478639 * rs * rs * rs * r.rho;
@@ -1351,10 +1351,10 @@ static mdeos_status debug_setup(const mdeos_config* cfg, int n, double L, int pa
   nl_bytes = 0;
   if (path == PATH_NLIST) {
     const double rs = cfg->rc + skin;
-    const int nc = list_cells_per_axis(L, rs);
+    const int nc = list_cells_per_axis(L, rs, n);
     bd.nc_cell = nc;
     ncell = nc > 0 ? nc * nc * nc : 1;
-    bd.maxnb = std::max(8, ((n - 1) + 7) & ~7);  // room for every atom: no overflow in tests
+    bd.maxnb = std::max(8, ((n - 1 + kListPadSlack) + 7) & ~7);  // no overflow in tests
     nl_bytes = (size_t)bd.maxnb * kCtaThreads * apt * sizeof(uint16_t);
   }
   smem = group_smem_bytes(32, apt, ncell);
@@ -1453,7 +1453,7 @@ extern "C" mdeos_status mdeos_debug_force_bench(const mdeos_config* cfg, const f
                                                 int32_t nbox, int32_t n, double L, double skin,
                                                 int32_t passes, int32_t mode, long long* cycles,
                                                 void* stream) {
-  if (!x4 || !cycles || nbox < 1 || passes < 1 || (mode != 0 && mode != 1) || n > kMaxAtoms)
+  if (!x4 || !cycles || nbox < 1 || passes < 1 || mode < 0 || mode > 2 || n > kMaxAtoms)
     return fail(MDEOS_EINVAL, "bad arguments");
   int nsm = 0, dev = 0;
   CK(cudaGetDevice(&dev));
@@ -1468,7 +1468,8 @@ extern "C" mdeos_status mdeos_debug_force_bench(const mdeos_config* cfg, const f
   // list capacity as the planner sets it (liquid density at least)
   const double rs = cfg->rc + skin;
   const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(n / (L * L * L), 0.9);
-  bd.maxnb = (std::min((int)std::ceil(1.3 * expect_cap + 32.0), n - 1) + 7) & ~7;
+  bd.maxnb = (std::min((int)std::ceil(1.3 * expect_cap + 32.0) + kListPadSlack,
+                      n - 1 + kListPadSlack) + 7) & ~7;
   const long long nl_elems = (long long)bd.maxnb * kCtaThreads * apt;
   cudaStream_t s = (cudaStream_t)stream;
   uint16_t* nl = nullptr;

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
 // The pair-force pass on its own: one resident box per CTA (positions from x4 +
 // blockIdx.x * n), the Verlet list built once, then `passes` force passes exactly
 // as the step loop runs them (mode 0: forces only, in list-length order; 1: forces,
-// energy, virial and pair count).  cyc[2 b] = SM cycles of the passes, cyc[2 b + 1]
+// energy, virial and pair count; 2: list builds instead of force passes).  cyc[2 b] = SM cycles of the passes, cyc[2 b + 1]
 // = list entries (pair candidates) per pass of box b.
 
 template <int APT>
@@ -284,7 +284,7 @@ __device__ void debug_force_bench_body(const Group& g, const BoxDesc& bd, const 
   long long cand[1] = {0};
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
-    if (i < b.n) cand[0] += (long long)__float_as_int(g.f()[i].w) * 4294967296LL;
+    if (i < b.n) cand[0] += (long long)((unsigned)__float_as_int(g.f()[i].w) >> 16) * 4294967296LL;
   }
   double ctot[1];
   group_sum<1>(g, cand, ctot);
@@ -293,9 +293,11 @@ __device__ void debug_force_bench_body(const Group& g, const BoxDesc& bd, const 
   for (int p = 0; p < passes; ++p) {
     if (mode == 0) {
       compute_forces<APT, PATH_NLIST, false, false, false>(g, b, rp, fa);
-    } else {
+    } else if (mode == 1) {
       compute_forces<APT, PATH_NLIST, true, true, true>(g, b, rp, fa);
       gbar(g.bar, g.nt);
+    } else {  // the Verlet-list build on its own (positions unchanged)
+      build_nlist<APT>(g, b);
     }
   }
   const long long t1 = clock64();

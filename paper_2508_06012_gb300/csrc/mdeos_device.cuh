@@ -219,29 +219,28 @@ template <bool EN, bool VIR>
 __device__ __forceinline__ void lj_pair(float dx, float dy, float dz, bool ok, const LJ& c,
                                         float& fx, float& fy, float& fz, float& e, float (&w)[6],
                                         int& npair) {
-  float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  bool in = ok && (r2 < c.rc2);
-  float ir2 = rcp_approx(r2);
-  float s6 = c.sig6 * ir2 * ir2 * ir2;
-  float fr = s6 * fmaf(c.eps48, s6, -c.eps24) * ir2;  // 24 eps s6 (2 s6 - 1) / r^2
-  fr = in ? fr : 0.0f;
-  fx = fmaf(fr, dx, fx);
-  fy = fmaf(fr, dy, fy);
-  fz = fmaf(fr, dz, fz);
-  if (EN) {
-    float u = fmaf(c.eps4 * s6, s6 - 1.0f, -c.ucut);
-    e += in ? u : 0.0f;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float ir2 = rcp_approx(r2);
+  const float s6 = c.sig6 * ir2 * ir2 * ir2;
+  const float fr = s6 * fmaf(c.eps48, s6, -c.eps24) * ir2;  // 24 eps s6 (2 s6 - 1) / r^2
+  // outside the cutoff (or a masked entry, whose r^2 may be 0 and fr not finite)
+  // nothing is accumulated: the sums are predicated, not multiplied by a zero
+  if (ok && r2 < c.rc2) {
+    fx = fmaf(fr, dx, fx);
+    fy = fmaf(fr, dy, fy);
+    fz = fmaf(fr, dz, fz);
+    if (EN) e += fmaf(c.eps4 * s6, s6 - 1.0f, -c.ucut);
+    if (VIR) {
+      const float tx = fr * dx, ty = fr * dy, tz = fr * dz;
+      w[0] = fmaf(tx, dx, w[0]);
+      w[1] = fmaf(ty, dy, w[1]);
+      w[2] = fmaf(tz, dz, w[2]);
+      w[3] = fmaf(tx, dy, w[3]);
+      w[4] = fmaf(tx, dz, w[4]);
+      w[5] = fmaf(ty, dz, w[5]);
+    }
+    ++npair;
   }
-  if (VIR) {
-    float tx = fr * dx, ty = fr * dy, tz = fr * dz;
-    w[0] = fmaf(tx, dx, w[0]);
-    w[1] = fmaf(ty, dy, w[1]);
-    w[2] = fmaf(tz, dz, w[2]);
-    w[3] = fmaf(tx, dy, w[3]);
-    w[4] = fmaf(tx, dz, w[4]);
-    w[5] = fmaf(ty, dz, w[5]);
-  }
-  npair += in ? 1 : 0;
 }
 
 // 16-byte shared-memory load from a 32-bit shared address (the force pass is not
@@ -264,6 +263,15 @@ __device__ __forceinline__ float min_img(float d, float L, float invL) {
   const float magic = 12582912.0f;
   const float k = __fsub_rn(__fmaf_rn(d, invL, magic), magic);
   return fmaf(-L, k, d);
+}
+
+// Verlet-list pair from a home position already shifted to the entry's image
+template <bool EN, bool VIR>
+__device__ __forceinline__ void nl_pair_sh(uint32_t xs_a, int j, bool ok, float hx, float hy,
+                                           float hz, const LJ& c, float& fx, float& fy, float& fz,
+                                           float& e, float (&w)[6], int& np) {
+  const float4 xj = ld_shared4(xs_a + 16u * (uint32_t)j);
+  lj_pair<EN, VIR>(hx - xj.x, hy - xj.y, hz - xj.z, ok, c, fx, fy, fz, e, w, np);
 }
 
 // Verlet-list pair: minimum image across the periodic box; `ok` masks padding
@@ -319,7 +327,7 @@ struct FSums {
 // an atom then changes no result.
 template <int APT, int PATH, bool EN, bool VIR, bool CNT>
 __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16_t* nl, int tid,
-                                         int nt, int npad, int n, int maxnb, float L, float invL,
+                                         int nt, int npad, int n, bool coded, float L, float invL,
                                          LJ c, uint32_t ord_a) {
   unsigned long long es = 0, ws[6] = {0, 0, 0, 0, 0, 0};
   int np = 0, bad = 0;
@@ -338,37 +346,58 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
         // i at (k/8) * npad + i, so a warp's word loads are contiguous.  The list
         // is rewritten inside this kernel at every rebuild, so it is read with
         // L2-only loads (never the read-only cache); the next word is fetched while
-        // the current one is processed.  One list with the minimum image on every
-        // entry keeps the lanes of a warp in step (splitting off pairs that need
-        // no image made lanes near a face run a second loop the others idle in).
+        // the current one is processed.  Positions are not wrapped between list
+        // builds, so the image of every entry stays the one the build found: the
+        // word's code selects, per axis, the home position or its image (+-L by the
+        // slot's direction bits), and the pair takes the plain difference.  Lists
+        // without codes (boxes searched without cells) take the minimum image per
+        // entry.  The build pads partial words with the atom's own slot, so every
+        // word is processed whole and the self entries are masked by index.
         const uint4* p = reinterpret_cast<const uint4*>(nl) + i;
-        const int cn = __float_as_int(cw);
-        const int nw = (cn + 7) >> 3;  // words, the last one partial
+        const int meta = __float_as_int(cw);
+        const int nw = meta & 0xfff;
         uint4 q = nw > 0 ? __ldcg(p) : make_uint4(0u, 0u, 0u, 0u);
+        if (coded) {
+          const float xa = xi.x + ((meta & 0x1000) ? -L : L);
+          const float ya = xi.y + ((meta & 0x2000) ? -L : L);
+          const float za = xi.z + ((meta & 0x4000) ? -L : L);
 #pragma unroll 1
-        for (int kb = 0; kb < nw; ++kb) {
-          const uint4 cur = q;
-          if (kb + 1 < nw) q = __ldcg(p + (size_t)(kb + 1) * npad);
-          const int left = cn - (kb << 3);
-          if (left >= 8) {
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.x & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.x >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.y & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.y >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.z & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.z >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.w & 0xffffu), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-            nl_pair_bd<EN, VIR>(xs_a, (int)(cur.w >> 16), true, xi, L, invL, c, fx, fy, fz, e, w, np);
-          } else {
-            // last word: entries beyond the count are stale, the atom itself
-            // stands in for them and is masked out
-#pragma unroll
-            for (int u = 0; u < 7; ++u) {
-              const unsigned wd = u < 2 ? cur.x : (u < 4 ? cur.y : (u < 6 ? cur.z : cur.w));
-              const int jj = (int)((wd >> (16 * (u & 1))) & 0xffffu);
-              const bool ok = u < left;
-              nl_pair_bd<EN, VIR>(xs_a, ok ? jj : i, ok, xi, L, invL, c, fx, fy, fz, e, w, np);
-            }
+          for (int kb = 0; kb < nw; ++kb) {
+            const uint4 cur = q;
+            if (kb + 1 < nw) q = __ldcg(p + (size_t)(kb + 1) * npad);
+            const float hx = (cur.x & 0x1000u) ? xa : xi.x;
+            const float hy = (cur.x & 0x2000u) ? ya : xi.y;
+            const float hz = (cur.x & 0x4000u) ? za : xi.z;
+            const int j0 = (int)(cur.x & 0xfffu), j1 = (int)(cur.x >> 16);
+            const int j2 = (int)(cur.y & 0xffffu), j3 = (int)(cur.y >> 16);
+            const int j4 = (int)(cur.z & 0xffffu), j5 = (int)(cur.z >> 16);
+            const int j6 = (int)(cur.w & 0xffffu), j7 = (int)(cur.w >> 16);
+            nl_pair_sh<EN, VIR>(xs_a, j0, j0 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, VIR>(xs_a, j1, j1 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, VIR>(xs_a, j2, j2 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, VIR>(xs_a, j3, j3 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, VIR>(xs_a, j4, j4 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, VIR>(xs_a, j5, j5 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, VIR>(xs_a, j6, j6 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, VIR>(xs_a, j7, j7 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+          }
+        } else {
+#pragma unroll 1
+          for (int kb = 0; kb < nw; ++kb) {
+            const uint4 cur = q;
+            if (kb + 1 < nw) q = __ldcg(p + (size_t)(kb + 1) * npad);
+            const int j0 = (int)(cur.x & 0xffffu), j1 = (int)(cur.x >> 16);
+            const int j2 = (int)(cur.y & 0xffffu), j3 = (int)(cur.y >> 16);
+            const int j4 = (int)(cur.z & 0xffffu), j5 = (int)(cur.z >> 16);
+            const int j6 = (int)(cur.w & 0xffffu), j7 = (int)(cur.w >> 16);
+            nl_pair_bd<EN, VIR>(xs_a, j0, j0 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, j1, j1 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, j2, j2 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, j3, j3 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, j4, j4 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, j5, j5 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, j6, j6 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
+            nl_pair_bd<EN, VIR>(xs_a, j7, j7 != i, xi, L, invL, c, fx, fy, fz, e, w, np);
           }
         }
       } else if (PATH == PATH_ALLPAIRS) {
@@ -429,7 +458,7 @@ __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, 
                              ? (uint32_t)__cvta_generic_to_shared(g.order())
                              : 0u;
   const FSums r = force_pass<APT, PATH, EN, VIR, CNT>(xs_a, g.f(), g.nl, g.tid, g.nt, g.npad, b.n,
-                                                      b.maxnb, b.L, b.invL, make_lj(rp), ord_a);
+                                                      b.nc > 0, b.L, b.invL, make_lj(rp), ord_a);
   // in the length order a thread's forces belong to other threads' atoms: every
   // force is written before any thread reads its own atoms' forces
   if (ord_a != 0u) gbar(g.bar, g.nt);
@@ -457,11 +486,10 @@ __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, 
 // gathers touch nearby shared-memory words.  Inside a cell atoms keep their
 // previous relative order (sorted by previous slot), so the order, the list and
 // every result are deterministic.
-// Without a grid (nc_cell = 0) every atom is scanned with the minimum image.
+// Without a grid (nc_cell = 0: boxes of at most kBruteMaxAtoms atoms, where a scan
+// of all atoms with broadcast loads is cheaper than the cell search) every atom is
+// scanned with the minimum image, without re-ordering.
 // The list length of slot s is kept in f[s].w (as int bits).
-__device__ __forceinline__ void nl_store(uint16_t* row, int k, int npad, int j) {
-  row[(size_t)(k >> 3) * npad * 8 + (k & 7)] = (uint16_t)j;
-}
 
 __device__ __forceinline__ int cell_of(const float4& x, float cinv, int nc) {
   const int cx = min((int)(x.x * cinv), nc - 1);
@@ -490,7 +518,7 @@ __device__ void build_order(const Group& g, const BoxCtx& b) {
     const int sl = g.tid + a * nt;
     cls[a] = 0;
     if (sl < n) {
-      const int len = __float_as_int(f[sl].w);
+      const int len = (__float_as_int(f[sl].w) & 0xfff) << 3;  // entries incl. padding
       cls[a] = 31 - min(31, (int)(((long long)len * 32) / (b.maxnb + 1)));
       atomicAdd(&cnt[4 * cls[a]], 1);
     }
@@ -535,28 +563,111 @@ __device__ __forceinline__ void st_shared_v4(uint32_t a, float4 v) {
                : "memory");
 }
 
+// List layout shared by the searches and the force pass.  Entries are uint16 slots,
+// eight to a 16-byte word.  The word's bits 12..14 of its first entry (slots stay
+// below 4096) say on which axes (x, y, z) its entries lie across a face of the box
+// from the home atom, so the force pass shifts the home atom once per word instead
+// of taking the minimum image per entry.  Along each axis only one face can be
+// crossed within R < L / 2: the upper one for an atom in the lower half of the cell
+// grid (the home atom is then shifted by +L), the lower one otherwise (-L); that
+// direction per axis is a bit of the slot's list word.  The list word of a slot (the
+// w component of its force entry) packs the word count (bits 0..11), the directions
+// (bits 12..14, x, y, z: 1 = shift by -L) and the entry count without padding (bits
+// 16..31).  Lists without codes (the minimum image per entry) carry no directions.
+__device__ __forceinline__ int list_meta(int nw, int dirs, int k) {
+  return nw | (dirs << 12) | (k << 16);
+}
+
+// One output stream of the cell search: eight entries assembled in four registers,
+// each new entry entering at the top (after eight the first sits in the low half of
+// w0), with the image code of the entries it holds.
+struct LStream {
+  uint32_t w0, w1, w2, w3;
+  int cnt, code;
+};
+
+__device__ __forceinline__ void ls_push(LStream& s, uint32_t e) {
+  s.w0 = __funnelshift_r(s.w0, s.w1, 16);
+  s.w1 = __funnelshift_r(s.w1, s.w2, 16);
+  s.w2 = __funnelshift_r(s.w2, s.w3, 16);
+  s.w3 = __funnelshift_r(s.w3, e, 16);
+}
+
+// store the assembled word as word kw of the slot's row (counted beyond the capacity)
+__device__ __forceinline__ void ls_store(LStream& s, uint4* lrow, int npad, int& kw, int maxw) {
+  if (kw < maxw)
+    lrow[(size_t)kw * npad] = make_uint4(s.w0 | ((uint32_t)s.code << 12), s.w1, s.w2, s.w3);
+  ++kw;
+  s.cnt = 0;
+}
+
+// a partial word is completed with the slot itself (masked by index in the force pass)
+__device__ __forceinline__ void ls_flush(LStream& s, uint32_t pad, uint4* lrow, int npad, int& kw,
+                                         int maxw) {
+  if (s.cnt > 0) {
+#pragma unroll 1
+    for (int u = s.cnt; u < 8; ++u) ls_push(s, pad);
+    ls_store(s, lrow, npad, kw, maxw);
+  }
+}
+
+// entries of slots t0..t1-1 within R of the (shifted) home position a, into stream s
+// under image code `code`; a code change first closes the stream's partial word
+__device__ __forceinline__ void ls_scan(LStream& s, int code, int t0, int t1, float ax, float ay,
+                                        float az, uint32_t xs_a, int sl, float rcs2, uint4* lrow,
+                                        int npad, int& kw, int maxw, int& k) {
+  if (t0 >= t1) return;
+  if (s.code != code) {
+    ls_flush(s, (uint32_t)sl, lrow, npad, kw, maxw);
+    s.code = code;
+  }
+#pragma unroll 1
+  for (int t = t0; t < t1; t += 2) {
+    const float4 xa = ld_shared4(xs_a + 16u * (uint32_t)t);
+    const float4 xb = ld_shared4(xs_a + 16u * (uint32_t)min(t + 1, t1 - 1));
+    const float dax = ax - xa.x, day = ay - xa.y, daz = az - xa.z;
+    const float dbx = ax - xb.x, dby = ay - xb.y, dbz = az - xb.z;
+    const float ra = fmaf(dax, dax, fmaf(day, day, daz * daz));
+    const float rb = fmaf(dbx, dbx, fmaf(dby, dby, dbz * dbz));
+    if (ra < rcs2 && t != sl) {
+      ls_push(s, (uint32_t)t);
+      ++k;
+      if (++s.cnt == 8) ls_store(s, lrow, npad, kw, maxw);
+    }
+    if (rb < rcs2 && t + 1 != sl && t + 1 < t1) {
+      ls_push(s, (uint32_t)(t + 1));
+      ++k;
+      if (++s.cnt == 8) ls_store(s, lrow, npad, kw, maxw);
+    }
+  }
+}
+
 // Verlet-list search over the cell-ordered box (cells of side h >= R / 2, R = rc +
-// skin).  Every lane walks the same 5 x 5 rows of cells around its home cell (z and
-// y offsets -2..2, a warp-uniform loop), and in each row only the x range of cells
-// that can hold an atom within R of its own: R^2 less the squared distance to the
-// row's y-z rectangle bounds the x extent.  A row's cells are contiguous slots in
-// cell order, cut into at most three segments where the x range wraps around the
-// box, each with its image shift applied to the home atom once.  Ranges use R
-// enlarged by 1e-5 so rounding drops no cell, and the home position is clamped into
-// [0, L] so the indices stay in range even for a state that has blown up (the box
-// then fails on its temperature); entries are accepted on r^2 < R^2.  A cell reached
-// through two images (grids of fewer than 5 cells) holds at most one image of each
-// atom within R, since L >= 2 R.  The slot's force-array word (stage_a + 16 slot)
-// stages eight entries at a time, written to the list as one 16-byte store; at the
-// end it receives (0, 0, 0, list length).  Out of line and fed only scalars and
-// shared-memory addresses, so the search has the whole register budget.
+// skin, at least 4 per axis).  Every lane walks 5 x 5 rows of cells around its home
+// cell (z and y offsets -2..2), and in each row only the x range of cells that can
+// hold an atom within R of its own: R^2 less the squared distance to the row's y-z
+// rectangle bounds the x extent.  A row's cells are contiguous slots in cell order;
+// the part of the range inside the box goes to one output stream, the part across
+// an x face (at most one side) to a second one with its image shift applied to the
+// home atom.  The rows are taken in an order that keeps rows crossing the same y and
+// z faces together (offsets that cross no face first along each axis, then blocks
+// (z inside, y inside), (z inside, y across), (z across, y inside), (z across, y
+// across)), so each stream changes its image code at most three times and few words
+// are closed early.  Ranges use R enlarged by 1e-5 so rounding drops no cell, and the
+// home position is clamped into [0, L] so the indices stay in range even for a state
+// that has blown up (the box then fails on its temperature); entries are accepted on
+// r^2 < R^2.  A cell reached through two images (grids of 4 cells) holds at most one
+// image of each atom within R, since L >= 2 R.  At the end the slot's force entry
+// receives (0, 0, 0, list word).  Out of line and fed only scalars and shared-memory
+// addresses, so the search has the whole register budget.
 template <int APT>
-__device__ __noinline__ void nl_search(uint32_t xs_a, uint32_t stage_a, uint32_t cs_a,
+__device__ __noinline__ void nl_search(uint32_t xs_a, uint32_t meta_a, uint32_t cs_a,
                                        uint32_t ovf_a, uint16_t* nl, int tid, int nt, int npad,
                                        int n, int nc, float L, float cinv, float rcs2, int maxnb) {
   const float Rs = 1.00001f * sqrtf(rcs2);
   const float Rs2 = Rs * Rs;
   const float h = L / (float)nc;
+  const int maxw = maxnb >> 3;
 #pragma unroll 1
   for (int a = 0; a < APT; ++a) {
     const int sl = tid + a * nt;
@@ -567,65 +678,118 @@ __device__ __noinline__ void nl_search(uint32_t xs_a, uint32_t stage_a, uint32_t
     xi.z = fminf(fmaxf(xi.z, 0.f), L);
     const int cx = min((int)(xi.x * cinv), nc - 1), cy = min((int)(xi.y * cinv), nc - 1);
     const int cz = min((int)(xi.z * cinv), nc - 1);
-    const uint32_t stage = stage_a + 16u * (uint32_t)sl;
+    // the face an axis can cross: upper half of the grid -> the upper face
+    const int hx = 2 * cx >= nc, hy = 2 * cy >= nc, hz = 2 * cz >= nc;
+    // offsets (of -2..2) that cross it, and the rotation putting the others first
+    const int wy = hy ? max(cy + 3 - nc, 0) : max(2 - cy, 0);
+    const int wz = hz ? max(cz + 3 - nc, 0) : max(2 - cz, 0);
+    const int ny0 = 5 - wy, nz0 = 5 - wz;
+    const int ry = hy ? 0 : wy, rz = hz ? 0 : wz;
     uint4* lrow = reinterpret_cast<uint4*>(nl) + sl;  // word w at lrow + w * npad
-    int k = 0;
+    LStream s0 = {0u, 0u, 0u, 0u, 0, 0}, s1 = {0u, 0u, 0u, 0u, 0, 1};
+    int kw = 0, k = 0;
+    int yb = 0, zb = 0, iy = 0, iz = 0;  // block (z across, y across) and offsets in it
 #pragma unroll 1
-    for (int dz = -2; dz <= 2; ++dz) {
-      const int qz = cz + dz;
+    for (int r = 0; r < 25; ++r) {
+      const int dz = (iz + rz < 5 ? iz + rz : iz + rz - 5) - 2;
+      const int dy = (iy + ry < 5 ? iy + ry : iy + ry - 5) - 2;
+      const int qz = cz + dz, qy = cy + dy;
       const float zl = (float)qz * h;
       const float ez = fmaxf(fmaxf(zl - xi.z, xi.z - (zl + h)), 0.f);
-      const int wz = qz < 0 ? qz + nc : (qz >= nc ? qz - nc : qz);
+      const int wzc = qz < 0 ? qz + nc : (qz >= nc ? qz - nc : qz);
       const float az = xi.z - (qz < 0 ? -L : (qz >= nc ? L : 0.f));
-#pragma unroll 1
-      for (int dy = -2; dy <= 2; ++dy) {
-        const int qy = cy + dy;
-        const float yl = (float)qy * h;
-        const float ey = fmaxf(fmaxf(yl - xi.y, xi.y - (yl + h)), 0.f);
-        const float rx2 = Rs2 - ez * ez - ey * ey;
-        // x cells within the radius left over (none when the row is out of range)
-        const float rx = sqrtf(fmaxf(rx2, 0.f));
-        int x0 = max((int)floorf((xi.x - rx) * cinv), cx - 2);
-        int x1 = min((int)floorf((xi.x + rx) * cinv), cx + 2);
-        if (rx2 < 0.f) x1 = x0 - 1;
-        const int wy = qy < 0 ? qy + nc : (qy >= nc ? qy - nc : qy);
-        const float ay = xi.y - (qy < 0 ? -L : (qy >= nc ? L : 0.f));
-        const uint32_t rowa = cs_a + 4u * (uint32_t)((wz * nc + wy) * nc);
-#pragma unroll 1
-        for (int sg = 0; sg < 3; ++sg) {
-          // sg 0: cells x0..-1 (image -L), 1: 0..nc-1 (none), 2: nc..x1 (image +L)
-          const int lo = sg == 0 ? x0 : (sg == 1 ? max(x0, 0) : max(x0, nc));
-          const int hi = sg == 0 ? min(x1, -1) : (sg == 1 ? min(x1, nc - 1) : x1);
-          if (lo > hi) continue;
-          const int off = sg == 0 ? nc : (sg == 1 ? 0 : -nc);
-          const float ax = xi.x - (sg == 0 ? -L : (sg == 1 ? 0.f : L));
-          int t = ld_shared_s32(rowa + 4u * (uint32_t)(lo + off));
-          const int t1 = ld_shared_s32(rowa + 4u * (uint32_t)(hi + off + 1));
-#pragma unroll 1
-          for (; t < t1; t += 2) {
-            const float4 xa = ld_shared4(xs_a + 16u * (uint32_t)t);
-            const float4 xb = ld_shared4(xs_a + 16u * (uint32_t)min(t + 1, t1 - 1));
-            const float dax = ax - xa.x, day = ay - xa.y, daz = az - xa.z;
-            const float dbx = ax - xb.x, dby = ay - xb.y, dbz = az - xb.z;
-            const float ra = fmaf(dax, dax, fmaf(day, day, daz * daz));
-            const float rb = fmaf(dbx, dbx, fmaf(dby, dby, dbz * dbz));
-            const bool pa = ra < rcs2 && t != sl;
-            const bool pb = rb < rcs2 && t + 1 != sl && t + 1 < t1;
-            if (pa) {
-              if (k < maxnb) {
-                st_shared_u16(stage + 2u * (uint32_t)(k & 7), t);
-                if ((k & 7) == 7) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
-              }
-              ++k;
-            }
-            if (pb) {
-              if (k < maxnb) {
-                st_shared_u16(stage + 2u * (uint32_t)(k & 7), t + 1);
-                if ((k & 7) == 7) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
-              }
-              ++k;
-            }
+      const float yl = (float)qy * h;
+      const float ey = fmaxf(fmaxf(yl - xi.y, xi.y - (yl + h)), 0.f);
+      const int wyc = qy < 0 ? qy + nc : (qy >= nc ? qy - nc : qy);
+      const float ay = xi.y - (qy < 0 ? -L : (qy >= nc ? L : 0.f));
+      const float rx2 = Rs2 - ez * ez - ey * ey;
+      // x cells within the radius left over (none when the row is out of range)
+      const float rx = sqrtf(fmaxf(rx2, 0.f));
+      const int x0 = max((int)floorf((xi.x - rx) * cinv), cx - 2);
+      int x1 = min((int)floorf((xi.x + rx) * cinv), cx + 2);
+      if (rx2 < 0.f) x1 = x0 - 1;
+      const uint32_t rowa = cs_a + 4u * (uint32_t)((wzc * nc + wyc) * nc);
+      const int code = (yb << 1) | (zb << 2);
+      {  // cells inside the box
+        const int lo = max(x0, 0), hi = min(x1, nc - 1);
+        if (lo <= hi)
+          ls_scan(s0, code, ld_shared_s32(rowa + 4u * (uint32_t)lo),
+                  ld_shared_s32(rowa + 4u * (uint32_t)(hi + 1)), xi.x, ay, az, xs_a, sl, rcs2,
+                  lrow, npad, kw, maxw, k);
+      }
+      {  // cells across the lower (x0 < 0) or upper (x1 >= nc) x face
+        const int lo = x0 < 0 ? x0 + nc : max(x0, nc) - nc;
+        const int hi = x0 < 0 ? min(x1, -1) + nc : x1 - nc;
+        if (lo <= hi)
+          ls_scan(s1, code | 1, ld_shared_s32(rowa + 4u * (uint32_t)lo),
+                  ld_shared_s32(rowa + 4u * (uint32_t)(hi + 1)), xi.x + (x0 < 0 ? L : -L), ay,
+                  az, xs_a, sl, rcs2, lrow, npad, kw, maxw, k);
+      }
+      // next row: the block's y offsets, then its z offsets, then the next block
+      if (++iy == (yb ? 5 : ny0)) {
+        iy = yb ? ny0 : 0;
+        if (++iz == (zb ? 5 : nz0)) {
+          if (yb == 0 && wy > 0) {
+            yb = 1;
+          } else {
+            yb = 0;
+            zb = 1;
           }
+          iz = zb ? nz0 : 0;
+          iy = yb ? ny0 : 0;
+        }
+      }
+    }
+    ls_flush(s0, (uint32_t)sl, lrow, npad, kw, maxw);
+    ls_flush(s1, (uint32_t)sl, lrow, npad, kw, maxw);
+    if (kw > maxw) {
+      atomicOr(reinterpret_cast<int*>(__cvta_shared_to_generic(ovf_a)), 1);
+      kw = maxw;
+    }
+    st_shared_v4(meta_a + 16u * (uint32_t)sl,
+                 make_float4(0.f, 0.f, 0.f,
+                             __int_as_float(list_meta(kw, hx | (hy << 1) | (hz << 2), k))));
+  }
+}
+
+// Verlet-list search without cells (small boxes): every lane scans all atoms in
+// the same order, so each position load is one broadcast to the warp, four
+// candidates at a time; minimum image per candidate, and per entry in the force
+// pass (no image codes).  Entries are staged eight at a time in the slot's force
+// entry and stored as one 16-byte word; the last word is padded with the atom's own
+// slot.  Out of line, scalars and shared-memory addresses only.
+template <int APT>
+__device__ __noinline__ void nl_search_all(uint32_t xs_a, uint32_t stage_a, uint32_t ovf_a,
+                                           uint16_t* nl, int tid, int nt, int npad, int n,
+                                           float L, float invL, float rcs2, int maxnb) {
+#pragma unroll 1
+  for (int a = 0; a < APT; ++a) {
+    const int sl = tid + a * nt;
+    if (sl >= n) break;
+    const float4 xi = ld_shared4(xs_a + 16u * (uint32_t)sl);
+    const uint32_t stage = stage_a + 16u * (uint32_t)sl;
+    uint4* lrow = reinterpret_cast<uint4*>(nl) + sl;
+    int k = 0;
+#pragma unroll 1
+    for (int j0 = 0; j0 < n; j0 += 4) {
+      float r2[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 xo = ld_shared4(xs_a + 16u * (uint32_t)min(j0 + u, n - 1));
+        const float dx = min_img(xi.x - xo.x, L, invL);
+        const float dy = min_img(xi.y - xo.y, L, invL);
+        const float dz = min_img(xi.z - xo.z, L, invL);
+        r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u;
+        if (r2[u] < rcs2 && j != sl && j < n) {
+          if (k < maxnb) {
+            st_shared_u16(stage + 2u * (uint32_t)(k & 7), j);
+            if ((k & 7) == 7) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
+          }
+          ++k;
         }
       }
     }
@@ -633,8 +797,11 @@ __device__ __noinline__ void nl_search(uint32_t xs_a, uint32_t stage_a, uint32_t
       atomicOr(reinterpret_cast<int*>(__cvta_shared_to_generic(ovf_a)), 1);
       k = maxnb;
     }
-    if ((k & 7) != 0) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);  // partial word
-    st_shared_v4(stage, make_float4(0.f, 0.f, 0.f, __int_as_float(k)));
+    if ((k & 7) != 0) {
+      for (int u = k & 7; u < 8; ++u) st_shared_u16(stage + 2u * (uint32_t)u, sl);
+      lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
+    }
+    st_shared_v4(stage, make_float4(0.f, 0.f, 0.f, __int_as_float(list_meta((k + 7) >> 3, 0, k))));
   }
 }
 
@@ -747,31 +914,9 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, long long* prof = n
     MDEOS_PHASE(5)
   } else {
     gbar(g.bar, g.nt);  // positions just wrapped by their owners
-#pragma unroll
-    for (int a = 0; a < APT; ++a) {
-      const int i = g.tid + a * g.nt;
-      if (i < n) {
-        const float4 xi = xs[i];
-        uint16_t* row = g.nl + (size_t)i * 8;
-        int k = 0;
-        for (int j = 0; j < n; ++j) {
-          const float4 xo = xs[j];
-          const float ddx = min_img(xi.x - xo.x, b.L, b.invL);
-          const float ddy = min_img(xi.y - xo.y, b.L, b.invL);
-          const float ddz = min_img(xi.z - xo.z, b.L, b.invL);
-          const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-          if (j != i && r2 < b.rcs2) {
-            if (k < b.maxnb) nl_store(row, k, g.npad, j);
-            ++k;
-          }
-        }
-        if (k > b.maxnb) {
-          atomicOr(&g.ctrl()[CTRL_OVERFLOW], 1);
-          k = b.maxnb;
-        }
-        srt[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
-      }
-    }
+    nl_search_all<APT>((uint32_t)__cvta_generic_to_shared(xs), (uint32_t)__cvta_generic_to_shared(srt),
+                       (uint32_t)__cvta_generic_to_shared(&g.ctrl()[CTRL_OVERFLOW]), g.nl, g.tid,
+                       g.nt, g.npad, n, b.L, b.invL, b.rcs2, b.maxnb);
     gbar(g.bar, g.nt);
     MDEOS_PHASE(5)
   }
@@ -1194,7 +1339,7 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
         for (int a = 0; a < APT; ++a) {
           const int i = g.tid + a * g.nt;
           if (i < n) {
-            const int cw = __float_as_int(g.f()[i].w);
+            const int cw = (int)((unsigned)__float_as_int(g.f()[i].w) >> 16);
             cand += (PATH == PATH_NLIST) ? cw
                                          : (PATH == PATH_ALLPAIRS ? n : 8 * n);
           }

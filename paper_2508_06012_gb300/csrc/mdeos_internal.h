@@ -29,12 +29,18 @@ constexpr int kMaxCellsBig = 32768;   // cells of the list build (<= 32 per axis
 constexpr int kBigSharedBytes = 4096; // shared memory of a big-box CTA (reductions only)
 
 // Cells per axis of a shared-memory box's Verlet-list build: side at least
-// R / 2 (R = rc + skin), at most 12 per axis; 0 = no cell grid (brute-force
-// search).  The search walks the 5 x 5 x 5 cells around an atom's home cell, which
+// R / 2 (R = rc + skin), at most 12 per axis; 0 = no cell grid (a scan of all
+// atoms, for boxes of at most kBruteMaxAtoms atoms, where it is the cheaper search).  The search walks the 5 x 5 x 5 cells around an atom's home cell, which
 // is valid for any such grid once L >= 2 R (a cell reached through two images holds
 // at most one image of each atom within R).
-__host__ __device__ inline int list_cells_per_axis(double L, double R) {
-  if (!(L >= 2.0 * R)) return 0;
+constexpr int kBruteMaxAtoms = 768;  // shared-memory boxes up to this size: no cell grid
+// List entries a cell-searched list may spend on padding beyond its n - 1 neighbours:
+// each of its two output streams closes at most four partial words of at most seven
+// pad entries when its image code changes.
+constexpr int kListPadSlack = 56;
+
+__host__ __device__ inline int list_cells_per_axis(double L, double R, int n) {
+  if (!(L >= 2.0 * R) || n <= kBruteMaxAtoms) return 0;
   int nc = (int)(2.0 * L / R);
   return nc < 12 ? nc : 12;
 }

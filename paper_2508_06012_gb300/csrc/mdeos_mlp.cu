@@ -303,16 +303,18 @@ __global__ void mlp_normalise(const double* Xp, float* X, int B, double m0, doub
   X[2 * b + 1] = (float)((Xp[2 * b + 1] - m1) / s1);
 }
 
-// ensemble mean and (population) standard deviation of the physical outputs
+// ensemble mean and (population) standard deviation of the physical outputs; with
+// p_asinh the networks predict asinh(P), mapped back by sinh before averaging
 __global__ void mlp_ensemble(const float* Y, int B, int E, double ym0, double ym1, double ys0,
-                             double ys1, double* mean, double* sd) {
+                             double ys1, int p_asinh, double* mean, double* sd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * 2) return;
   const int o = i % 2;
   const double m = o ? ym1 : ym0, s = o ? ys1 : ys0;
   double a = 0.0, q = 0.0;
   for (int e = 0; e < E; ++e) {
-    const double y = (double)Y[(long long)e * B * 2 + i] * s + m;
+    double y = (double)Y[(long long)e * B * 2 + i] * s + m;
+    if (o == 0 && p_asinh) y = sinh(y);
     a += y;
     q += y * y;
   }
@@ -572,6 +574,7 @@ struct mdeos_surrogate {
   mdeos_handle* h = nullptr;
   int E = 4, maxB = 0;
   double norm[8] = {0, 0, 1, 1, 0, 0, 1, 1};  // x mean(2), x std(2), y mean(2), y std(2)
+  int p_asinh = 0;  // 1: the networks learn asinh(P) (norm[4], norm[6] in those units)
   long long step = 0;
   float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr;
   __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W4b = nullptr;
@@ -767,8 +770,10 @@ static mdeos_status load_batch(mdeos_surrogate* s, const double* xp, const doubl
   if (yp) {
     t.resize(2 * (size_t)n);
     for (int b = 0; b < n; ++b)
-      for (int c = 0; c < 2; ++c)
-        t[2 * b + c] = (float)((yp[2 * b + c] - s->norm[4 + c]) / s->norm[6 + c]);
+      for (int c = 0; c < 2; ++c) {
+        const double y = (c == 0 && s->p_asinh) ? std::asinh(yp[2 * b]) : yp[2 * b + c];
+        t[2 * b + c] = (float)((y - s->norm[4 + c]) / s->norm[6 + c]);
+      }
     SCK(cudaMemcpyAsync(s->T, t.data(), t.size() * 4, cudaMemcpyHostToDevice, st));
   }
   SCK(cudaStreamSynchronize(st));  // the host vectors go out of scope
@@ -804,10 +809,12 @@ extern "C" mdeos_status mdeos_surrogate_train(mdeos_surrogate* s, const double* 
     for (int c = 0; c < 4; ++c) {
       const double* a = c < 2 ? x : y;
       const int col = c % 2;
+      const bool as = c == 2 && s->p_asinh;  // pressure learned as asinh(P)
+      auto val = [&](int i) { return as ? std::asinh(a[2 * i + col]) : a[2 * i + col]; };
       double m = 0.0, q = 0.0;
-      for (int i = 0; i < n; ++i) m += a[2 * i + col];
+      for (int i = 0; i < n; ++i) m += val(i);
       m /= n;
-      for (int i = 0; i < n; ++i) q += (a[2 * i + col] - m) * (a[2 * i + col] - m);
+      for (int i = 0; i < n; ++i) q += (val(i) - m) * (val(i) - m);
       const double sdv = std::sqrt(q / n);
       s->norm[(c < 2 ? 0 : 4) + col] = m;
       s->norm[(c < 2 ? 2 : 6) + col] = sdv > 0 ? sdv : 1.0;
@@ -889,8 +896,15 @@ static cudaError_t infer(mdeos_surrogate* s, const double* dx, int B, double* dm
   }
   if (e != cudaSuccess) return e;
   mlp_ensemble<<<nblk(2 * B), 256, 0, st>>>(s->Y, B, s->E, s->norm[4], s->norm[5], s->norm[6],
-                                            s->norm[7], dmean, dsd);
+                                            s->norm[7], s->p_asinh, dmean, dsd);
   return cudaGetLastError();
+}
+
+extern "C" mdeos_status mdeos_surrogate_set_output_transform(mdeos_surrogate* s, int32_t mode) {
+  if (!s || (mode != MDEOS_SURROGATE_P_LINEAR && mode != MDEOS_SURROGATE_P_ASINH))
+    return set_error(MDEOS_EINVAL, "bad output transform");
+  s->p_asinh = mode == MDEOS_SURROGATE_P_ASINH ? 1 : 0;
+  return MDEOS_OK;
 }
 
 extern "C" mdeos_status mdeos_surrogate_set_infer_path(mdeos_surrogate* s, int32_t path) {

@@ -147,7 +147,14 @@ def test_force_paths_agree_on_one_box(m, orc):
     fm = m.mdeos_debug_forces(_to_dev(x32), L, 1)[0].cpu().numpy()[:, :3]
     fn = m.mdeos_debug_forces(_to_dev(x32), L, 2, skin=0.4)[0].cpu().numpy()[:, :3]
     assert _force_err(fm.astype(np.float64), fa.astype(np.float64)) <= 1e-6
-    assert _force_err(fn.astype(np.float64), fa.astype(np.float64)) <= 1e-6
+    # the list path shifts the home atom to the image its build found (x +- L) where
+    # the all-pairs path takes the minimum image of each difference: the two round a
+    # difference across a face differently (u L per axis), so they agree within the
+    # FP32 bound each has against the FP64 forces
+    fn64, fa64 = fn.astype(np.float64), fa.astype(np.float64)
+    assert _force_err(fn64, fa64) <= 1e-5
+    err = np.linalg.norm(fn64 - fa64, axis=1)
+    assert (err <= 2.0 * _fp32_atom_bound(x32, L, fa64)).all()
 
 
 @pytest.mark.parametrize("n,rho,skin", [(1372, 0.9, 0.3), (2048, 0.5, 0.3), (864, 1.1, 0.2)])
