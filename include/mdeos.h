@@ -141,6 +141,11 @@ mdeos_status mdeos_create(const mdeos_config* cfg, mdeos_handle** out);
 /* Submit n host requests (copied before return) and start them on the GPU.
  * *ticket receives an id for mdeos_poll.  The whole batch runs as one
  * persistent kernel launch; per-box problems are reported in the results.
+ * Launch shape: a batch that fills the GPU packs boxes into work items of one
+ * CTA; one with no more boxes than SMs gives each box its own CTA; one with fewer
+ * boxes than half the SMs, all of at most 768 atoms, runs each box on a
+ * thread-block cluster of up to 8 CTAs (each holds the box and computes the forces
+ * of its share of the atoms).  Results do not depend on the launch shape.
  * Errors: MDEOS_EINVAL (n < 1, NULL, or a request field out of range),
  * MDEOS_ENOMEM, MDEOS_ECUDA. */
 mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs, int32_t n,
@@ -182,9 +187,9 @@ mdeos_result* mdeos_batch_device_results(mdeos_batch* b);
 mdeos_status mdeos_batch_results(mdeos_batch* b, mdeos_result* out);
 mdeos_status mdeos_batch_destroy(mdeos_batch* b);
 
-/* Describe the plan: number of work items, CTAs launched, dynamic shared
- * memory per CTA, neighbour-list scratch bytes, and a 64-bit checksum of
- * the packing (host ints/size_t written when the pointer is non-NULL). */
+/* Describe the plan: number of work items, CTAs launched (items x cluster size
+ * for a clustered batch), dynamic shared memory per CTA and neighbour-list scratch
+ * bytes (host ints/size_t written when the pointer is non-NULL). */
 mdeos_status mdeos_batch_info(const mdeos_batch* b, int32_t* n_items, int32_t* n_ctas,
                               int32_t* smem_bytes, size_t* scratch_bytes);
 
@@ -238,7 +243,9 @@ mdeos_status mdeos_submit_noalloc(const mdeos_config* cfg, const mdeos_request* 
  * reqs, `steps` MD steps each) is timed with CUDA events for every skin in
  * {0.2, 0.25, 0.3, 0.35, 0.4, 0.5} and the planner's warps per box and up to two
  * doublings of it (at most 32); the fastest shape per box whose boxes all succeed
- * is kept in the handle and used by later planning of that atom count while
+ * (the planner's own -- skin cfg.skin, else 0.3, and its warps -- unless another is
+ * faster by 2% or more: one wave's time varies by about a percent) is kept in the
+ * handle and used by later planning of that atom count while
  * cfg.skin <= 0 (the skin) and for batches that fill the GPU (the warps; a batch
  * with no more boxes than SMs runs each box in its own CTA, one atom per thread).
  * table (host double[4 * max_out], may be NULL) receives (natoms, skin, warps per
@@ -505,7 +512,24 @@ mdeos_status mdeos_surrogate_set_output_transform(mdeos_surrogate* s, int32_t mo
 mdeos_status mdeos_surrogate_infer_device(mdeos_surrogate* s, const double* d_x, int32_t n,
                                           double* d_mean, double* d_sd, void* stream);
 
-/* Gated evaluation of n requests: where sd(P) <= threshold * max(|mean P|, 1) the
+/* Misfit map of the gate (Sec. I's learned accelerators answer only where they are
+ * reliable; the members' spread does not see a region where all of them miss the
+ * same rough data, such as a phase boundary).  fit_misfit predicts the ensemble mean
+ * at n inputs x (host double[n][2] = (rho, e)) with MD answers y (host double[n][2] =
+ * (P, T)), and keeps per cell of a bins x bins grid over the inputs' range (1..1024)
+ * the RMS of |mean P - P| / max(|P|, 1); cells with fewer than min_count samples are
+ * unknown (infinite).  misfit (host out double[n]) reads the map at n inputs (outside
+ * the fitted range: infinite).  set_misfit_threshold: the gate also sends to MD every
+ * request whose cell exceeds the threshold (INFINITY, the default: the map is not
+ * used).  Errors: EINVAL (bad arguments, no map fitted), ECUDA. */
+mdeos_status mdeos_surrogate_fit_misfit(mdeos_surrogate* s, const double* x, const double* y,
+                                        int32_t n, int32_t bins, int32_t min_count);
+mdeos_status mdeos_surrogate_misfit(const mdeos_surrogate* s, const double* x, int32_t n,
+                                    double* out);
+mdeos_status mdeos_surrogate_set_misfit_threshold(mdeos_surrogate* s, double threshold);
+
+/* Gated evaluation of n requests: where sd(P) <= threshold * max(|mean P|, 1) (and
+ * the request's misfit cell is within the misfit threshold, when one is set) the
  * result is the ensemble mean (path = -2, P_se / T_se = the ensemble spread), else
  * the request runs on the MD path with natoms = md_natoms (> 0) or its own.
  * used_md (host int32[n], may be NULL) marks the MD answers.  Synchronous. */

@@ -39,6 +39,8 @@ EXPORTED = [
     "mdeos_surrogate_grads", "mdeos_surrogate_train", "mdeos_surrogate_predict",
     "mdeos_surrogate_gated_eval", "mdeos_surrogate_destroy", "mdeos_surrogate_set_infer_path",
     "mdeos_surrogate_infer_device", "mdeos_surrogate_set_output_transform",
+    "mdeos_surrogate_fit_misfit", "mdeos_surrogate_misfit",
+    "mdeos_surrogate_set_misfit_threshold",
     "mdeos_debug_gemm_bf16", "mdeos_debug_tanh",
     "mdeos_autotune",
 ]
@@ -203,6 +205,9 @@ def lib():
         L.mdeos_surrogate_destroy.argtypes = [vp]
         L.mdeos_surrogate_set_infer_path.argtypes = [vp, i32]
         L.mdeos_surrogate_set_output_transform.argtypes = [vp, i32]
+        L.mdeos_surrogate_fit_misfit.argtypes = [vp, vp, vp, i32, i32, i32]
+        L.mdeos_surrogate_misfit.argtypes = [vp, vp, i32, vp]
+        L.mdeos_surrogate_set_misfit_threshold.argtypes = [vp, d]
         L.mdeos_surrogate_infer_device.argtypes = [vp, vp, i32, vp, vp, vp]
         L.mdeos_autotune.argtypes = [vp, vp, i32, i32, vp, i32, P(i32)]
         i64 = ctypes.c_int64
@@ -621,6 +626,23 @@ class Surrogate:
     def set_output_transform(self, mode: int):
         """SURROGATE_P_LINEAR (default) or SURROGATE_P_ASINH (learn asinh(P))."""
         _check(lib().mdeos_surrogate_set_output_transform(self.s, mode))
+
+    def fit_misfit(self, x, y, bins: int = 32, min_count: int = 8):
+        """Misfit map of the gate from MD answers y (n, 2) = (P, T) at inputs x (n, 2)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        _check(lib().mdeos_surrogate_fit_misfit(self.s, _vp(x), _vp(y), len(x), bins, min_count))
+
+    def misfit(self, x):
+        """The misfit map at inputs x (n, 2): RMS relative P residual of the cell."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros(len(x))
+        _check(lib().mdeos_surrogate_misfit(self.s, _vp(x), len(x), _vp(out)))
+        return out
+
+    def set_misfit_threshold(self, threshold: float):
+        """Gate also on the misfit map (math.inf: not used)."""
+        _check(lib().mdeos_surrogate_set_misfit_threshold(self.s, float(threshold)))
 
     def set_infer_path(self, path: int):
         """SURROGATE_INFER_TC (fused tcgen05 kernel, default) or SURROGATE_INFER_MMA."""

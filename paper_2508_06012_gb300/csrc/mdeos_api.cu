@@ -24,7 +24,7 @@ cudaError_t set_batch_attributes(int max_smem);
 cudaError_t launch_eos_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int* counter,
                              mdeos_result* results, uint16_t* nl, long long nl_elems_per_cta,
                              const RunParams& rp, int grid, int smem, cudaStream_t st,
-                             int* ready);
+                             int* ready, int cluster);
 cudaError_t set_debug_attributes(int max_smem);
 cudaError_t launch_debug_lift(const BoxDesc& bd, const RunParams& rp, double T, int apt,
                               int ncell_cap, int smem, float4* x4, float4* v4, double* e_out,
@@ -276,6 +276,7 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
     p.ncell = nc > 0 ? nc * nc * nc : 1;
     const double expect = 4.18879020478639 * rs * rs * rs * r.rho;
     b.maxnb = list_capacity(c, n, r.rho, rs, cap_min);
+    if (nc == 0) b.maxnb = brute_list_capacity(n, b.maxnb);
     p.cost = steps * n * (expect * 1.0 + 8.0);
   } else {
     b.skin = 0.f;
@@ -289,7 +290,8 @@ static BoxPlan plan_box(const mdeos_request& r, const mdeos_config& c, int idx, 
   int warps = 4;
   while (warps < 32 && warps * 32 * 4 < n) warps *= 2;
   if (spread) {
-    warps = std::max(warps, std::min(32, pow2_ceil((n + 31) / 32)));
+    const int tpa = (b.path == PATH_NLIST && b.nc_cell == 0) ? brute_tpa(n) : 1;
+    warps = std::max(warps, std::min(32, pow2_ceil((n * tpa + 31) / 32)));
   } else if (tuned) {
     const auto it = tuned->find(n);
     if (it != tuned->end() && it->second.warps > warps && it->second.warps <= 32)
@@ -310,11 +312,13 @@ struct Plan {
   int smem = 0;
   long long nl_per_cta = 0;
   int grid = 0;
+  int cluster = 1;  // CTAs per box (thread-block clusters, eos_cluster_kernel); 1: none
 };
 
 static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_config& c, int nsm,
                               int smem_max, Plan& plan, bool allow_big = true,
-                              const ShapeTable* tuned = nullptr, const int* cap_min = nullptr) {
+                              const ShapeTable* tuned = nullptr, const int* cap_min = nullptr,
+                              bool allow_cluster = false) {
   plan.boxes.clear();
   plan.items.clear();
   plan.status.assign(n, MDEOS_OK);
@@ -337,6 +341,23 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
                                  cap_min ? cap_min[p.bd.out_index] : 0, true);
       p.warps = q.warps;
       p.apt = q.apt;
+    }
+  }
+  // Fewer boxes than half the SMs, all searched without cells: a thread-block
+  // cluster of up to kMaxCluster CTAs per box (the whole CTA as its group), the
+  // largest power of two that keeps every box's cluster on the GPU at once
+  plan.cluster = 1;
+  if (allow_cluster && spread && (int)bp.size() == nsmall) {
+    bool all = true;
+    for (const BoxPlan& p : bp) all = all && p.bd.path == PATH_NLIST && p.bd.nc_cell == 0;
+    int C = 1;
+    while (C < kMaxCluster && 2LL * C * nsmall <= nsm) C *= 2;
+    if (all && C > 1) {
+      plan.cluster = C;
+      for (BoxPlan& p : bp) {
+        p.warps = kCtaThreads / 32;
+        p.apt = round_apt((p.bd.natoms + kCtaThreads - 1) / kCtaThreads);
+      }
     }
   }
   // size classes by (warps, apt); inside a class, sort by cost so an item's
@@ -412,7 +433,8 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
   std::stable_sort(items.begin(), items.end(),
                    [](const ItemCost& a, const ItemCost& b) { return a.cost > b.cost; });
   for (auto& it : items) plan.items.push_back(it.wi);
-  plan.grid = std::max(1, std::min(nsm, (int)plan.items.size()));
+  plan.grid = plan.cluster > 1 ? (int)plan.items.size() * plan.cluster
+                               : std::max(1, std::min(nsm, (int)plan.items.size()));
   return MDEOS_OK;
 }
 
@@ -700,7 +722,8 @@ extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs,
   std::lock_guard<std::mutex> lock(h->mu);
   CK(cudaSetDevice(h->device));
   Plan plan;
-  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin);
+  mdeos_status st =
+      make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin, nullptr, true);
   if (st != MDEOS_OK) return st;
   assign_warm(h, plan, reqs);
   TicketState t;
@@ -753,7 +776,7 @@ extern "C" mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs,
     CK(cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream));
     e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni, (int*)(d + off_cnt),
                          (mdeos_result*)(d + off_res), h->d_nl, plan.nl_per_cta, h->rp, plan.grid,
-                         plan.smem, h->stream, nullptr);
+                         plan.smem, h->stream, nullptr, plan.cluster);
     if (e != cudaSuccess) return cuda_fail(e, "eos_batch_kernel launch");
     h->launches += 1;
     CK(cudaMemcpyAsync(t.h_out.p, d + off_res, (size_t)n * sizeof(mdeos_result),
@@ -791,7 +814,7 @@ static mdeos_status run_plan_sync(mdeos_handle* h, const Plan& plan, int n, mdeo
   if (e == cudaSuccess)
     e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni, (int*)(d + off_cnt),
                          (mdeos_result*)(d + off_res), h->d_nl, plan.nl_per_cta, h->rp, plan.grid,
-                         plan.smem, h->stream, nullptr);
+                         plan.smem, h->stream, nullptr, plan.cluster);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, d + off_res, (size_t)n * sizeof(mdeos_result),
                         cudaMemcpyDeviceToHost, h->stream);
@@ -825,7 +848,7 @@ static void rerun_overflowed(mdeos_handle* h, TicketState& t, mdeos_result* res)
     }
     Plan plan;
     if (make_plan(sub.data(), m, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin,
-                  cmin.data()) != MDEOS_OK)
+                  cmin.data(), true) != MDEOS_OK)
       return;
     for (BoxDesc& bd : plan.boxes) {  // same warm slot and stored box side as the first plan
       const BoxDesc& first = t.planned[idx[bd.out_index]];
@@ -909,7 +932,7 @@ extern "C" mdeos_status mdeos_batch_create(mdeos_handle* h, const mdeos_request*
   b->h = h;
   b->n = n;
   mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, b->plan, true,
-                              &h->tuned_skin);
+                              &h->tuned_skin, nullptr, true);
   if (st != MDEOS_OK) {
     delete b;
     return st;
@@ -952,7 +975,7 @@ extern "C" mdeos_status mdeos_batch_create(mdeos_handle* h, const mdeos_request*
   cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
   if (ni > 0)
     launch_eos_batch(b->d_boxes, b->d_items, (int)ni, b->d_counter, b->d_results, b->d_nl,
-                     p.nl_per_cta, h->rp, p.grid, p.smem, cs, nullptr);
+                     p.nl_per_cta, h->rp, p.grid, p.smem, cs, nullptr, p.cluster);
   e = cudaStreamEndCapture(cs, &b->graph);
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) {
@@ -1040,7 +1063,7 @@ static mdeos_status time_plan(mdeos_handle* h, const Plan& plan, int n, float* m
   if (e == cudaSuccess)
     e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni, (int*)(d + off_cnt),
                          (mdeos_result*)(d + off_res), h->d_nl, plan.nl_per_cta, h->rp, plan.grid,
-                         plan.smem, h->stream, nullptr);
+                         plan.smem, h->stream, nullptr, plan.cluster);
   if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
   std::vector<mdeos_result> res(n);
   if (e == cudaSuccess)
@@ -1075,14 +1098,20 @@ extern "C" mdeos_status mdeos_autotune(mdeos_handle* h, const mdeos_request* req
     cls[reqs[i].natoms].push_back(i);
     warps0[reqs[i].natoms] = p.big ? 0 : p.warps;
   }
-  const float cand[] = {0.2f, 0.25f, 0.3f, 0.35f, 0.4f, 0.5f};
+  // the planner's own skin: the configured one, else 0.3
+  const float skin0 = h->cfg.skin > 0 ? (float)h->cfg.skin : 0.3f;
+  std::vector<float> cand = {0.2f, 0.25f, 0.3f, 0.35f, 0.4f, 0.5f};
+  if (std::find(cand.begin(), cand.end(), skin0) == cand.end()) cand.push_back(skin0);
+  // a shape replaces the planner's own (the configured skin, its warps per box) only
+  // when it is faster by this margin: one wave's timing varies by about a percent
+  const float kMargin = 0.98f;
   int k_out = 0;
   for (const auto& kv : cls) {
     // warps per box: the planner's choice and up to two doublings (at most 32)
     std::vector<int> wopt;
     for (int w = warps0[kv.first]; w > 0 && w <= 32 && wopt.size() < 3; w *= 2) wopt.push_back(w);
     if (wopt.empty()) wopt.push_back(0);  // global-memory boxes: one CTA each
-    float best = 0.f;
+    float best = 0.f, base = 0.f;
     LaunchShape best_shape;
     for (int w : wopt) {
       // one full wave of the GPU: nSM CTAs, each with as many boxes as an item holds
@@ -1111,12 +1140,18 @@ extern "C" mdeos_status mdeos_autotune(mdeos_handle* h, const mdeos_request* req
         bool ok = true;
         for (int v : status) ok = ok && v == MDEOS_OK;
         const float per_box = ms / count;
+        if (ok && w == wopt[0] && sk == skin0) base = per_box;
         if (ok && (best_shape.skin == 0.f || per_box < best)) {
           best = per_box;
           best_shape.skin = sk;
           best_shape.warps = w;
         }
       }
+    }
+    if (base > 0.f && best > kMargin * base) {  // no shape clearly faster: the planner's
+      best = base;
+      best_shape.skin = skin0;
+      best_shape.warps = wopt[0];
     }
     if (best_shape.skin > 0.f) {
       h->tuned_skin[kv.first] = best_shape;
@@ -1229,7 +1264,8 @@ mdeos_status eval_into_device(mdeos_handle* h, const mdeos_request* reqs, int n,
   CK(cudaSetDevice(h->device));
   CK(cudaStreamSynchronize(h->stream));
   Plan plan;
-  mdeos_status st = make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin);
+  mdeos_status st =
+      make_plan(reqs, n, h->cfg, h->nsm, h->smem_max, plan, true, &h->tuned_skin, nullptr, true);
   if (st != MDEOS_OK) return st;
   assign_warm(h, plan, reqs);
   const size_t nb = plan.boxes.size(), ni = plan.items.size();
@@ -1275,7 +1311,7 @@ mdeos_status eval_into_device(mdeos_handle* h, const mdeos_request* reqs, int n,
   CK(cudaMemsetAsync(d + off_cnt, 0, sizeof(int), h->stream));
   cudaError_t e = launch_eos_batch((BoxDesc*)d, (WorkItem*)(d + off_items), (int)ni,
                                    (int*)(d + off_cnt), d_results, h->d_nl, plan.nl_per_cta, h->rp,
-                                   plan.grid, plan.smem, h->stream, nullptr);
+                                   plan.grid, plan.smem, h->stream, nullptr, plan.cluster);
   if (e != cudaSuccess) return cuda_fail(e, "eos_batch_kernel launch");
   h->launches += 1;
   return MDEOS_OK;
@@ -1355,6 +1391,7 @@ static mdeos_status debug_setup(const mdeos_config* cfg, int n, double L, int pa
     bd.nc_cell = nc;
     ncell = nc > 0 ? nc * nc * nc : 1;
     bd.maxnb = std::max(8, ((n - 1 + kListPadSlack) + 7) & ~7);  // no overflow in tests
+    if (nc == 0) bd.maxnb = brute_list_capacity(n, n);
     nl_bytes = (size_t)bd.maxnb * kCtaThreads * apt * sizeof(uint16_t);
   }
   smem = group_smem_bytes(32, apt, ncell);
@@ -1470,6 +1507,7 @@ extern "C" mdeos_status mdeos_debug_force_bench(const mdeos_config* cfg, const f
   const double expect_cap = 4.18879020478639 * rs * rs * rs * std::max(n / (L * L * L), 0.9);
   bd.maxnb = (std::min((int)std::ceil(1.3 * expect_cap + 32.0) + kListPadSlack,
                       n - 1 + kListPadSlack) + 7) & ~7;
+  if (bd.nc_cell == 0) bd.maxnb = brute_list_capacity(n, bd.maxnb);
   const long long nl_elems = (long long)bd.maxnb * kCtaThreads * apt;
   cudaStream_t s = (cudaStream_t)stream;
   uint16_t* nl = nullptr;

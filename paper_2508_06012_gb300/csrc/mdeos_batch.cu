@@ -55,6 +55,41 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   }
 }
 
+// Cluster form for batches too small to fill the GPU: one box per thread-block
+// cluster of csize CTAs (cluster c runs item c, one box, the whole CTA as its group).
+// Every CTA holds the box and advances it alike; each computes the forces and lists
+// of its share of the atoms and sends the forces to the others (run_box with
+// Group::csize > 1).  All CTAs of a cluster take the same path through the box, so
+// they meet at the same cluster barriers; the last one below keeps every CTA alive
+// until no other can still store into its shared memory.
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    eos_cluster_kernel(const BoxDesc* __restrict__ boxes, const WorkItem* __restrict__ items,
+                       int nitems, mdeos_result* __restrict__ results, uint16_t* nl_scratch,
+                       long long nl_elems_per_cta, RunParams rp, int* ready) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int csize = cluster_size(), crank = cluster_rank();
+  const int it = blockIdx.x / csize;
+  uint16_t* nl_cta = nl_scratch + (long long)blockIdx.x * nl_elems_per_cta;
+  if (it < nitems) {
+    const WorkItem wi = items[it];
+    const BoxDesc& bd = boxes[wi.box[0]];
+    Group g = make_group(smem, threadIdx.x, wi.warps_per_box, wi.apt, wi.ncell_cap, 1, nl_cta);
+    g.crank = crank;
+    g.csize = csize;
+    mdeos_result* out = results + bd.out_index;
+    switch (wi.apt) {
+      case 1: run_box_path<1>(g, bd, rp, out); break;
+      case 2: run_box_path<2>(g, bd, rp, out); break;
+      default: run_box_path<4>(g, bd, rp, out); break;
+    }
+    if (ready != nullptr && crank == 0 && g.tid == 0) {
+      __threadfence_system();
+      reinterpret_cast<volatile int*>(ready)[bd.out_index] = 1;
+    }
+  }
+  cluster_sync();
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -173,6 +208,9 @@ cudaError_t set_batch_attributes(int max_smem) {
   cudaError_t e = cudaFuncSetAttribute(eos_serve_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(eos_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(eos_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               max_smem);
 }
@@ -185,7 +223,24 @@ cudaError_t launch_eos_serve(const ServeQueue& q, const RunParams& rp, uint16_t*
 
 cudaError_t launch_eos_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int* counter,
                              mdeos_result* results, uint16_t* nl, long long nl_elems_per_cta,
-                             const RunParams& rp, int grid, int smem, cudaStream_t st, int* ready) {
+                             const RunParams& rp, int grid, int smem, cudaStream_t st, int* ready,
+                             int cluster) {
+  if (cluster > 1) {  // grid = nitems * cluster CTAs in clusters of `cluster`
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid, 1, 1);
+    lc.blockDim = dim3(kCtaThreads, 1, 1);
+    lc.dynamicSmemBytes = (size_t)smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, eos_cluster_kernel, boxes, items, nitems, results, nl,
+                              nl_elems_per_cta, rp, ready);
+  }
   eos_batch_kernel<<<grid, kCtaThreads, smem, st>>>(boxes, items, nitems, counter, results, nl,
                                                     nl_elems_per_cta, rp, ready);
   return cudaGetLastError();

@@ -284,7 +284,7 @@ __device__ void debug_force_bench_body(const Group& g, const BoxDesc& bd, const 
   long long cand[1] = {0};
   for (int a = 0; a < APT; ++a) {
     const int i = g.tid + a * g.nt;
-    if (i < b.n) cand[0] += (long long)((unsigned)__float_as_int(g.f()[i].w) >> 16) * 4294967296LL;
+    if (i < b.n) cand[0] += (long long)list_entries(__float_as_int(g.f()[i].w), b.tpa) * 4294967296LL;
   }
   double ctot[1];
   group_sum<1>(g, cand, ctot);

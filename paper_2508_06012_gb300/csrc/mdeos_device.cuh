@@ -34,6 +34,47 @@ __device__ __forceinline__ void gbar(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// Thread-block clusters: rank and size, the cluster-wide barrier (every thread of
+// every CTA; release/acquire, so shared-memory stores into other CTAs before it are
+// visible after it), and stores into another CTA's shared memory (mapa maps a local
+// shared address to the same offset in CTA `rank`).
+__device__ __forceinline__ int cluster_rank() {
+  int r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ int cluster_size() {
+  int r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_cluster_v4(uint32_t a, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_s64(uint32_t a, long long v) {
+  asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_s32(uint32_t a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
 // barrier that also ORs a predicate over the participating threads
 __device__ __forceinline__ bool gbar_or(int id, int n, bool p) {
   int r;
@@ -106,18 +147,18 @@ enum { CTRL_STATUS = 0, CTRL_OVERFLOW = 1, CTRL_WARM = 2 };
 struct Group {
   unsigned char* base;
   uint16_t* nl;  // neighbour scratch: word (kb, i) at ((kb * npad + i) * 8) uint16 units
-  int tid, nt, bar, npad, nwarps, off_red;
+  int tid, nt, bar, npad, nwarps, off_red, off_clu;
+  // thread-block cluster sharing the box (csize 1: none): every CTA holds the whole
+  // box and advances it alike; CTA crank computes the forces and lists of its share
+  // of the atoms and sends them to the others
+  int crank, csize;
   __device__ __forceinline__ int warp() const { return tid >> 5; }
   __device__ __forceinline__ int lane() const { return tid & 31; }
   __device__ __forceinline__ float4* x() const { return reinterpret_cast<float4*>(base); }
   __device__ __forceinline__ float4* f() const { return reinterpret_cast<float4*>(base) + npad; }
   __device__ __forceinline__ float4* v() const { return reinterpret_cast<float4*>(base) + 2 * npad; }
-  // force-pass order: slot processed at position tid + a * nt (0xffff: none)
-  __device__ __forceinline__ uint16_t* order() const {
-    return reinterpret_cast<uint16_t*>(base + (size_t)48 * npad);
-  }
   __device__ __forceinline__ int* cell() const {
-    return reinterpret_cast<int*>(base + (size_t)50 * npad);
+    return reinterpret_cast<int*>(base + (size_t)48 * npad);
   }
   __device__ __forceinline__ long long* red() const {
     return reinterpret_cast<long long*>(base + off_red);
@@ -128,6 +169,9 @@ struct Group {
   __device__ __forceinline__ double* acc() const { return bc() + 8; }
   __device__ __forceinline__ int* bcnt() const { return reinterpret_cast<int*>(acc() + kAccDoubles); }
   __device__ __forceinline__ int* ctrl() const { return bcnt() + kMaxSeBlocks; }
+  __device__ __forceinline__ long long* clu() const {
+    return reinterpret_cast<long long*>(base + off_clu);
+  }
 };
 
 __device__ inline Group make_group(unsigned char* base, int tid, int warps, int apt, int ncell_cap,
@@ -141,6 +185,9 @@ __device__ inline Group make_group(unsigned char* base, int tid, int warps, int 
   g.npad = warps * 32 * apt;
   g.nwarps = warps;
   g.off_red = group_red_offset(warps, apt, ncell_cap);
+  g.off_clu = group_cluster_offset(warps, apt, ncell_cap);
+  g.crank = 0;
+  g.csize = 1;
   return g;
 }
 
@@ -176,6 +223,7 @@ __device__ __forceinline__ long long warp_partials_ll(const long long* red, int 
 // Per-box constants in registers.
 struct BoxCtx {
   int n, maxnb, nc;
+  int tpa;  // threads per atom of the list passes (brute_tpa for lists without cells)
   float L, invL, half_skin, rcs2, cinv;
 };
 
@@ -184,6 +232,7 @@ __device__ inline BoxCtx make_ctx(const BoxDesc& bd, const RunParams& rp) {
   b.n = bd.natoms;
   b.maxnb = bd.maxnb;
   b.nc = bd.nc_cell;
+  b.tpa = (bd.path == PATH_NLIST && bd.nc_cell == 0) ? brute_tpa(bd.natoms) : 1;
   b.L = (float)bd.L;
   b.invL = (float)(1.0 / bd.L);
   b.half_skin = 0.5f * bd.skin;
@@ -305,6 +354,32 @@ __device__ __forceinline__ int ld_shared_u16(uint32_t a) {
   return (int)v;
 }
 
+// List words of boxes searched without cells: `tpa` sub-lists per atom (sub-list p
+// holds the neighbours among slots p, p + tpa, p + 2 tpa, ...: slots of these boxes
+// keep their lattice order, so interleaved slots give every sub-list about the same
+// share of an atom's neighbours), sub-list p of slot i being unit u = i tpa + p with
+// word kb at kb * npad * tpa + u.
+// The slot's list word packs the entry counts of its sub-lists (8 bits each for 4,
+// 16 bits each for 2).
+__device__ __forceinline__ int sub_entries(int meta, int tpa, int p) {
+  return tpa == 4 ? (meta >> (8 * p)) & 0xff : (tpa == 2 ? (meta >> (16 * p)) & 0xffff
+                                                         : (int)((unsigned)meta >> 16));
+}
+
+// list entries of a slot (without padding), from its list word
+__device__ __forceinline__ int list_entries(int meta, int tpa) {
+  if (tpa == 1) return (int)((unsigned)meta >> 16);
+  int k = 0;
+  for (int p = 0; p < tpa; ++p) k += sub_entries(meta, tpa, p);
+  return k;
+}
+
+// lanes of the tpa-group of the calling lane (tpa consecutive lanes, one atom)
+__device__ __forceinline__ unsigned tpa_mask(int tpa) {
+  const int lane = threadIdx.x & 31;
+  return (tpa >= 32 ? 0xffffffffu : ((1u << tpa) - 1u)) << (lane & ~(tpa - 1));
+}
+
 // per-thread partial sums of one force pass: energy and virial in fxp units
 // (already halved: each pair appears in two atoms' lists), wrapping integer adds
 struct FSums {
@@ -320,22 +395,21 @@ struct FSums {
 // caller's step state is saved once per call, and positions are read with
 // explicit shared-memory loads.
 //
-// ord_a (shared address, 0 = none): the slot to take at position tid + a * nt, from
-// the last list build (slots by list length, longest first, dealt over the rows in a
-// snake), so the lanes of a warp walk lists of similar length and the warps of the
-// group carry similar totals.  Only force-only passes use it: which thread computes
-// an atom then changes no result.
-template <int APT, int PATH, bool EN, bool VIR, bool CNT>
+// CODED (Verlet path): lists with image codes (cell search) or with the minimum image
+// per entry (search without cells); separate instances keep each loop's registers.
+template <int APT, int PATH, bool EN, bool VIR, bool CNT, bool CODED>
 __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16_t* nl, int tid,
-                                         int nt, int npad, int n, bool coded, float L, float invL,
-                                         LJ c, uint32_t ord_a) {
+                                         int nt, int npad, int n, int tpa, int u0, int u1,
+                                         float L, float invL, LJ c) {
   unsigned long long es = 0, ws[6] = {0, 0, 0, 0, 0, 0};
   int np = 0, bad = 0;
+  // units u0 .. u1 - 1 (u0 a multiple of tpa); unit u = i tpa + p: sub-list p of atom
+  // i (tpa = 1 but for lists without cells)
+  const int sh = tpa == 4 ? 2 : (tpa == 2 ? 1 : 0);
 #pragma unroll 1
-  for (int a = 0; a < APT; ++a) {
-    int i = tid + a * nt;
-    if (ord_a != 0u) i = ld_shared_u16(ord_a + 2u * (uint32_t)i);
-    if (i < n) {
+  for (int u = u0 + tid; u < u1; u += nt) {
+    const int i = u >> sh, p = u & (tpa - 1);
+    {
       const float4 xi = ld_shared4(xs_a + 16u * (uint32_t)i);
       const float cw = fs[i].w;  // packed list lengths (Verlet path), kept across steps
       float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -353,18 +427,19 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
         // without codes (boxes searched without cells) take the minimum image per
         // entry.  The build pads partial words with the atom's own slot, so every
         // word is processed whole and the self entries are masked by index.
-        const uint4* p = reinterpret_cast<const uint4*>(nl) + i;
+        const uint4* lp = reinterpret_cast<const uint4*>(nl) + u;
+        const size_t wst = (size_t)npad * tpa;  // words between word kb and kb + 1
         const int meta = __float_as_int(cw);
-        const int nw = meta & 0xfff;
-        uint4 q = nw > 0 ? __ldcg(p) : make_uint4(0u, 0u, 0u, 0u);
-        if (coded) {
+        const int nw = CODED ? meta & 0xfff : (sub_entries(meta, tpa, p) + 7) >> 3;
+        uint4 q = nw > 0 ? __ldcg(lp) : make_uint4(0u, 0u, 0u, 0u);
+        if (CODED) {
           const float xa = xi.x + ((meta & 0x1000) ? -L : L);
           const float ya = xi.y + ((meta & 0x2000) ? -L : L);
           const float za = xi.z + ((meta & 0x4000) ? -L : L);
 #pragma unroll 1
           for (int kb = 0; kb < nw; ++kb) {
             const uint4 cur = q;
-            if (kb + 1 < nw) q = __ldcg(p + (size_t)(kb + 1) * npad);
+            if (kb + 1 < nw) q = __ldcg(lp + (size_t)(kb + 1) * wst);
             const float hx = (cur.x & 0x1000u) ? xa : xi.x;
             const float hy = (cur.x & 0x2000u) ? ya : xi.y;
             const float hz = (cur.x & 0x4000u) ? za : xi.z;
@@ -385,7 +460,7 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
 #pragma unroll 1
           for (int kb = 0; kb < nw; ++kb) {
             const uint4 cur = q;
-            if (kb + 1 < nw) q = __ldcg(p + (size_t)(kb + 1) * npad);
+            if (kb + 1 < nw) q = __ldcg(lp + (size_t)(kb + 1) * wst);
             const int j0 = (int)(cur.x & 0xffffu), j1 = (int)(cur.x >> 16);
             const int j2 = (int)(cur.y & 0xffffu), j3 = (int)(cur.y >> 16);
             const int j4 = (int)(cur.z & 0xffffu), j5 = (int)(cur.z >> 16);
@@ -426,7 +501,18 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
           }
         }
       }
-      fs[i] = make_float4(fx, fy, fz, cw);
+      if (tpa > 1) {  // the partial forces of the atom's units, in a fixed order
+        const unsigned m = tpa_mask(tpa);
+        fx += __shfl_xor_sync(m, fx, 1);
+        fy += __shfl_xor_sync(m, fy, 1);
+        fz += __shfl_xor_sync(m, fz, 1);
+        if (tpa > 2) {
+          fx += __shfl_xor_sync(m, fx, 2);
+          fy += __shfl_xor_sync(m, fy, 2);
+          fz += __shfl_xor_sync(m, fz, 2);
+        }
+      }
+      if (p == 0) fs[i] = make_float4(fx, fy, fz, cw);
       if (EN) {
         es += (unsigned long long)fxp(0.5f * e);
         bad |= !(fabsf(e) < 1e9f);
@@ -449,19 +535,81 @@ struct ForceAcc {
   int np = 0, bad = 0;
 };
 
+// Cluster form of a force pass's end: the sums of this CTA's threads (exact), sent
+// with the forces of its own atoms (a0 .. a1 - 1) to every CTA of the cluster; after
+// the cluster barrier thread 0 of every CTA holds the cluster's sums (added over the
+// ranks in order: the same integers everywhere) and the other threads none.
+static __device__ void cluster_exchange(const Group& g, FSums& r, int a0, int a1) {
+  long long q[9] = {(long long)r.e,  (long long)r.w0, (long long)r.w1,
+                    (long long)r.w2, (long long)r.w3, (long long)r.w4,
+                    (long long)r.w5, (long long)r.np, (long long)r.bad};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) q[k] = warp_sum_ll(q[k]);
+  long long* red = g.red();
+  if (g.lane() == 0)
+    for (int k = 0; k < 9; ++k) red[g.warp() * kRedSlots + k] = q[k];
+  gbar(g.bar, g.nt);
+  const uint32_t f_a = (uint32_t)__cvta_generic_to_shared(g.f());
+  for (int i = a0 + g.tid; i < a1; i += g.nt) {
+    const float4 fi = g.f()[i];
+    for (int rk = 0; rk < g.csize; ++rk)
+      if (rk != g.crank) st_cluster_v4(cluster_map(f_a + 16u * (uint32_t)i, rk), fi);
+  }
+  if (g.tid == 0) {
+    long long t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < g.nwarps; ++w)
+      for (int k = 0; k < 9; ++k) t[k] += red[w * kRedSlots + k];
+    const uint32_t c_a = (uint32_t)__cvta_generic_to_shared(g.clu() + g.crank * kRedSlots);
+    for (int rk = 0; rk < g.csize; ++rk)
+      for (int k = 0; k < 9; ++k) st_cluster_s64(cluster_map(c_a + 8u * k, rk), t[k]);
+  }
+  cluster_sync();
+  FSums z = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0, 0};
+  if (g.tid == 0) {
+    long long t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int rk = 0; rk < g.csize; ++rk)
+      for (int k = 0; k < 9; ++k) t[k] += g.clu()[rk * kRedSlots + k];
+    z.e = (unsigned long long)t[0];
+    z.w0 = (unsigned long long)t[1];
+    z.w1 = (unsigned long long)t[2];
+    z.w2 = (unsigned long long)t[3];
+    z.w3 = (unsigned long long)t[4];
+    z.w4 = (unsigned long long)t[5];
+    z.w5 = (unsigned long long)t[6];
+    z.np = (int)t[7];
+    z.bad = t[8] != 0;
+  }
+  r = z;
+}
+
+// the atoms a CTA of the cluster computes (all of them without a cluster)
+__device__ __forceinline__ void own_atoms(const Group& g, int n, int& a0, int& a1) {
+  const int A = (n + g.csize - 1) / g.csize;
+  a0 = min(n, g.crank * A);
+  a1 = min(n, a0 + A);
+}
+
 template <int APT, int PATH, bool EN, bool VIR, bool CNT>
 __device__ __forceinline__ void compute_forces(const Group& g, const BoxCtx& b, const RunParams& rp,
                                                ForceAcc& acc) {
   const uint32_t xs_a = (uint32_t)__cvta_generic_to_shared(g.x());
-  // the length order only where no sum depends on which thread takes which atom
-  const uint32_t ord_a = (PATH == PATH_NLIST && !EN && !VIR && !CNT)
-                             ? (uint32_t)__cvta_generic_to_shared(g.order())
-                             : 0u;
-  const FSums r = force_pass<APT, PATH, EN, VIR, CNT>(xs_a, g.f(), g.nl, g.tid, g.nt, g.npad, b.n,
-                                                      b.nc > 0, b.L, b.invL, make_lj(rp), ord_a);
-  // in the length order a thread's forces belong to other threads' atoms: every
-  // force is written before any thread reads its own atoms' forces
-  if (ord_a != 0u) gbar(g.bar, g.nt);
+  int a0, a1;
+  own_atoms(g, b.n, a0, a1);
+  // before another CTA's forces land here, every CTA has read its forces of the
+  // last pass (the half kicks)
+  if (g.csize > 1) cluster_sync();
+  FSums r =
+      (PATH != PATH_NLIST || b.nc > 0)
+          ? force_pass<APT, PATH, EN, VIR, CNT, true>(xs_a, g.f(), g.nl, g.tid, g.nt, g.npad, b.n,
+                                                      b.tpa, a0 * b.tpa, a1 * b.tpa, b.L, b.invL,
+                                                      make_lj(rp))
+          : force_pass<APT, PATH, EN, VIR, CNT, false>(xs_a, g.f(), g.nl, g.tid, g.nt, g.npad,
+                                                       b.n, b.tpa, a0 * b.tpa, a1 * b.tpa, b.L,
+                                                       b.invL, make_lj(rp));
+  // with several threads per atom an atom's force is written by the first thread of
+  // its group, not by the thread that owns the atom in the step
+  if (b.tpa > 1 || g.csize > 1) gbar(g.bar, g.nt);
+  if (g.csize > 1) cluster_exchange(g, r, a0, a1);
   if (EN) acc.e += r.e;
   if (VIR) {
     acc.w[0] += r.w0;
@@ -496,59 +644,6 @@ __device__ __forceinline__ int cell_of(const float4& x, float cinv, int nc) {
   const int cy = min((int)(x.y * cinv), nc - 1);
   const int cz = min((int)(x.z * cinv), nc - 1);
   return (cz * nc + cy) * nc + cx;
-}
-
-// Force-pass order after a list build: slots counting-sorted by list length into 32
-// classes (longest first), rank r dealt to position r in even rows of nt and mirrored
-// in odd rows (a snake), so each thread's APT atoms mix long and short lists.  The
-// class counters live in the x components of the force array (dead until the next
-// force pass; the lengths sit in its w components).  Order within a class follows
-// the shared-memory atomics: the order is used only where that changes no result.
-template <int APT>
-__device__ void build_order(const Group& g, const BoxCtx& b) {
-  const int n = b.n, nt = g.nt;
-  float4* f = g.f();
-  uint16_t* ord = g.order();
-  int* cnt = reinterpret_cast<int*>(f);  // class k counter at int index 4 k (f[k].x)
-  if (g.tid < 32) cnt[4 * g.tid] = 0;
-  gbar(g.bar, g.nt);
-  int cls[APT];
-#pragma unroll
-  for (int a = 0; a < APT; ++a) {
-    const int sl = g.tid + a * nt;
-    cls[a] = 0;
-    if (sl < n) {
-      const int len = (__float_as_int(f[sl].w) & 0xfff) << 3;  // entries incl. padding
-      cls[a] = 31 - min(31, (int)(((long long)len * 32) / (b.maxnb + 1)));
-      atomicAdd(&cnt[4 * cls[a]], 1);
-    }
-  }
-  gbar(g.bar, g.nt);
-  if (g.warp() == 0) {  // exclusive scan over the 32 classes, one per lane
-    const int lane = g.lane();
-    const int c0 = cnt[4 * lane];
-    int incl = c0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    cnt[4 * lane] = incl - c0;
-  }
-  gbar(g.bar, g.nt);
-#pragma unroll
-  for (int a = 0; a < APT; ++a) {
-    const int p = g.tid + a * nt;
-    const int q = (a & 1) ? a * nt + (nt - 1 - g.tid) : p;  // rank taken at position p
-    if (q >= n) ord[p] = 0xffff;
-    const int sl = p;
-    if (sl < n) {
-      const int r = atomicAdd(&cnt[4 * cls[a]], 1);
-      const int ra = r / nt, rt = r - ra * nt;
-      ord[(ra & 1) ? ra * nt + (nt - 1 - rt) : r] = (uint16_t)sl;
-    }
-  }
-  gbar(g.bar, g.nt);
 }
 
 __device__ __forceinline__ int ld_shared_s32(uint32_t a) {
@@ -752,56 +847,68 @@ __device__ __noinline__ void nl_search(uint32_t xs_a, uint32_t meta_a, uint32_t 
   }
 }
 
-// Verlet-list search without cells (small boxes): every lane scans all atoms in
-// the same order, so each position load is one broadcast to the warp, four
-// candidates at a time; minimum image per candidate, and per entry in the force
-// pass (no image codes).  Entries are staged eight at a time in the slot's force
-// entry and stored as one 16-byte word; the last word is padded with the atom's own
-// slot.  Out of line, scalars and shared-memory addresses only.
-template <int APT>
-__device__ __noinline__ void nl_search_all(uint32_t xs_a, uint32_t stage_a, uint32_t ovf_a,
-                                           uint16_t* nl, int tid, int nt, int npad, int n,
-                                           float L, float invL, float rcs2, int maxnb) {
+// Verlet-list search without cells (small boxes): unit u = i tpa + p scans the
+// slots p, p + tpa, ... with the minimum image; the lanes of a warp with the same p
+// load the same position (a broadcast), four candidates at a time.  The
+// minimum image is taken again per entry in the force pass (no image codes).
+// Entries are assembled eight at a time in registers and stored as one 16-byte
+// word; the last word is padded with the atom's own slot.  Out of line, scalars and
+// shared-memory addresses only.
+static __device__ __noinline__ void nl_search_all(uint32_t xs_a, uint32_t meta_a, uint32_t ovf_a,
+                                                  uint16_t* nl, int tid, int nt, int npad, int n,
+                                                  int tpa, int u0, int u1, float L, float invL,
+                                                  float rcs2, int maxnb) {
+  const int maxw = (maxnb / tpa) >> 3;
+  const size_t wstride = (size_t)npad * tpa;  // words between word kb and kb + 1
 #pragma unroll 1
-  for (int a = 0; a < APT; ++a) {
-    const int sl = tid + a * nt;
-    if (sl >= n) break;
-    const float4 xi = ld_shared4(xs_a + 16u * (uint32_t)sl);
-    const uint32_t stage = stage_a + 16u * (uint32_t)sl;
-    uint4* lrow = reinterpret_cast<uint4*>(nl) + sl;
-    int k = 0;
+  for (int u = u0 + tid; u < u1; u += nt) {
+    const int i = u / tpa, p = u - i * tpa;
+    const int jlast = n - 1 - (n - 1 - p) % tpa;  // the last slot of this sub-list's share
+    const float4 xi = ld_shared4(xs_a + 16u * (uint32_t)i);
+    uint4* lrow = reinterpret_cast<uint4*>(nl) + u;
+    LStream st = {0u, 0u, 0u, 0u, 0, 0};
+    int k = 0, kw = 0;
 #pragma unroll 1
-    for (int j0 = 0; j0 < n; j0 += 4) {
+    for (int jb = p; jb < n; jb += 4 * tpa) {
       float r2[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4 xo = ld_shared4(xs_a + 16u * (uint32_t)min(j0 + u, n - 1));
+      for (int q = 0; q < 4; ++q) {
+        const float4 xo = ld_shared4(xs_a + 16u * (uint32_t)min(jb + q * tpa, jlast));
         const float dx = min_img(xi.x - xo.x, L, invL);
         const float dy = min_img(xi.y - xo.y, L, invL);
         const float dz = min_img(xi.z - xo.z, L, invL);
-        r2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        r2[q] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u;
-        if (r2[u] < rcs2 && j != sl && j < n) {
-          if (k < maxnb) {
-            st_shared_u16(stage + 2u * (uint32_t)(k & 7), j);
-            if ((k & 7) == 7) lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
-          }
+      for (int q = 0; q < 4; ++q) {
+        const int j = jb + q * tpa;
+        if (r2[q] < rcs2 && j != i && j < n) {
+          ls_push(st, (uint32_t)j);
           ++k;
+          if (++st.cnt == 8) {
+            if (kw < maxw) lrow[(size_t)kw * wstride] = make_uint4(st.w0, st.w1, st.w2, st.w3);
+            ++kw;
+            st.cnt = 0;
+          }
         }
       }
     }
-    if (k > maxnb) {
+    if (st.cnt > 0) {
+#pragma unroll 1
+      for (int q = st.cnt; q < 8; ++q) ls_push(st, (uint32_t)i);
+      if (kw < maxw) lrow[(size_t)kw * wstride] = make_uint4(st.w0, st.w1, st.w2, st.w3);
+      ++kw;
+    }
+    if (kw > maxw) {
       atomicOr(reinterpret_cast<int*>(__cvta_shared_to_generic(ovf_a)), 1);
-      k = maxnb;
+      k = maxw * 8;
     }
-    if ((k & 7) != 0) {
-      for (int u = k & 7; u < 8; ++u) st_shared_u16(stage + 2u * (uint32_t)u, sl);
-      lrow[(size_t)(k >> 3) * npad] = ld_shared_u4(stage);
-    }
-    st_shared_v4(stage, make_float4(0.f, 0.f, 0.f, __int_as_float(list_meta((k + 7) >> 3, 0, k))));
+    // the counts of the atom's sub-lists, packed into its list word by lane p = 0
+    const unsigned m = tpa_mask(tpa);
+    int meta = tpa == 1 ? list_meta((k + 7) >> 3, 0, k) : (k << ((tpa == 4 ? 8 : 16) * p));
+    if (tpa > 1) meta |= __shfl_xor_sync(m, meta, 1);
+    if (tpa > 2) meta |= __shfl_xor_sync(m, meta, 2);
+    if (p == 0) st_shared_v4(meta_a + 16u * (uint32_t)i, make_float4(0.f, 0.f, 0.f, __int_as_float(meta)));
   }
 }
 
@@ -914,13 +1021,22 @@ __device__ void build_nlist(const Group& g, const BoxCtx& b, long long* prof = n
     MDEOS_PHASE(5)
   } else {
     gbar(g.bar, g.nt);  // positions just wrapped by their owners
-    nl_search_all<APT>((uint32_t)__cvta_generic_to_shared(xs), (uint32_t)__cvta_generic_to_shared(srt),
-                       (uint32_t)__cvta_generic_to_shared(&g.ctrl()[CTRL_OVERFLOW]), g.nl, g.tid,
-                       g.nt, g.npad, n, b.L, b.invL, b.rcs2, b.maxnb);
+    // the lists of this CTA's atoms (all of them without a cluster)
+    int a0, a1;
+    own_atoms(g, n, a0, a1);
+    nl_search_all((uint32_t)__cvta_generic_to_shared(xs), (uint32_t)__cvta_generic_to_shared(srt),
+                  (uint32_t)__cvta_generic_to_shared(&g.ctrl()[CTRL_OVERFLOW]), g.nl, g.tid, g.nt,
+                  g.npad, n, b.tpa, a0 * b.tpa, a1 * b.tpa, b.L, b.invL, b.rcs2, b.maxnb);
     gbar(g.bar, g.nt);
+    if (g.csize > 1) {  // a list overflow anywhere ends the box in every CTA alike
+      if (g.tid == 0 && g.ctrl()[CTRL_OVERFLOW] != 0) {
+        const uint32_t o_a = (uint32_t)__cvta_generic_to_shared(&g.ctrl()[CTRL_OVERFLOW]);
+        for (int rk = 0; rk < g.csize; ++rk) st_cluster_s32(cluster_map(o_a, rk), 1);
+      }
+      cluster_sync();
+    }
     MDEOS_PHASE(5)
   }
-  build_order<APT>(g, b);
 #undef MDEOS_PHASE
 }
 
@@ -1339,7 +1455,7 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
         for (int a = 0; a < APT; ++a) {
           const int i = g.tid + a * g.nt;
           if (i < n) {
-            const int cw = (int)((unsigned)__float_as_int(g.f()[i].w) >> 16);
+            const int cw = list_entries(__float_as_int(g.f()[i].w), b.tpa);
             cand += (PATH == PATH_NLIST) ? cw
                                          : (PATH == PATH_ALLPAIRS ? n : 8 * n);
           }
@@ -1429,12 +1545,13 @@ __device__ void run_box(const Group& g, const BoxDesc& __restrict__ bd, const Ru
   if (bd.warm_state != nullptr) {
     // a list overflow leaves the stored state as it was (the host re-runs the box
     // with a larger list); any other failure invalidates it
-    if (status == MDEOS_OK) save_warm<APT>(g, b, bd, lam);
-    if (g.tid == 0 && status != MDEOS_ENBR)
+    // (in a cluster every CTA holds the same state: the first one stores it)
+    if (status == MDEOS_OK && g.crank == 0) save_warm<APT>(g, b, bd, lam);
+    if (g.tid == 0 && g.crank == 0 && status != MDEOS_ENBR)
       *(volatile unsigned long long*)bd.warm_tag = (status == MDEOS_OK) ? bd.element_id : 0ull;
   }
   // restriction: time averages and block standard errors
-  if (g.tid == 0) {
+  if (g.tid == 0 && g.crank == 0) {
     const double E_cold = boxc[0], E_ref = boxc[1], Tk = boxc[3];
     const double m = bd.steps_avg;
     mdeos_result r;

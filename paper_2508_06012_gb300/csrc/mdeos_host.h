@@ -19,6 +19,7 @@ struct PlanOut {
   int smem = 0;
   int grid = 0;
   long long nl_per_cta = 0;
+  int cluster = 1;  // CTAs per box (thread-block clusters); 1: the persistent kernel
 };
 
 mdeos_status set_error(mdeos_status st, const std::string& msg);
@@ -35,7 +36,7 @@ mdeos_status eval_into_device(mdeos_handle* h, const mdeos_request* reqs, int n,
 cudaError_t launch_eos_batch(const BoxDesc* boxes, const WorkItem* items, int nitems, int* counter,
                              mdeos_result* results, uint16_t* nl, long long nl_elems_per_cta,
                              const RunParams& rp, int grid, int smem, cudaStream_t st,
-                             int* ready);
+                             int* ready, int cluster = 1);
 
 cudaError_t launch_eos_serve(const ServeQueue& q, const RunParams& rp, uint16_t* nl,
                              long long nl_elems_per_cta, int grid, int smem, cudaStream_t st);

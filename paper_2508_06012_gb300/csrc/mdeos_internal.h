@@ -23,6 +23,7 @@ constexpr int kMaxAtoms = 4096;       // 1024 threads x 4 atoms per thread
 constexpr int kMaxSeBlocks = 32;
 constexpr int kMaxCells = 1728;       // cell-list cells per box (12 per axis)
 constexpr int kRedSlots = 11;         // reduction quantities per warp (64-bit fixed point)
+constexpr int kMaxCluster = 8;        // CTAs of a thread-block cluster that share one box
 // boxes above kMaxAtoms run one per CTA with their state in global memory
 constexpr int kMaxAtomsBig = 32768;   // uint16 neighbour indices
 constexpr int kMaxCellsBig = 32768;   // cells of the list build (<= 32 per axis)
@@ -38,6 +39,21 @@ constexpr int kBruteMaxAtoms = 768;  // shared-memory boxes up to this size: no 
 // each of its two output streams closes at most four partial words of at most seven
 // pad entries when its image code changes.
 constexpr int kListPadSlack = 56;
+
+// Threads per atom of a box whose list is built without cells (n <= kBruteMaxAtoms):
+// an atom's neighbours are split by slot modulo that number into sub-lists, each with
+// its own thread; the partial forces combine in a fixed order, so results depend on
+// the box alone.  Small boxes are latency-bound with one thread per atom.
+__host__ __device__ inline int brute_tpa(int n) { return n <= 384 ? 4 : 2; }
+
+// List entries per atom of such a box: brute_tpa sub-lists, each within the planner's
+// capacity and within its share of the slots (which no sub-list can outgrow).
+__host__ __device__ inline int brute_list_capacity(int n, int cap_total) {
+  const int t = brute_tpa(n);
+  const int chunk = (n + t - 1) / t;
+  const int cv = ((cap_total < chunk ? cap_total : chunk) + 7) & ~7;
+  return t * cv;
+}
 
 __host__ __device__ inline int list_cells_per_axis(double L, double R, int n) {
   if (!(L >= 2.0 * R) || n <= kBruteMaxAtoms) return 0;
@@ -128,23 +144,28 @@ constexpr int kAccDoubles = 2 * kMaxSeBlocks + 24;  // block sums of P and T, ru
 
 // Shared-memory layout of one box group (host planner and device agree):
 //   positions, forces, velocities  float4[npad] each (48 B per atom slot)
-//   force-pass order               uint16[npad] (slots by list length)
 //   cell counts / starts           int[2 * ncell_cap + 2]
 //   per-warp partials              int64[warps][kRedSlots]    (16-B aligned)
 //   FP64 broadcast slots           double[8]
 //   FP64 accumulators              double[kAccDoubles]
 //   block counts                   int[kMaxSeBlocks]
 //   control words                  int[16]
+//   cluster partials               int64[kMaxCluster][kRedSlots]  (16-B aligned)
 __host__ __device__ inline int group_red_offset(int warps, int apt, int ncell_cap) {
   int npad = warps * 32 * apt;
-  int b = npad * 50 + (2 * ncell_cap + 2) * 4;
+  int b = npad * 48 + (2 * ncell_cap + 2) * 4;
+  return (b + 15) & ~15;
+}
+
+__host__ __device__ inline int group_cluster_offset(int warps, int apt, int ncell_cap) {
+  int b = group_red_offset(warps, apt, ncell_cap);
+  b += warps * kRedSlots * 8;
+  b += 8 * 8 + kAccDoubles * 8 + kMaxSeBlocks * 4 + 16 * 4;
   return (b + 15) & ~15;
 }
 
 __host__ __device__ inline int group_smem_bytes(int warps, int apt, int ncell_cap) {
-  int b = group_red_offset(warps, apt, ncell_cap);
-  b += warps * kRedSlots * 8;
-  b += 8 * 8 + kAccDoubles * 8 + kMaxSeBlocks * 4 + 16 * 4;
+  const int b = group_cluster_offset(warps, apt, ncell_cap) + kMaxCluster * kRedSlots * 8;
   return (b + 127) & ~127;
 }
 

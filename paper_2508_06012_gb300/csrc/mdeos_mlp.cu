@@ -587,6 +587,12 @@ struct mdeos_surrogate {
   bool tc_ready = false;
   int nsm = 1;
   std::vector<void*> allocs;
+  // misfit map: RMS relative pressure residual of the ensemble mean per cell of a
+  // bins x bins grid over the inputs it was fitted on (infinite: too few samples)
+  int mis_bins = 0;
+  double mis_lo[2] = {0, 0}, mis_hi[2] = {1, 1};
+  std::vector<double> mis;
+  double mis_threshold = INFINITY;  // gate: reject above this (infinite: map not used)
 };
 
 #define SCK(call)                                                                      \
@@ -958,6 +964,74 @@ extern "C" mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double
 
 // Surrogate answer where the ensemble agrees (sd_P <= threshold * max(|P|, 1)),
 // the MD path (requests evaluated with natoms = md_natoms) elsewhere.
+// cell of the misfit grid holding input (rho, e); -1 outside the fitted range
+static int misfit_cell(const mdeos_surrogate* s, double rho, double e) {
+  if (s->mis_bins < 1) return -1;
+  const double in[2] = {rho, e};
+  int c[2];
+  for (int k = 0; k < 2; ++k) {
+    const double t = (in[k] - s->mis_lo[k]) / (s->mis_hi[k] - s->mis_lo[k]);
+    if (!(t >= 0.0 && t <= 1.0)) return -1;
+    c[k] = std::min((int)(t * s->mis_bins), s->mis_bins - 1);
+  }
+  return c[0] * s->mis_bins + c[1];
+}
+
+static double misfit_at(const mdeos_surrogate* s, double rho, double e) {
+  const int c = misfit_cell(s, rho, e);
+  return c < 0 ? INFINITY : s->mis[c];
+}
+
+extern "C" mdeos_status mdeos_surrogate_fit_misfit(mdeos_surrogate* s, const double* x,
+                                                   const double* y, int32_t n, int32_t bins,
+                                                   int32_t min_count) {
+  if (!s || !x || !y || n < 1 || bins < 1 || bins > 1024 || min_count < 1)
+    return set_error(MDEOS_EINVAL, "bad fit_misfit arguments");
+  std::vector<double> mean(2 * (size_t)n), sd(2 * (size_t)n);
+  mdeos_status ms = mdeos_surrogate_predict(s, x, n, mean.data(), sd.data(), nullptr);
+  if (ms != MDEOS_OK) return ms;
+  for (int k = 0; k < 2; ++k) {
+    s->mis_lo[k] = INFINITY;
+    s->mis_hi[k] = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+      s->mis_lo[k] = std::min(s->mis_lo[k], x[2 * i + k]);
+      s->mis_hi[k] = std::max(s->mis_hi[k], x[2 * i + k]);
+    }
+    if (!(s->mis_hi[k] > s->mis_lo[k])) s->mis_hi[k] = s->mis_lo[k] + 1.0;
+  }
+  s->mis_bins = bins;
+  std::vector<double> sum((size_t)bins * bins, 0.0);
+  std::vector<int> cnt((size_t)bins * bins, 0);
+  for (int i = 0; i < n; ++i) {
+    const int c = misfit_cell(s, x[2 * i], x[2 * i + 1]);
+    if (c < 0) continue;
+    const double r = (mean[2 * i] - y[2 * i]) / std::max(std::fabs(y[2 * i]), 1.0);
+    sum[c] += r * r;
+    ++cnt[c];
+  }
+  s->mis.assign((size_t)bins * bins, INFINITY);
+  for (size_t c = 0; c < s->mis.size(); ++c)
+    if (cnt[c] >= min_count) s->mis[c] = std::sqrt(sum[c] / cnt[c]);
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_misfit(const mdeos_surrogate* s, const double* x,
+                                               int32_t n, double* out) {
+  if (!s || !x || !out || n < 0) return set_error(MDEOS_EINVAL, "bad misfit arguments");
+  if (s->mis_bins < 1) return set_error(MDEOS_EINVAL, "no misfit map fitted");
+  for (int i = 0; i < n; ++i) out[i] = misfit_at(s, x[2 * i], x[2 * i + 1]);
+  return MDEOS_OK;
+}
+
+extern "C" mdeos_status mdeos_surrogate_set_misfit_threshold(mdeos_surrogate* s,
+                                                             double threshold) {
+  if (!s || !(threshold >= 0.0)) return set_error(MDEOS_EINVAL, "bad misfit threshold");
+  if (std::isfinite(threshold) && s->mis_bins < 1)
+    return set_error(MDEOS_EINVAL, "no misfit map fitted");
+  s->mis_threshold = threshold;
+  return MDEOS_OK;
+}
+
 extern "C" mdeos_status mdeos_surrogate_gated_eval(mdeos_surrogate* s, const mdeos_request* reqs,
                                                    int32_t n, double threshold, int32_t md_natoms,
                                                    mdeos_result* out, int32_t* used_md) {
@@ -974,7 +1048,9 @@ extern "C" mdeos_status mdeos_surrogate_gated_eval(mdeos_surrogate* s, const mde
   std::vector<int> idx;
   for (int i = 0; i < n; ++i) {
     const bool ok = sd[2 * i] <= threshold * std::max(std::fabs(mean[2 * i]), 1.0) &&
-                    (reqs[i].flags & MDEOS_REQ_TEMPERATURE) == 0;
+                    (reqs[i].flags & MDEOS_REQ_TEMPERATURE) == 0 &&
+                    (!std::isfinite(s->mis_threshold) ||
+                     misfit_at(s, reqs[i].rho, reqs[i].e) <= s->mis_threshold);
     if (used_md) used_md[i] = ok ? 0 : 1;
     if (ok) {
       mdeos_result& r = out[i];

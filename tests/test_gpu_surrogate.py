@@ -287,3 +287,35 @@ def test_trained_network_gains_over_md_only(m, h):
     assert np.array_equal(out["P"][~answered], rtest["P"][~answered])
     # MD boxes run: the gated path's MD share against one per query without it
     assert int((~answered).sum()) <= len(test) // 2
+
+
+def test_misfit_map_flags_a_rough_region(m, h):
+    """The misfit map holds the RMS relative residual of the ensemble mean per cell of
+    its training inputs: where the data are rough (here: noise added for rho > 0.8)
+    every member misses them alike, the map is high there, and the gate with a misfit
+    threshold sends such requests to MD while it still answers the smooth region."""
+    rng = np.random.default_rng(3)
+    n = 8192
+    x = np.stack([rng.uniform(0.5, 1.0, n), rng.uniform(1.0, 3.0, n)], axis=1)
+    P = 2.0 * x[:, 0] * x[:, 1] + x[:, 0] ** 2
+    rough = x[:, 0] > 0.8
+    Pn = P * (1.0 + np.where(rough, 0.1, 0.0) * rng.normal(size=n))
+    y = np.stack([Pn, x[:, 1] / 1.5], axis=1)
+    with m.Surrogate(h, 4, 2048, seed=5) as sg:
+        sg.train(x, y, epochs=40, batch=512, lr=2e-3, seed=3)
+        sg.fit_misfit(x, y, bins=10, min_count=8)
+        xs = np.stack([np.full(50, 0.6), np.linspace(1.2, 2.8, 50)], axis=1)
+        xr = np.stack([np.full(50, 0.95), np.linspace(1.2, 2.8, 50)], axis=1)
+        ms, mr = sg.misfit(xs), sg.misfit(xr)
+        assert np.isfinite(ms).all() and np.isfinite(mr).all()
+        assert np.median(mr) > 0.05 > 0.02 > np.median(ms), (np.median(ms), np.median(mr))
+        assert np.isinf(sg.misfit(np.array([[0.3, 2.0], [0.7, 5.0]]))).all()  # outside the map
+        reqs = [dict(rho=float(r), e=float(e), natoms=108, steps_equil=20, steps_avg=20, seed=k)
+                for k, (r, e) in enumerate(np.concatenate([xs[::10], xr[::10]]))]
+        sg.set_misfit_threshold(0.03)
+        out, used = sg.gated_eval(reqs, 1e9)  # the spread alone would answer everything
+        assert (used[:5] == 0).all() and (used[5:] == 1).all(), used
+        assert (out["path"][5:] >= 0).all() and (out["status"] == 0).all()
+        sg.set_misfit_threshold(float("inf"))
+        _, used = sg.gated_eval(reqs, 1e9)
+        assert (used == 0).all()
