@@ -225,7 +225,7 @@ def ours(args):
         boxes = w.config2(base_seed=20250807 + rank)
     reqs = gpu_requests(m, boxes)
     nbox = len(reqs)
-    h = m.mdeos_create(m.mdeos_config_default(device=local))
+    h = m.mdeos_create(m.mdeos_config_default(device=local, max_cluster=args.max_cluster))
     tune = None
     if not args.no_autotune:  # measured skin per atom count (outside the timed region)
         t_tune = time.perf_counter()
@@ -1029,6 +1029,8 @@ def main():
                     help="forcepass: 0 forces, 1 forces + energy/virial, 2 list build")
     ap.add_argument("--fb-passes", type=int, default=5, help="forcepass: passes per launch")
     ap.add_argument("--big-natoms", type=int, default=32000, help="bigbox: atoms per box")
+    ap.add_argument("--max-cluster", type=int, default=0,
+                    help="CTAs per box for batches of few small boxes (0: up to 4, 1: none)")
     ap.add_argument("--workload", choices=["uneven", "config1", "coupled", "serving",
                                            "surrogate", "surrogate-infer", "forcepass",
                                            "bigbox"],

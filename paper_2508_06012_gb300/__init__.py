@@ -59,6 +59,7 @@ class mdeos_config(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
         ("warm_lift_iters", ctypes.c_int32), ("warm_slots", ctypes.c_int32),
         ("warm_atoms", ctypes.c_int32), ("nlist_capacity", ctypes.c_int32),
+        ("max_cluster", ctypes.c_int32),
     ]
 
 

@@ -547,6 +547,7 @@ static __device__ void cluster_exchange(const Group& g, FSums& r, int a0, int a1
   for (int k = 0; k < 9; ++k) q[k] = warp_sum_ll(q[k]);
   long long* red = g.red();
   if (g.lane() == 0)
+#pragma unroll
     for (int k = 0; k < 9; ++k) red[g.warp() * kRedSlots + k] = q[k];
   gbar(g.bar, g.nt);
   const uint32_t f_a = (uint32_t)__cvta_generic_to_shared(g.f());
@@ -555,29 +556,35 @@ static __device__ void cluster_exchange(const Group& g, FSums& r, int a0, int a1
     for (int rk = 0; rk < g.csize; ++rk)
       if (rk != g.crank) st_cluster_v4(cluster_map(f_a + 16u * (uint32_t)i, rk), fi);
   }
-  if (g.tid == 0) {
-    long long t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int w = 0; w < g.nwarps; ++w)
-      for (int k = 0; k < 9; ++k) t[k] += red[w * kRedSlots + k];
-    const uint32_t c_a = (uint32_t)__cvta_generic_to_shared(g.clu() + g.crank * kRedSlots);
-    for (int rk = 0; rk < g.csize; ++rk)
-      for (int k = 0; k < 9; ++k) st_cluster_s64(cluster_map(c_a + 8u * k, rk), t[k]);
+  // lane k < 9 of warp 0: the CTA's sum of quantity k, into slot (crank, k) of every CTA
+  const int lane = g.lane();
+  if (g.warp() == 0 && lane < 9) {
+    long long t = 0;
+    for (int w = 0; w < g.nwarps; ++w) t += red[w * kRedSlots + lane];
+    const uint32_t c_a =
+        (uint32_t)__cvta_generic_to_shared(g.clu() + g.crank * kRedSlots + lane);
+    for (int rk = 0; rk < g.csize; ++rk) st_cluster_s64(cluster_map(c_a, rk), t);
   }
   cluster_sync();
   FSums z = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0, 0};
-  if (g.tid == 0) {
-    long long t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int rk = 0; rk < g.csize; ++rk)
-      for (int k = 0; k < 9; ++k) t[k] += g.clu()[rk * kRedSlots + k];
-    z.e = (unsigned long long)t[0];
-    z.w0 = (unsigned long long)t[1];
-    z.w1 = (unsigned long long)t[2];
-    z.w2 = (unsigned long long)t[3];
-    z.w3 = (unsigned long long)t[4];
-    z.w4 = (unsigned long long)t[5];
-    z.w5 = (unsigned long long)t[6];
-    z.np = (int)t[7];
-    z.bad = t[8] != 0;
+  if (g.warp() == 0) {
+    long long t = 0;
+    if (lane < 9)
+      for (int rk = 0; rk < g.csize; ++rk) t += g.clu()[rk * kRedSlots + lane];
+    long long v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = __shfl_sync(0xffffffffu, t, k);
+    if (lane == 0) {
+      z.e = (unsigned long long)v[0];
+      z.w0 = (unsigned long long)v[1];
+      z.w1 = (unsigned long long)v[2];
+      z.w2 = (unsigned long long)v[3];
+      z.w3 = (unsigned long long)v[4];
+      z.w4 = (unsigned long long)v[5];
+      z.w5 = (unsigned long long)v[6];
+      z.np = (int)v[7];
+      z.bad = v[8] != 0;
+    }
   }
   r = z;
 }

@@ -40,9 +40,9 @@ def _filler(m, count):
 
 def test_clustered_boxes_equal_packed_boxes(m):
     reqs = _small(m, 0, 10)
-    with m.Engine() as eng:
+    with m.Engine() as eng, m.Engine(max_cluster=8) as eng8:
         alone = eng.evaluate(reqs)          # 10 boxes: clusters of 4 CTAs (152 SMs)
-        one = eng.evaluate(reqs[:1])        # 1 box: a cluster of 8
+        one = eng8.evaluate(reqs[:1])       # 1 box: a cluster of 8
         mixed = eng.evaluate(reqs + _filler(m, 300))[:10]  # packed, no clusters
     assert (alone["status"] == 0).all()
     assert alone.tobytes() == mixed.tobytes()
@@ -59,7 +59,7 @@ def test_cluster_plan_shape(m):
         b = m.mdeos_batch_create(h, reqs)
         info = m.mdeos_batch_info(b)
         C = 1
-        while C < 8 and 2 * C * 10 <= nsm:
+        while C < 4 and 2 * C * 10 <= nsm:
             C *= 2
         assert info["items"] == 10 and info["ctas"] == 10 * C
         m.mdeos_batch_launch(b)
