@@ -433,9 +433,10 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
         const int nw = CODED ? meta & 0xfff : (sub_entries(meta, tpa, p) + 7) >> 3;
         uint4 q = nw > 0 ? __ldcg(lp) : make_uint4(0u, 0u, 0u, 0u);
         if (CODED) {
-          const float xa = xi.x + ((meta & 0x1000) ? -L : L);
-          const float ya = xi.y + ((meta & 0x2000) ? -L : L);
-          const float za = xi.z + ((meta & 0x4000) ? -L : L);
+          // home shift along an axis: +L for atoms in the lower half of the grid
+#define MDEOS_SHIFT(bit) ((meta & (bit)) ? -L : L)
+          const float xa = xi.x + MDEOS_SHIFT(0x1000), ya = xi.y + MDEOS_SHIFT(0x2000);
+          const float za = xi.z + MDEOS_SHIFT(0x4000);
 #pragma unroll 1
           for (int kb = 0; kb < nw; ++kb) {
             const uint4 cur = q;
@@ -447,14 +448,53 @@ __device__ __noinline__ FSums force_pass(uint32_t xs_a, float4* fs, const uint16
             const int j2 = (int)(cur.y & 0xffffu), j3 = (int)(cur.y >> 16);
             const int j4 = (int)(cur.z & 0xffffu), j5 = (int)(cur.z >> 16);
             const int j6 = (int)(cur.w & 0xffffu), j7 = (int)(cur.w >> 16);
-            nl_pair_sh<EN, VIR>(xs_a, j0, j0 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
-            nl_pair_sh<EN, VIR>(xs_a, j1, j1 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
-            nl_pair_sh<EN, VIR>(xs_a, j2, j2 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
-            nl_pair_sh<EN, VIR>(xs_a, j3, j3 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
-            nl_pair_sh<EN, VIR>(xs_a, j4, j4 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
-            nl_pair_sh<EN, VIR>(xs_a, j5, j5 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
-            nl_pair_sh<EN, VIR>(xs_a, j6, j6 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
-            nl_pair_sh<EN, VIR>(xs_a, j7, j7 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            const float px = fx, py = fy, pz = fz;  // the force before this word
+            // the virial is taken per atom below, not per pair
+            nl_pair_sh<EN, false>(xs_a, j0, j0 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, false>(xs_a, j1, j1 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, false>(xs_a, j2, j2 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, false>(xs_a, j3, j3 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, false>(xs_a, j4, j4 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, false>(xs_a, j5, j5 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, false>(xs_a, j6, j6 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            nl_pair_sh<EN, false>(xs_a, j7, j7 != i, hx, hy, hz, c, fx, fy, fz, e, w, np);
+            if (VIR) {
+              // image term of the word: its shift S (per axis: sx, sy, sz or 0) times
+              // its force G, symmetrised, into w (xx, yy, zz, xy, xz, yz)
+              const float gx = fx - px, gy = fy - py, gz = fz - pz;
+              if (cur.x & 0x1000u) {
+                const float sh = MDEOS_SHIFT(0x1000);
+                w[0] = fmaf(sh, gx, w[0]);
+                w[3] = fmaf(0.5f * sh, gy, w[3]);
+                w[4] = fmaf(0.5f * sh, gz, w[4]);
+              }
+              if (cur.x & 0x2000u) {
+                const float sh = MDEOS_SHIFT(0x2000);
+                w[1] = fmaf(sh, gy, w[1]);
+                w[3] = fmaf(0.5f * sh, gx, w[3]);
+                w[5] = fmaf(0.5f * sh, gz, w[5]);
+              }
+              if (cur.x & 0x4000u) {
+                const float sh = MDEOS_SHIFT(0x4000);
+                w[2] = fmaf(sh, gz, w[2]);
+                w[4] = fmaf(0.5f * sh, gx, w[4]);
+                w[5] = fmaf(0.5f * sh, gy, w[5]);
+              }
+            }
+          }
+#undef MDEOS_SHIFT
+          if (VIR) {
+            // Virial of the box from the atom's total force: with full lists and
+            // f_ji = -f_ij, sum_{i<j} d_ij (x) f_ij = sum_i [x_i (x) F_i +
+            // 1/2 sum_w S_w (x) F_i,w] (x_i the positions the forces were taken at,
+            // F_i,w the force from word w, S_w its image shift), symmetrised; w held
+            // the image terms, and the halving of the per-pair form below is undone
+            w[0] = 2.0f * fmaf(xi.x, fx, 0.5f * w[0]);
+            w[1] = 2.0f * fmaf(xi.y, fy, 0.5f * w[1]);
+            w[2] = 2.0f * fmaf(xi.z, fz, 0.5f * w[2]);
+            w[3] = 2.0f * fmaf(0.5f * xi.x, fy, fmaf(0.5f * xi.y, fx, 0.5f * w[3]));
+            w[4] = 2.0f * fmaf(0.5f * xi.x, fz, fmaf(0.5f * xi.z, fx, 0.5f * w[4]));
+            w[5] = 2.0f * fmaf(0.5f * xi.y, fz, fmaf(0.5f * xi.z, fy, 0.5f * w[5]));
           }
         } else {
 #pragma unroll 1
