@@ -43,8 +43,10 @@ constexpr int kListPadSlack = 56;
 // Threads per atom of a box whose list is built without cells (n <= kBruteMaxAtoms):
 // an atom's neighbours are split by slot modulo that number into sub-lists, each with
 // its own thread; the partial forces combine in a fixed order, so results depend on
-// the box alone.  Small boxes are latency-bound with one thread per atom.
-__host__ __device__ inline int brute_tpa(int n) { return n <= 384 ? 4 : 2; }
+// the box alone.  Boxes of up to 384 atoms are latency-bound with one thread per atom;
+// from 385 atoms on, the extra sub-list work costs more than it gains (measured on
+// 500-atom boxes packed many to a CTA).
+__host__ __device__ inline int brute_tpa(int n) { return n <= 384 ? 4 : 1; }
 
 // List entries per atom of such a box: brute_tpa sub-lists, each within the planner's
 // capacity and within its share of the slots (which no sub-list can outgrow).

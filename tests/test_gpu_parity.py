@@ -108,10 +108,10 @@ CASES = [
     (256, 0.8, 0, 2),
     (108, 1.15, 1, 3),     # all-pairs over two images per axis (L = 4.5 < 2 rc)
     (64, 0.9, 1, 4),
-    (500, 0.9, 2, 5),      # Verlet list, brute-force build (L = 8.2 < 3 (rc + skin)), 2 threads per atom
+    (500, 0.9, 2, 5),      # Verlet list, brute-force build (L = 8.2 < 3 (rc + skin)), 1 thread per atom
     (256, 0.85, 2, 8),     # brute-force build, 4 threads per atom
     (384, 0.7, 2, 9),      # largest box with 4 threads per atom
-    (385, 0.7, 2, 10),     # smallest with 2
+    (385, 0.7, 2, 10),     # smallest with 1
     (2048, 1.1, 2, 6),     # Verlet list from the shared-memory cell list
     (4000, 0.3, 2, 7),     # largest config-2 box, dilute
     (4000, 1.2, 2, 8),     # largest config-2 box, dense
