@@ -786,12 +786,12 @@ def surrogate(args):
                         "tflops_incl_host_copies": flops / t_inf / 1e12,
                         "bf16_peak_tflops": peaks.get("bf16_tflops")}
     # device-resident inference (inputs and outputs in HBM), CUDA events on the launching
-    # stream, fused tcgen05 kernel vs the layered mma.sync path
+    # stream, fused tcgen05 kernel vs the layered path (GEMM + elementwise kernels)
     xd = torch.from_numpy(xi).cuda()
     md, sdd = torch.zeros_like(xd), torch.zeros_like(xd)
     st = torch.cuda.Stream()
     dev = {}
-    for name, path in (("tcgen05_fused", m.SURROGATE_INFER_TC), ("mma_layered", m.SURROGATE_INFER_MMA)):
+    for name, path in (("tcgen05_fused", m.SURROGATE_INFER_TC), ("gemm_layered", m.SURROGATE_INFER_MMA)):
         big.set_infer_path(path)
         with torch.cuda.stream(st):
             for _ in range(3):
@@ -833,7 +833,8 @@ SURROGATE_INFER = ("surrogate inference: ensemble of 4 MLPs 2-128-128-128-2 (bf1
 
 def surrogate_infer(args):
     """Inference throughput of the surrogate ensemble on device-resident queries: the
-    fused tcgen05 kernel (timed) against the layered mma.sync path (reported beside)."""
+    fused tcgen05 kernel (timed) against the layered path of GEMM and elementwise kernels
+    (reported beside)."""
     import torch
 
     import paper_2508_06012_gb300 as m
@@ -855,7 +856,7 @@ def surrogate_infer(args):
     res = {}
     l0 = m.mdeos_stats(h)["launches"]
     for name, path in (("tcgen05_fused", m.SURROGATE_INFER_TC),
-                       ("mma_layered", m.SURROGATE_INFER_MMA)):
+                       ("gemm_layered", m.SURROGATE_INFER_MMA)):
         sg.set_infer_path(path)
         with torch.cuda.stream(st):
             for _ in range(args.warmup):

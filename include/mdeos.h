@@ -488,9 +488,10 @@ mdeos_status mdeos_surrogate_predict(mdeos_surrogate* s, const double* x, int32_
 /* Inference paths.  TC (default): one fused kernel per 128 inputs and model; layer 1
  * on the CUDA cores, the two 128 x 128 layers as tcgen05.mma with the accumulator in
  * tensor memory, bias + tanh + the output layer in the epilogue.  MMA: the layered
- * path the training step uses (mma.sync GEMMs and elementwise kernels, activations
- * through device memory).  Both apply the same bf16 roundings; they differ only in
- * the FP32 summation order.  EINVAL for any other value. */
+ * path the training step uses (its tcgen05 GEMMs, one per layer over all inputs, and
+ * elementwise kernels, activations through device memory).  Both apply the same bf16
+ * roundings; they differ only in the FP32 summation order.  EINVAL for any other
+ * value. */
 #define MDEOS_SURROGATE_INFER_TC 0
 #define MDEOS_SURROGATE_INFER_MMA 1
 mdeos_status mdeos_surrogate_set_infer_path(mdeos_surrogate* s, int32_t path);

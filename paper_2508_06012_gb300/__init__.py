@@ -646,7 +646,8 @@ class Surrogate:
         _check(lib().mdeos_surrogate_set_misfit_threshold(self.s, float(threshold)))
 
     def set_infer_path(self, path: int):
-        """SURROGATE_INFER_TC (fused tcgen05 kernel, default) or SURROGATE_INFER_MMA."""
+        """SURROGATE_INFER_TC (fused tcgen05 kernel, default) or SURROGATE_INFER_MMA (the
+        layered path of the training step)."""
         _check(lib().mdeos_surrogate_set_infer_path(self.s, path))
 
     def infer_device(self, x, mean, sd, stream=None):

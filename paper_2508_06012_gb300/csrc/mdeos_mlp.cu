@@ -33,9 +33,8 @@ constexpr int kOffB2 = kOffW2 + kH * kH, kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 +
 constexpr int kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + 2 * kH, kNParam = kOffB4 + 2;
 
 // ---------------------------------------------------------------------------
-// C[z](m, n) = sum_k A[z](m, k) B[z](k, n), bf16 operands with arbitrary strides (in
-// elements), fp32 result.  64x64 tile per CTA, k in steps of 32 staged in shared
-// memory as [row][k] for both operands, 4 warps of 32x32, mma.m16n8k16.
+// C[z](m, n) = sum_k A[z](m, k) B[z](k, n): bf16 operands with arbitrary strides (in
+// elements), fp32 result (bf16_gemm_tc_kernel below).
 struct GemmArgs {
   const __nv_bfloat16* A;
   const __nv_bfloat16* B;
@@ -43,81 +42,6 @@ struct GemmArgs {
   int M, N, K;
   long long sa_m, sa_k, sa_z, sb_k, sb_n, sb_z, sc_m, sc_n, sc_z;
 };
-
-constexpr int kTM = 64, kTN = 64, kTK = 32, kTKP = kTK + 8;  // padded rows: no bank conflicts
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__global__ void __launch_bounds__(128) bf16_gemm_kernel(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[kTM][kTKP];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kTN][kTKP];
-  const int z = blockIdx.z;
-  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-  const __nv_bfloat16* A = g.A + (long long)z * g.sa_z;
-  const __nv_bfloat16* B = g.B + (long long)z * g.sb_z;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int gq = lane >> 2, tq = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int k0 = 0; k0 < g.K; k0 += kTK) {
-    // stage: 64 x 32 elements of each operand, zero outside the matrix
-    for (int e = tid; e < kTM * kTK; e += 128) {
-      const int r = e / kTK, c = e % kTK;
-      const int m = m0 + r, n = n0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < g.K) ? A[(long long)m * g.sa_m + (long long)k * g.sa_k] : zero;
-      Bs[r][c] = (n < g.N && k < g.K) ? B[(long long)k * g.sb_k + (long long)n * g.sb_n] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < kTK; ks += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + gq;
-        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq]);
-        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq]);
-        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq + 8]);
-        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = wn + j * 8 + gq;
-        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * tq]);
-        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
-    }
-    __syncthreads();
-  }
-  float* C = g.C + (long long)z * g.sc_z;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + gq + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + 2 * tq + (r & 1);
-        if (m < g.M && n < g.N) C[(long long)m * g.sc_m + (long long)n * g.sc_n] = acc[i][j][r];
-      }
-}
 
 // ---------------------------------------------------------------------------
 // elementwise parts; index layout [model][sample][unit]
@@ -561,6 +485,141 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* X
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// The training products on the 5th-generation tensor cores: C[z](m, n) =
+// sum_k A[z](m, k) B[z](k, n) with arbitrary strides (GemmArgs), one 128 x 128 tile of
+// C per CTA with the fp32 accumulator in
+// tensor memory.  K runs in chunks of 64: the 128 threads stage A's 128 x 64 and B's
+// (128 columns of C) x 64 elements into the canonical no-swizzle K-major layout (8 x 8
+// core matrices of 128 B: element (r, k) at (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16
+// + (k % 8) * 2; zero outside the matrices), one thread issues four tcgen05.mma of
+// K = 16 and commits to an mbarrier, and every thread waits (at most ~1 s, then the
+// error flag is set and the tile is left unwritten) before the next chunk overwrites the
+// tiles.  Epilogue: thread t reads TMEM lane t (row m0 + t), 32 columns at a time.
+
+constexpr int kGK = 64;                   // K per staged chunk
+constexpr uint32_t kGSbo = 1024;          // bytes between 8-row groups of a chunk
+constexpr int kGTile = kTcRows * kGK * 2; // 16 KB per operand chunk
+
+__device__ __forceinline__ uint32_t gk_off(int r, int k) {
+  return (uint32_t)((r >> 3) * kGSbo + (k >> 3) * kLbo + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t gk_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kGSbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* err) {
+  __shared__ __align__(1024) unsigned char gsm[2 * kGTile];
+  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ uint32_t s_tmem;
+  const int z = blockIdx.z, m0 = blockIdx.y * kTcRows, n0 = blockIdx.x * kH;
+  const __nv_bfloat16* A = g.A + (long long)z * g.sa_z;
+  const __nv_bfloat16* B = g.B + (long long)z * g.sb_z;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sA = (uint32_t)__cvta_generic_to_shared(gsm), sB = sA + kGTile;
+  const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // 128 TMEM columns: the 128 x 128 fp32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(&s_tmem)), "r"(kH) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&s_tmem);
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  uint32_t commits = 0;
+  bool ok = true;
+  // operands contiguous along K (and 16-byte aligned rows): eight elements per load,
+  // one core-matrix row per store; otherwise element by element with the contiguous
+  // index (M or N) running fastest across the threads
+  const bool a_vec = g.sa_k == 1 && (g.sa_m & 7) == 0 && (g.sa_z & 7) == 0 &&
+                     ((uintptr_t)g.A & 15) == 0 && (g.K & 7) == 0;
+  const bool b_vec = g.sb_k == 1 && (g.sb_n & 7) == 0 && (g.sb_z & 7) == 0 &&
+                     ((uintptr_t)g.B & 15) == 0 && (g.K & 7) == 0;
+  for (int k0 = 0; k0 < g.K; k0 += kGK) {
+    if (a_vec) {
+      for (int q = tid; q < kTcRows * (kGK / 8); q += kTcRows) {
+        const int r = q & (kTcRows - 1), c = (q >> 7) * 8;  // consecutive threads: rows
+        const int m = m0 + r, k = k0 + c;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (m < g.M && k < g.K) v = *reinterpret_cast<const uint4*>(A + (long long)m * g.sa_m + k);
+        *reinterpret_cast<uint4*>(gsm + gk_off(r, c)) = v;
+      }
+    } else {
+      for (int e = tid; e < kTcRows * kGK; e += kTcRows) {
+        const int r = e & (kTcRows - 1), c = e >> 7;  // consecutive threads: rows (M)
+        const int m = m0 + r, k = k0 + c;
+        *reinterpret_cast<__nv_bfloat16*>(gsm + gk_off(r, c)) =
+            (m < g.M && k < g.K) ? A[(long long)m * g.sa_m + (long long)k * g.sa_k] : zero;
+      }
+    }
+    if (b_vec) {
+      for (int q = tid; q < kTcRows * (kGK / 8); q += kTcRows) {
+        const int r = q & (kTcRows - 1), c = (q >> 7) * 8;
+        const int n = n0 + r, k = k0 + c;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (n < g.N && k < g.K) v = *reinterpret_cast<const uint4*>(B + (long long)n * g.sb_n + k);
+        *reinterpret_cast<uint4*>(gsm + kGTile + gk_off(r, c)) = v;
+      }
+    } else {
+      for (int e = tid; e < kTcRows * kGK; e += kTcRows) {
+        const int r = e & (kTcRows - 1), c = e >> 7;  // consecutive threads: columns (N)
+        const int n = n0 + r, k = k0 + c;
+        *reinterpret_cast<__nv_bfloat16*>(gsm + kGTile + gk_off(r, c)) =
+            (n < g.N && k < g.K) ? B[(long long)k * g.sb_k + (long long)n * g.sb_n] : zero;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // tiles -> tensor core
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < kGK / 16; ++ks)  // K step of 16 = two core matrices along K
+        tc_mma(tmem, gk_desc(sA + ks * 2 * kLbo), gk_desc(sB + ks * 2 * kLbo),
+               (k0 > 0 || ks > 0) ? 1u : 0u);
+      tc_commit(mbar);
+    }
+    __syncwarp();
+    const bool done = mbar_wait(mbar, commits & 1u);
+    ++commits;
+    ok = __syncthreads_and(done) != 0;  // the same decision in every thread
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) break;
+  }
+  if (ok) {
+    const int m = m0 + tid;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    float* C = g.C + (long long)z * g.sc_z;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float v[32];
+      tc_ld32(tl + (uint32_t)c0, v);  // every lane of the warp, in or out of the matrix
+      if (m < g.M)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < g.N) C[(long long)m * g.sc_m + (long long)n * g.sc_n] = v[j];
+        }
+    }
+  } else {  // leave the tile unwritten; let the MMAs in flight finish (bounded)
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(mbar, (commits - 1u) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  __syncwarp();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kH)
+                 : "memory");
+}
+
 __global__ void debug_tanh_kernel(const float* x, float* y, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = tanh_act(x[i]);
@@ -602,13 +661,15 @@ struct mdeos_surrogate {
       return set_error(MDEOS_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
   } while (0)
 
-static cudaError_t gemm(cudaStream_t st, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C,
-                        int M, int N, int K, long long sa_m, long long sa_k, long long sa_z,
-                        long long sb_k, long long sb_n, long long sb_z, long long sc_m,
-                        long long sc_n, long long sc_z, int Z) {
+// the training products: tcgen05 tiles of 128 x 128 (bf16_gemm_tc_kernel); a tensor-core
+// wait that ran out sets *err (device int) and leaves its tile unwritten
+static cudaError_t gemm(cudaStream_t st, int* err, const __nv_bfloat16* A,
+                        const __nv_bfloat16* B, float* C, int M, int N, int K, long long sa_m,
+                        long long sa_k, long long sa_z, long long sb_k, long long sb_n,
+                        long long sb_z, long long sc_m, long long sc_n, long long sc_z, int Z) {
   GemmArgs g{A, B, C, M, N, K, sa_m, sa_k, sa_z, sb_k, sb_n, sb_z, sc_m, sc_n, sc_z};
-  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, Z);
-  bf16_gemm_kernel<<<grid, 128, 0, st>>>(g);
+  dim3 grid((N + kH - 1) / kH, (M + kTcRows - 1) / kTcRows, Z);
+  bf16_gemm_tc_kernel<<<grid, kTcRows, 0, st>>>(g, err);
   return cudaGetLastError();
 }
 
@@ -622,10 +683,10 @@ static cudaError_t forward(mdeos_surrogate* s, int B, const float* T, cudaStream
   cudaError_t e;
   mlp_layer1<<<nblk(EB * kH), 256, 0, st>>>(s->X, s->P, s->W1b, s->H1, B, E);
   // Z2 = H1 W2^T: A(m=b, k=j) = H1[b][j], B(k=j, n=o) = W2[o][j]
-  e = gemm(st, s->H1, s->W2b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->H1, s->W2b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_bias_tanh<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->P, kOffB2, s->H2, B, E);
-  e = gemm(st, s->H2, s->W3b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->H2, s->W3b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_bias_tanh<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->P, kOffB3, s->H3, B, E);
   mlp_output<<<nblk(EB * 2), 256, 0, st>>>(s->H3, s->P, s->W4b, T, s->Y, s->dY, s->loss, B, E);
@@ -641,17 +702,17 @@ static cudaError_t backward(mdeos_surrogate* s, int B, cudaStream_t st) {
   mlp_back_out_w<<<nblk(E * (2 * kH + 2)), 256, 0, st>>>(s->dY, s->H3, s->G, B, E);
   mlp_back_out_dz<<<nblk(EB * kH), 256, 0, st>>>(s->dY, s->H3, s->W4b, s->dZb, B, E);
   // dW3 = dZ3^T H2: A(m=o, k=b) = dZ3[b][o], B(k=b, n=j) = H2[b][j]
-  e = gemm(st, s->dZb, s->H2, s->G + kOffW3, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
+  e = gemm(st, s->err, s->dZb, s->H2, s->G + kOffW3, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
   if (e != cudaSuccess) return e;
   mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(s->dZb, nullptr, s->G, kOffB3, B, E);
   // dH2 = dZ3 W3: A(m=b, k=o) = dZ3[b][o], B(k=o, n=j) = W3[o][j]
-  e = gemm(st, s->dZb, s->W3b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->dZb, s->W3b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_deriv<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->H2, s->dZb, nullptr, EB * kH);
-  e = gemm(st, s->dZb, s->H1, s->G + kOffW2, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
+  e = gemm(st, s->err, s->dZb, s->H1, s->G + kOffW2, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
   if (e != cudaSuccess) return e;
   mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(s->dZb, nullptr, s->G, kOffB2, B, E);
-  e = gemm(st, s->dZb, s->W2b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->dZb, s->W2b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_deriv<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->H1, nullptr, s->dZf, EB * kH);
   mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(nullptr, s->dZf, s->G, kOffB1, B, E);
@@ -765,6 +826,16 @@ extern "C" mdeos_status mdeos_surrogate_get_params(mdeos_surrogate* s, float* pa
   return MDEOS_OK;
 }
 
+// the tensor-core error flag of the surrogate's kernels: read and cleared (synchronous)
+static mdeos_status take_tc_error(mdeos_surrogate* s, cudaStream_t st) {
+  int err = 0;
+  SCK(cudaMemcpyAsync(&err, s->err, 4, cudaMemcpyDeviceToHost, st));
+  SCK(cudaMemsetAsync(s->err, 0, 4, st));
+  SCK(cudaStreamSynchronize(st));
+  if (err) return set_error(MDEOS_ETIMEDOUT, "surrogate: a tensor-core wait ran out");
+  return MDEOS_OK;
+}
+
 // normalised inputs/targets of n samples into s->X / s->T (host FP64 in)
 static mdeos_status load_batch(mdeos_surrogate* s, const double* xp, const double* yp, int n,
                                cudaStream_t st) {
@@ -803,7 +874,7 @@ extern "C" mdeos_status mdeos_surrogate_grads(mdeos_surrogate* s, const double* 
   SCK(cudaMemcpyAsync(&l, s->loss, 4, cudaMemcpyDeviceToHost, st));
   SCK(cudaStreamSynchronize(st));
   if (loss) *loss = (double)l / (2.0 * n * s->E);
-  return MDEOS_OK;
+  return take_tc_error(s, st);
 }
 
 extern "C" mdeos_status mdeos_surrogate_train(mdeos_surrogate* s, const double* x, const double* y,
@@ -867,7 +938,7 @@ extern "C" mdeos_status mdeos_surrogate_train(mdeos_surrogate* s, const double* 
     }
     if (loss_out) loss_out[ep] = nb ? lsum / nb : 0.0;
   }
-  return MDEOS_OK;
+  return take_tc_error(s, st);
 }
 
 // inference of B <= maxB inputs (device FP64 [B][2]) -> per-model s->Y and the ensemble
@@ -1101,10 +1172,18 @@ extern "C" mdeos_status mdeos_debug_gemm_bf16(const uint16_t* A, const uint16_t*
   if (!A || !B || !C || M < 1 || N < 1 || K < 1)
     return set_error(MDEOS_EINVAL, "bad gemm arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  SCK(gemm(st, reinterpret_cast<const __nv_bfloat16*>(A),
-           reinterpret_cast<const __nv_bfloat16*>(B), C, M, N, K, sa_m, sa_k, 0, sb_k, sb_n, 0,
-           sc_m, sc_n, 0, 1));
-  SCK(cudaStreamSynchronize(st));
+  int* err = nullptr;
+  SCK(cudaMallocAsync(&err, sizeof(int), st));
+  SCK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  cudaError_t e = gemm(st, err, reinterpret_cast<const __nv_bfloat16*>(A),
+                       reinterpret_cast<const __nv_bfloat16*>(B), C, M, N, K, sa_m, sa_k, 0, sb_k,
+                       sb_n, 0, sc_m, sc_n, 0, 1);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(err, st);
+  if (e != cudaSuccess) return set_error(MDEOS_ECUDA, cudaGetErrorString(e));
+  if (herr) return set_error(MDEOS_ETIMEDOUT, "gemm: a tensor-core wait ran out");
   return MDEOS_OK;
 }
 
