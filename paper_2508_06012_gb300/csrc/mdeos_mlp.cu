@@ -41,6 +41,11 @@ struct GemmArgs {
   float* C;
   int M, N, K;
   long long sa_m, sa_k, sa_z, sb_k, sb_n, sb_z, sc_m, sc_n, sc_z;
+  // split of K over S CTAs per tile (kchunk elements of K each, a multiple of the
+  // staged chunk): with S > 1 every CTA writes its partial tile to ws[s][z][m][n]
+  // (dense), summed in the order s = 0, 1, ... by gemm_splitk_reduce
+  int S, kchunk;
+  float* ws;
 };
 
 // ---------------------------------------------------------------------------
@@ -514,7 +519,9 @@ __global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* 
   __shared__ __align__(1024) unsigned char gsm[2 * kGTile];
   __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ uint32_t s_tmem;
-  const int z = blockIdx.z, m0 = blockIdx.y * kTcRows, n0 = blockIdx.x * kH;
+  const int z = blockIdx.z / g.S, sk = blockIdx.z - z * g.S;
+  const int m0 = blockIdx.y * kTcRows, n0 = blockIdx.x * kH;
+  const int kbeg = sk * g.kchunk, kend = min(g.K, kbeg + g.kchunk);  // this CTA's part of K
   const __nv_bfloat16* A = g.A + (long long)z * g.sa_z;
   const __nv_bfloat16* B = g.B + (long long)z * g.sb_z;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -543,21 +550,26 @@ __global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* 
                      ((uintptr_t)g.A & 15) == 0 && (g.K & 7) == 0;
   const bool b_vec = g.sb_k == 1 && (g.sb_n & 7) == 0 && (g.sb_z & 7) == 0 &&
                      ((uintptr_t)g.B & 15) == 0 && (g.K & 7) == 0;
-  for (int k0 = 0; k0 < g.K; k0 += kGK) {
+  for (int k0 = kbeg; k0 < kend; k0 += kGK) {
     if (a_vec) {
       for (int q = tid; q < kTcRows * (kGK / 8); q += kTcRows) {
         const int r = q & (kTcRows - 1), c = (q >> 7) * 8;  // consecutive threads: rows
         const int m = m0 + r, k = k0 + c;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (m < g.M && k < g.K) v = *reinterpret_cast<const uint4*>(A + (long long)m * g.sa_m + k);
+        if (m < g.M && k < kend) v = *reinterpret_cast<const uint4*>(A + (long long)m * g.sa_m + k);
         *reinterpret_cast<uint4*>(gsm + gk_off(r, c)) = v;
       }
-    } else {
-      for (int e = tid; e < kTcRows * kGK; e += kTcRows) {
-        const int r = e & (kTcRows - 1), c = e >> 7;  // consecutive threads: rows (M)
-        const int m = m0 + r, k = k0 + c;
-        *reinterpret_cast<__nv_bfloat16*>(gsm + gk_off(r, c)) =
-            (m < g.M && k < g.K) ? A[(long long)m * g.sa_m + (long long)k * g.sa_k] : zero;
+    } else {  // eight loads in flight per thread, then their stores
+      for (int c0 = 0; c0 < kGK; c0 += 8) {
+        const int r = tid, m = m0 + r;  // consecutive threads: rows (M)
+        __nv_bfloat16 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + c0 + u;
+          v[u] = (m < g.M && k < kend) ? A[(long long)m * g.sa_m + (long long)k * g.sa_k] : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) *reinterpret_cast<__nv_bfloat16*>(gsm + gk_off(r, c0 + u)) = v[u];
       }
     }
     if (b_vec) {
@@ -565,15 +577,21 @@ __global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* 
         const int r = q & (kTcRows - 1), c = (q >> 7) * 8;
         const int n = n0 + r, k = k0 + c;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (n < g.N && k < g.K) v = *reinterpret_cast<const uint4*>(B + (long long)n * g.sb_n + k);
+        if (n < g.N && k < kend) v = *reinterpret_cast<const uint4*>(B + (long long)n * g.sb_n + k);
         *reinterpret_cast<uint4*>(gsm + kGTile + gk_off(r, c)) = v;
       }
     } else {
-      for (int e = tid; e < kTcRows * kGK; e += kTcRows) {
-        const int r = e & (kTcRows - 1), c = e >> 7;  // consecutive threads: columns (N)
-        const int n = n0 + r, k = k0 + c;
-        *reinterpret_cast<__nv_bfloat16*>(gsm + kGTile + gk_off(r, c)) =
-            (n < g.N && k < g.K) ? B[(long long)k * g.sb_k + (long long)n * g.sb_n] : zero;
+      for (int c0 = 0; c0 < kGK; c0 += 8) {
+        const int r = tid, n = n0 + r;  // consecutive threads: columns (N)
+        __nv_bfloat16 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + c0 + u;
+          v[u] = (n < g.N && k < kend) ? B[(long long)k * g.sb_k + (long long)n * g.sb_n] : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          *reinterpret_cast<__nv_bfloat16*>(gsm + kGTile + gk_off(r, c0 + u)) = v[u];
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // tiles -> tensor core
@@ -583,7 +601,7 @@ __global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* 
 #pragma unroll
       for (int ks = 0; ks < kGK / 16; ++ks)  // K step of 16 = two core matrices along K
         tc_mma(tmem, gk_desc(sA + ks * 2 * kLbo), gk_desc(sB + ks * 2 * kLbo),
-               (k0 > 0 || ks > 0) ? 1u : 0u);
+               (k0 > kbeg || ks > 0) ? 1u : 0u);
       tc_commit(mbar);
     }
     __syncwarp();
@@ -596,7 +614,9 @@ __global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* 
   if (ok) {
     const int m = m0 + tid;
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    float* C = g.C + (long long)z * g.sc_z;
+    const int Z = gridDim.z / g.S;
+    float* C = g.S > 1 ? g.ws + ((long long)sk * Z + z) * g.M * g.N : g.C + (long long)z * g.sc_z;
+    const long long cm = g.S > 1 ? g.N : g.sc_m, cn = g.S > 1 ? 1 : g.sc_n;
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
       float v[32];
@@ -605,7 +625,7 @@ __global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* 
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c0 + j;
-          if (n < g.N) C[(long long)m * g.sc_m + (long long)n * g.sc_n] = v[j];
+          if (n < g.N) C[(long long)m * cm + (long long)n * cn] = v[j];
         }
     }
   } else {  // leave the tile unwritten; let the MMAs in flight finish (bounded)
@@ -618,6 +638,21 @@ __global__ void __launch_bounds__(kTcRows) bf16_gemm_tc_kernel(GemmArgs g, int* 
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kH)
                  : "memory");
+}
+
+// C[z](m, n) = sum over s = 0, 1, ..., S - 1 of the partial tiles ws[s][z][m][n]
+__global__ void gemm_splitk_reduce(const float* ws, float* C, int M, int N, int Z, int S,
+                                   long long sc_m, long long sc_n, long long sc_z) {
+  const long long per = (long long)M * N, all = per * Z;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < all;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int z = (int)(i / per);
+    const long long r = i - z * per;
+    const int m = (int)(r / N), n = (int)(r - (long long)m * N);
+    float acc = ws[i];
+    for (int s = 1; s < S; ++s) acc += ws[s * all + i];
+    C[z * sc_z + m * sc_m + n * sc_n] = acc;
+  }
 }
 
 __global__ void debug_tanh_kernel(const float* x, float* y, int n) {
@@ -642,6 +677,8 @@ struct mdeos_surrogate {
   float* loss = nullptr;
   double *Xp = nullptr, *mean = nullptr, *sd = nullptr;
   int* err = nullptr;  // set by the fused kernel when an MMA wait ran out
+  float* ws = nullptr;  // partial tiles of the products whose K is split
+  long long ws_elems = 0;
   int infer_path = MDEOS_SURROGATE_INFER_TC;
   bool tc_ready = false;
   int nsm = 1;
@@ -661,15 +698,37 @@ struct mdeos_surrogate {
       return set_error(MDEOS_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
   } while (0)
 
+constexpr int kMaxSplitK = 16;  // most CTAs one tile's K is split over
+
 // the training products: tcgen05 tiles of 128 x 128 (bf16_gemm_tc_kernel); a tensor-core
-// wait that ran out sets *err (device int) and leaves its tile unwritten
-static cudaError_t gemm(cudaStream_t st, int* err, const __nv_bfloat16* A,
-                        const __nv_bfloat16* B, float* C, int M, int N, int K, long long sa_m,
-                        long long sa_k, long long sa_z, long long sb_k, long long sb_n,
-                        long long sb_z, long long sc_m, long long sc_n, long long sc_z, int Z) {
-  GemmArgs g{A, B, C, M, N, K, sa_m, sa_k, sa_z, sb_k, sb_n, sb_z, sc_m, sc_n, sc_z};
-  dim3 grid((N + kH - 1) / kH, (M + kTcRows - 1) / kTcRows, Z);
+// wait that ran out sets *err (device int) and leaves its tile unwritten.  Products with
+// few tiles and a long K (the weight gradients, K = batch) split K over up to
+// kMaxSplitK CTAs per tile, at least two chunks each, when the workspace ws (ws_elems
+// floats) holds the partial tiles; the partials are summed in a fixed order, so every
+// result is the same from run to run.
+static cudaError_t gemm(cudaStream_t st, int* err, float* ws, long long ws_elems,
+                        const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N,
+                        int K, long long sa_m, long long sa_k, long long sa_z, long long sb_k,
+                        long long sb_n, long long sb_z, long long sc_m, long long sc_n,
+                        long long sc_z, int Z) {
+  const int tiles = ((N + kH - 1) / kH) * ((M + kTcRows - 1) / kTcRows) * Z;
+  const int nch = (K + kGK - 1) / kGK;
+  int S = 1, per = nch;
+  if (ws && tiles < 64 && nch >= 4) {
+    const int s0 = std::min(nch / 2, kMaxSplitK);
+    per = (nch + s0 - 1) / s0;
+    S = (nch + per - 1) / per;  // every split holds at least one chunk
+    if ((long long)S * Z * M * N > ws_elems) S = 1, per = nch;
+  }
+  GemmArgs g{A, B, C, M, N, K, sa_m, sa_k, sa_z, sb_k, sb_n, sb_z, sc_m, sc_n, sc_z,
+             S, per * kGK, S > 1 ? ws : nullptr};
+  dim3 grid((N + kH - 1) / kH, (M + kTcRows - 1) / kTcRows, Z * S);
   bf16_gemm_tc_kernel<<<grid, kTcRows, 0, st>>>(g, err);
+  if (S > 1) {
+    const long long all = (long long)Z * M * N;
+    gemm_splitk_reduce<<<(int)std::min<long long>((all + 255) / 256, 1024), 256, 0, st>>>(
+        ws, C, M, N, Z, S, sc_m, sc_n, sc_z);
+  }
   return cudaGetLastError();
 }
 
@@ -683,10 +742,10 @@ static cudaError_t forward(mdeos_surrogate* s, int B, const float* T, cudaStream
   cudaError_t e;
   mlp_layer1<<<nblk(EB * kH), 256, 0, st>>>(s->X, s->P, s->W1b, s->H1, B, E);
   // Z2 = H1 W2^T: A(m=b, k=j) = H1[b][j], B(k=j, n=o) = W2[o][j]
-  e = gemm(st, s->err, s->H1, s->W2b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->ws, s->ws_elems, s->H1, s->W2b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_bias_tanh<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->P, kOffB2, s->H2, B, E);
-  e = gemm(st, s->err, s->H2, s->W3b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->ws, s->ws_elems, s->H2, s->W3b, s->Z, B, kH, kH, kH, 1, sz, 1, kH, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_bias_tanh<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->P, kOffB3, s->H3, B, E);
   mlp_output<<<nblk(EB * 2), 256, 0, st>>>(s->H3, s->P, s->W4b, T, s->Y, s->dY, s->loss, B, E);
@@ -702,17 +761,17 @@ static cudaError_t backward(mdeos_surrogate* s, int B, cudaStream_t st) {
   mlp_back_out_w<<<nblk(E * (2 * kH + 2)), 256, 0, st>>>(s->dY, s->H3, s->G, B, E);
   mlp_back_out_dz<<<nblk(EB * kH), 256, 0, st>>>(s->dY, s->H3, s->W4b, s->dZb, B, E);
   // dW3 = dZ3^T H2: A(m=o, k=b) = dZ3[b][o], B(k=b, n=j) = H2[b][j]
-  e = gemm(st, s->err, s->dZb, s->H2, s->G + kOffW3, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
+  e = gemm(st, s->err, s->ws, s->ws_elems, s->dZb, s->H2, s->G + kOffW3, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
   if (e != cudaSuccess) return e;
   mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(s->dZb, nullptr, s->G, kOffB3, B, E);
   // dH2 = dZ3 W3: A(m=b, k=o) = dZ3[b][o], B(k=o, n=j) = W3[o][j]
-  e = gemm(st, s->err, s->dZb, s->W3b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->ws, s->ws_elems, s->dZb, s->W3b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_deriv<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->H2, s->dZb, nullptr, EB * kH);
-  e = gemm(st, s->err, s->dZb, s->H1, s->G + kOffW2, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
+  e = gemm(st, s->err, s->ws, s->ws_elems, s->dZb, s->H1, s->G + kOffW2, kH, kH, B, 1, kH, sz, kH, 1, sz, kH, 1, kNParam, E);
   if (e != cudaSuccess) return e;
   mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(s->dZb, nullptr, s->G, kOffB2, B, E);
-  e = gemm(st, s->err, s->dZb, s->W2b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
+  e = gemm(st, s->err, s->ws, s->ws_elems, s->dZb, s->W2b, s->Z, B, kH, kH, kH, 1, sz, kH, 1, kH * kH, kH, 1, sz, E);
   if (e != cudaSuccess) return e;
   mlp_deriv<<<nblk(EB * kH), 256, 0, st>>>(s->Z, s->H1, nullptr, s->dZf, EB * kH);
   mlp_bias_grad<<<nblk(E * kH), 256, 0, st>>>(nullptr, s->dZf, s->G, kOffB1, B, E);
@@ -769,6 +828,8 @@ extern "C" mdeos_status mdeos_surrogate_create(mdeos_handle* h, int32_t n_models
   dalloc((void**)&s->mean, (size_t)max_batch * 2 * 8);
   dalloc((void**)&s->sd, (size_t)max_batch * 2 * 8);
   dalloc((void**)&s->err, 256);
+  s->ws_elems = (long long)kMaxSplitK * E * kH * kH;
+  dalloc((void**)&s->ws, (size_t)s->ws_elems * 4);
   if (e != cudaSuccess) {
     mdeos_surrogate_destroy(s);
     return set_error(MDEOS_ECUDA, std::string("surrogate_create: ") + cudaGetErrorString(e));
@@ -1173,15 +1234,19 @@ extern "C" mdeos_status mdeos_debug_gemm_bf16(const uint16_t* A, const uint16_t*
     return set_error(MDEOS_EINVAL, "bad gemm arguments");
   cudaStream_t st = (cudaStream_t)stream;
   int* err = nullptr;
+  float* ws = nullptr;
+  const long long ws_elems = (long long)kMaxSplitK * M * N;
   SCK(cudaMallocAsync(&err, sizeof(int), st));
   SCK(cudaMemsetAsync(err, 0, sizeof(int), st));
-  cudaError_t e = gemm(st, err, reinterpret_cast<const __nv_bfloat16*>(A),
+  SCK(cudaMallocAsync(&ws, (size_t)ws_elems * 4, st));
+  cudaError_t e = gemm(st, err, ws, ws_elems, reinterpret_cast<const __nv_bfloat16*>(A),
                        reinterpret_cast<const __nv_bfloat16*>(B), C, M, N, K, sa_m, sa_k, 0, sb_k,
                        sb_n, 0, sc_m, sc_n, 0, 1);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(err, st);
+  cudaFreeAsync(ws, st);
   if (e != cudaSuccess) return set_error(MDEOS_ECUDA, cudaGetErrorString(e));
   if (herr) return set_error(MDEOS_ETIMEDOUT, "gemm: a tensor-core wait ran out");
   return MDEOS_OK;

@@ -40,8 +40,11 @@ def _bits(a):
     return torch.from_numpy(u.astype(np.uint16).view(np.int16).copy()).cuda()
 
 
+# (128, 128, 1024) and (100, 128, 1000) run with K split over several CTAs (few tiles,
+# long K), the second with a last split that ends inside a staged chunk
 @pytest.mark.parametrize("M,N,K,ta,tb", [(1, 1, 1, 0, 0), (64, 64, 32, 0, 1), (100, 70, 45, 1, 0),
-                                         (128, 128, 1024, 1, 0), (257, 128, 128, 0, 1)])
+                                         (128, 128, 1024, 1, 0), (257, 128, 128, 0, 1),
+                                         (100, 128, 1000, 1, 1)])
 def test_tensor_core_gemm(m, M, N, K, ta, tb):
     rng = np.random.default_rng(M + N + K)
     A = S.bf16(rng.standard_normal((M, K)))
@@ -55,6 +58,21 @@ def test_tensor_core_gemm(m, M, N, K, ta, tb):
     ref = A @ B
     bound = K * 2.0 ** -23 * (np.abs(A) @ np.abs(B)) + 1e-30
     assert (np.abs(C - ref) <= bound).all()
+
+
+def test_split_k_gemm_is_reproducible(m):
+    """The partial tiles of a split K are summed in a fixed order: the same product
+    twice gives the same bytes."""
+    rng = np.random.default_rng(7)
+    M, N, K = 128, 128, 2048
+    A = S.bf16(rng.standard_normal((K, M)))   # stored transposed, as the weight gradients
+    B = S.bf16(rng.standard_normal((K, N)))
+    c1 = m.mdeos_debug_gemm_bf16(_bits(A.ravel()), _bits(B.ravel()), M, N, K, (1, M), (N, 1), (N, 1))
+    c2 = m.mdeos_debug_gemm_bf16(_bits(A.ravel()), _bits(B.ravel()), M, N, K, (1, M), (N, 1), (N, 1))
+    assert c1.cpu().numpy().tobytes() == c2.cpu().numpy().tobytes()
+    ref = A.T @ B
+    bound = K * 2.0 ** -23 * (np.abs(A.T) @ np.abs(B)) + 1e-30
+    assert (np.abs(c1.cpu().numpy()[:M * N].reshape(M, N) - ref) <= bound).all()
 
 
 def test_hidden_layer_tanh_error_bound(m):
