@@ -957,12 +957,15 @@ def forcepass(args):
 
 
 def bigbox(args):
-    """Boxes above the shared-memory limit on their own: one box of --big-natoms atoms
-    per SM (state, cells and Verlet lists in global memory, positions staged in
-    shared-memory windows), one batch launch timed with CUDA events.  Algorithmic HBM
-    bytes per atom and step: the kick-drift reads x, v, f and writes x, v (80 B); the
-    force pass reads the positions (16 B, once per window) and the list entries (2 B
-    each) and writes f (16 B).  The dram counters of the same launch come from ncu."""
+    """Boxes above the shared-memory limit on their own: --big-boxes boxes of
+    --big-natoms atoms (default one per SM; state, cells and Verlet lists in global
+    memory, positions staged in shared-memory windows), one batch timed end to end.
+    Few boxes (fewer than half the SMs) run each on a thread-block cluster of up to
+    --max-cluster CTAs (default 4; 1: one CTA per box), which sets the latency of one
+    large box.  Algorithmic HBM bytes per atom and step: the kick-drift reads x, v, f
+    and writes x, v (80 B); the force pass reads the positions (16 B, once per window)
+    and the list entries (2 B each) and writes f (16 B).  The dram counters of the same
+    launch come from ncu."""
     import torch
 
     import paper_2508_06012_gb300 as m
@@ -975,8 +978,8 @@ def bigbox(args):
     reqs = [dict(rho=float(rng.uniform(0.7, 0.9)),
                  e=m.e_from_temperature(float(rng.uniform(1.2, 2.0)), n), natoms=n,
                  steps_equil=steps // 2, steps_avg=steps - steps // 2, seed=1000 + k)
-            for k in range(nsm)]
-    h = m.mdeos_create(m.mdeos_config_default(device=0))
+            for k in range(args.big_boxes or nsm)]
+    h = m.mdeos_create(m.mdeos_config_default(device=0, max_cluster=args.max_cluster))
     times = []
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
@@ -992,8 +995,9 @@ def bigbox(args):
     print(json.dumps({"metric": "in-cutoff pairs/s (boxes above the shared-memory limit)",
                       "value": pairs / t, "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1e3 * t,
-                      "config": {"workload": f"{nsm} LJ boxes of {n} atoms (one per SM), "
-                                             f"rho*~U[0.7,0.9], T*~U[1.2,2.0], {steps} MD steps"},
+                      "config": {"workload": f"{len(reqs)} LJ boxes of {n} atoms, "
+                                             f"rho*~U[0.7,0.9], T*~U[1.2,2.0], {steps} MD steps",
+                                 "max_cluster": args.max_cluster},
                       "boxes_ok": int(ok.sum()), "eos_per_s": float(ok.sum()) / t,
                       "box_latency_s": t, "algorithmic_hbm_bytes": alg_bytes,
                       "algorithmic_hbm_gbs": alg_bytes / t / 1e9,
@@ -1030,6 +1034,7 @@ def main():
                     help="forcepass: 0 forces, 1 forces + energy/virial, 2 list build")
     ap.add_argument("--fb-passes", type=int, default=5, help="forcepass: passes per launch")
     ap.add_argument("--big-natoms", type=int, default=32000, help="bigbox: atoms per box")
+    ap.add_argument("--big-boxes", type=int, default=0, help="bigbox: boxes (0: one per SM)")
     ap.add_argument("--max-cluster", type=int, default=0,
                     help="CTAs per box for batches of few small boxes (0: up to 4, 1: none)")
     ap.add_argument("--workload", choices=["uneven", "config1", "coupled", "serving",

@@ -364,6 +364,15 @@ static mdeos_status make_plan(const mdeos_request* reqs, int n, const mdeos_conf
       }
     }
   }
+  // Only boxes above the shared-memory limit, fewer than half the SMs: each on a
+  // cluster of CTAs sharing its global-memory state (a slab of slots per CTA), the
+  // same cluster size rule
+  const int nbig = (int)bp.size() - nsmall;
+  if (allow_cluster && nsmall == 0 && nbig > 0) {
+    int C = 1;
+    while (2 * C <= cmax && 2LL * (2 * C) * nbig <= nsm) C *= 2;
+    if (C > 1) plan.cluster = C;
+  }
   // size classes by (warps, apt); inside a class, sort by cost so an item's
   // boxes finish together
   std::sort(bp.begin(), bp.end(), [](const BoxPlan& a, const BoxPlan& b) {

@@ -57,11 +57,13 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
 
 // Cluster form for batches too small to fill the GPU: one box per thread-block
 // cluster of csize CTAs (cluster c runs item c, one box, the whole CTA as its group).
-// Every CTA holds the box and advances it alike; each computes the forces and lists
-// of its share of the atoms and sends the forces to the others (run_box with
-// Group::csize > 1).  All CTAs of a cluster take the same path through the box, so
-// they meet at the same cluster barriers; the last one below keeps every CTA alive
-// until no other can still store into its shared memory.
+// Shared-memory boxes: every CTA holds the box and advances it alike; each computes
+// the forces and lists of its share of the atoms and sends the forces to the others
+// (run_box with Group::csize > 1).  Boxes above the shared-memory limit: one state in
+// the scratch of the cluster's first CTA, each CTA owning a slab of its slots
+// (run_big with csize > 1).  All CTAs of a cluster take the same path through the
+// box, so they meet at the same cluster barriers; the last one below keeps every CTA
+// alive until no other can still store into its shared memory.
 __global__ void __launch_bounds__(kCtaThreads, 1)
     eos_cluster_kernel(const BoxDesc* __restrict__ boxes, const WorkItem* __restrict__ items,
                        int nitems, mdeos_result* __restrict__ results, uint16_t* nl_scratch,
@@ -70,7 +72,16 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   const int csize = cluster_size(), crank = cluster_rank();
   const int it = blockIdx.x / csize;
   uint16_t* nl_cta = nl_scratch + (long long)blockIdx.x * nl_elems_per_cta;
-  if (it < nitems) {
+  if (it < nitems && items[it].big) {
+    const BoxDesc& bd = boxes[items[it].box[0]];
+    uint16_t* box_scratch = nl_scratch + (long long)(blockIdx.x - crank) * nl_elems_per_cta;
+    run_big(reinterpret_cast<unsigned char*>(box_scratch), reinterpret_cast<BigShared*>(smem), bd,
+            rp, results + bd.out_index, crank, csize);
+    if (ready != nullptr && crank == 0 && threadIdx.x == 0) {
+      __threadfence_system();
+      reinterpret_cast<volatile int*>(ready)[bd.out_index] = 1;
+    }
+  } else if (it < nitems) {
     const WorkItem wi = items[it];
     const BoxDesc& bd = boxes[wi.box[0]];
     Group g = make_group(smem, threadIdx.x, wi.warps_per_box, wi.apt, wi.ncell_cap, 1, nl_cta);

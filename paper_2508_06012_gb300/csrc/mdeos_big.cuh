@@ -24,6 +24,7 @@ constexpr int kMaxRounds = 16;  // force-pass rounds of a big box (position wind
 
 struct BigShared {
   long long red[32 * kRedSlots];
+  long long clu[2 * kMaxCluster * kRedSlots];  // cluster partials, two alternating sets
   double bc[8];
   double acc[kAccDoubles];
   int bcnt[kMaxSeBlocks];
@@ -33,7 +34,80 @@ struct BigShared {
   int wsz[kMaxRounds];  // its length in slots (cyclic over the box)
   int nround;           // rounds (0: no shared-memory positions)
   int rsz;              // slots per round (a multiple of the CTA's threads)
+  int flag;             // a cluster-wide predicate, broadcast to the CTA
 };
+
+// A big box on a thread-block cluster of csize CTAs (csize 1: the whole box on one
+// CTA).  The box state stays in one global scratch; CTA crank owns the slots
+// [lo, hi), a contiguous part of the cell order (a slab of cells), and computes their
+// lists, forces and updates; cells are dealt to the cluster's threads.  A CTA reads
+// the slots of other CTAs from L2 only (its L1 never holds a line it did not write
+// through its own slots), and phases meet at cluster barriers (release/acquire).  Box
+// sums add the exact per-CTA partials in rank order, so every CTA holds the same
+// integers and takes the same decisions, and every result equals the one-CTA run.
+struct BigClu {
+  int crank, csize;
+  int lo, hi;  // the CTA's slots
+  int seq;     // cluster exchanges so far (picks the partials' set)
+};
+
+__device__ __forceinline__ BigClu big_clu(int n, int crank, int csize) {
+  BigClu c;
+  c.crank = crank;
+  c.csize = csize;
+  c.lo = (int)((long long)n * crank / csize);
+  c.hi = (int)((long long)n * (crank + 1) / csize);
+  c.seq = 0;
+  return c;
+}
+
+// barrier of the phases that read what other CTAs wrote
+__device__ __forceinline__ void big_bar(const BigClu& cl) {
+  if (cl.csize > 1)
+    cluster_sync();
+  else
+    __syncthreads();
+}
+
+// loads of slots that other CTAs may have written: L2 only in a cluster
+__device__ __forceinline__ float4 big_ld4(const float4* p, bool l2) { return l2 ? __ldcg(p) : *p; }
+__device__ __forceinline__ int big_ldi(const int* p, bool l2) { return l2 ? __ldcg(p) : *p; }
+__device__ __forceinline__ float big_ldw(const float4* p, bool l2) {
+  return l2 ? __ldcg(reinterpret_cast<const float*>(p) + 3) : p->w;
+}
+
+// Cluster totals of per-CTA totals held by lanes k < NQ of warp 0 (called by every
+// thread; the other lanes' values are ignored): every rank's partial goes into the
+// same slot of every CTA, then each CTA adds them in rank order.  The two sets
+// alternate, so a set is not written again before every CTA has passed the barrier
+// of the exchange in between.
+template <int NQ>
+__device__ __forceinline__ unsigned long long big_cluster_total(BigShared* sh, BigClu& cl,
+                                                                unsigned long long t) {
+  if (cl.csize == 1) return t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long* set = sh->clu + (cl.seq & 1) * (kMaxCluster * kRedSlots);
+  if (warp == 0 && lane < NQ) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(set + cl.crank * kRedSlots + lane);
+    for (int rk = 0; rk < cl.csize; ++rk) st_cluster_s64(cluster_map(a, rk), (long long)t);
+  }
+  cluster_sync();
+  ++cl.seq;
+  unsigned long long s = 0;
+  if (warp == 0 && lane < NQ)
+    for (int rk = 0; rk < cl.csize; ++rk) s += (unsigned long long)set[rk * kRedSlots + lane];
+  return s;
+}
+
+// a predicate ORed over every thread of the cluster
+__device__ __forceinline__ bool big_or(BigShared* sh, BigClu& cl, bool p) {
+  const bool any = __syncthreads_or(p) != 0;
+  if (cl.csize == 1) return any;
+  const unsigned long long t = big_cluster_total<1>(sh, cl, any ? 1ull : 0ull);
+  if (threadIdx.x == 0) sh->flag = t != 0;
+  __syncthreads();
+  return sh->flag != 0;
+}
 
 static_assert(sizeof(BigShared) <= kBigSharedBytes, "big-box shared memory");
 
@@ -46,6 +120,8 @@ struct BigMem {
   int sx_cap;     // their capacity in atoms
   int nround, rsz;           // force-pass rounds from the last build (0: none)
   const int *wlo, *wsz;      // their windows (shared memory)
+  int lo, hi;                // this CTA's slots
+  bool l2;                   // other CTAs write the box too: read their slots from L2
 };
 
 // Position windows in the dynamic shared memory from offset `off` on: address and
@@ -58,8 +134,11 @@ __device__ __forceinline__ void big_pos_cache(BigMem& m, const unsigned char* dy
   m.sx_cap = cap >= 1024 ? cap : 0;
 }
 
-__device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
+__device__ inline BigMem big_mem(unsigned char* p, int n, int ncell, const BigClu& cl) {
   BigMem m;
+  m.lo = cl.lo;
+  m.hi = cl.hi;
+  m.l2 = cl.csize > 1;
   m.cap = big_cap(n);
   float4* q = reinterpret_cast<float4*>(p);
   m.x = q;
@@ -79,10 +158,10 @@ __device__ inline BigMem big_mem(unsigned char* p, int n, int ncell) {
   return m;
 }
 
-// Sum NQ per-thread fixed-point values (fxp units) over the CTA exactly; every
-// thread gets the totals as FP64 in real units.
+// Sum NQ per-thread fixed-point values (fxp units) over the CTA (and the cluster)
+// exactly; every thread gets the totals as FP64 in real units.
 template <int NQ>
-__device__ void block_sum(BigShared* sh, const long long (&q)[NQ], double (&out)[NQ]) {
+__device__ void block_sum(BigShared* sh, BigClu& cl, const long long (&q)[NQ], double (&out)[NQ]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
@@ -90,11 +169,11 @@ __device__ void block_sum(BigShared* sh, const long long (&q)[NQ], double (&out)
     if (lane == 0) sh->red[warp * kRedSlots + k] = s;
   }
   __syncthreads();
-  if (warp == 0 && lane < NQ) {
-    unsigned long long s = 0;
+  unsigned long long s = 0;
+  if (warp == 0 && lane < NQ)
     for (int w = 0; w < nw; ++w) s += (unsigned long long)sh->red[w * kRedSlots + lane];
-    sh->bc[lane] = (double)(long long)s * kFixInv;
-  }
+  s = big_cluster_total<NQ>(sh, cl, s);
+  if (warp == 0 && lane < NQ) sh->bc[lane] = (double)(long long)s * kFixInv;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NQ; ++k) out[k] = sh->bc[k];
@@ -104,7 +183,7 @@ __device__ void block_sum(BigShared* sh, const long long (&q)[NQ], double (&out)
 __device__ inline void big_lattice(const BigMem& m, const BoxDesc& bd) {
   const int nc = bd.nc_lat;
   const double a = bd.L / nc;
-  for (int i = threadIdx.x; i < bd.natoms; i += blockDim.x) {
+  for (int i = m.lo + threadIdx.x; i < m.hi; i += blockDim.x) {
     const int c = i >> 2, bb = i & 3;
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     const double bx = (bb == 1 || bb == 2) ? 0.5 : 0.0;
@@ -116,8 +195,8 @@ __device__ inline void big_lattice(const BigMem& m, const BoxDesc& bd) {
   }
 }
 
-__device__ inline void big_wrap(const BigMem& m, int n, float L, float invL) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+__device__ inline void big_wrap(const BigMem& m, float L, float invL) {
+  for (int i = m.lo + threadIdx.x; i < m.hi; i += blockDim.x) {
     float4 xi = m.x[i];
     xi.x -= L * floorf(xi.x * invL);
     xi.y -= L * floorf(xi.y * invL);
@@ -132,24 +211,29 @@ __device__ inline void big_wrap(const BigMem& m, int n, float L, float invL) {
 
 // Verlet list from wrapped positions: counting sort into cell order (inside a
 // cell by previous slot: deterministic), permutation of x and v into the second
-// buffers (then swapped), 27-cell search with one image shift per cell.
-static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float L, float cinv, float rs2,
-                          int maxnb) {
+// buffers (then swapped), 27-cell search with one image shift per cell.  In a
+// cluster: cells are dealt to the cluster's threads, slots to their owners, the
+// prefix sum over the cells is rank 0's, and each phase ends at a cluster barrier.
+// Returns whether a list overflowed anywhere in the cluster.
+static __device__ bool big_build(BigMem& m, BigShared* sh, BigClu& cl, int n, int nc, float L,
+                                 float cinv, float rs2, int maxnb) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int gt = cl.crank * nt + tid, gn = cl.csize * nt;  // the thread among the cluster's
+  const bool l2 = m.l2;
   const int ncell = nc * nc * nc;
-  for (int c = tid; c < ncell; c += nt) m.cnt[c] = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) {
+  for (int c = gt; c < ncell; c += gn) m.cnt[c] = 0;
+  big_bar(cl);
+  for (int i = m.lo + tid; i < m.hi; i += nt) {
     const int c = cell_of(m.x[i], cinv, nc);
     m.f[i].x = __int_as_float(c);
     atomicAdd(&m.cnt[c], 1);
   }
-  __syncthreads();
-  {  // exclusive scan of the counts into starts; counts become insertion cursors
+  big_bar(cl);
+  if (cl.crank == 0) {  // exclusive scan of the counts into starts; counts become cursors
     const int per = (ncell + nt - 1) / nt;
     const int lo = min(tid * per, ncell), hi = min(lo + per, ncell);
     int s = 0;
-    for (int c = lo; c < hi; ++c) s += m.cnt[c];
+    for (int c = lo; c < hi; ++c) s += big_ldi(m.cnt + c, l2);
     const int lane = tid & 31, warp = tid >> 5;
     int incl = s;
 #pragma unroll
@@ -171,41 +255,42 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
     __syncthreads();
     int off = (warp > 0 ? sh->scan[warp - 1] : 0) + incl - s;
     for (int c = lo; c < hi; ++c) {
-      const int k = m.cnt[c];
+      const int k = big_ldi(m.cnt + c, l2);
       m.start[c] = off;
       off += k;
       m.cnt[c] = 0;
     }
     if (tid == 0) m.start[ncell] = n;
   }
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) {
+  big_bar(cl);
+  for (int i = m.lo + tid; i < m.hi; i += nt) {
     const int c = __float_as_int(m.f[i].x);
-    const int s = m.start[c] + atomicAdd(&m.cnt[c], 1);
+    const int s = big_ldi(m.start + c, l2) + atomicAdd(&m.cnt[c], 1);
     reinterpret_cast<float*>(m.x2 + s)[3] = __int_as_float(i);
   }
-  __syncthreads();
-  for (int c = tid; c < ncell; c += nt) {  // insertion sort of the previous slots
-    const int lo = m.start[c], hi = m.start[c + 1];
+  big_bar(cl);
+  for (int c = gt; c < ncell; c += gn) {  // insertion sort of the previous slots
+    const int lo = big_ldi(m.start + c, l2), hi = big_ldi(m.start + c + 1, l2);
     for (int a = lo + 1; a < hi; ++a) {
-      const float key = m.x2[a].w;
+      const float key = big_ldw(m.x2 + a, l2);
       const int kk = __float_as_int(key);
       int b = a - 1;
-      while (b >= lo && __float_as_int(m.x2[b].w) > kk) {
-        reinterpret_cast<float*>(m.x2 + b + 1)[3] = m.x2[b].w;
+      float wb;
+      while (b >= lo && __float_as_int(wb = big_ldw(m.x2 + b, l2)) > kk) {
+        reinterpret_cast<float*>(m.x2 + b + 1)[3] = wb;
         --b;
       }
       reinterpret_cast<float*>(m.x2 + b + 1)[3] = key;
     }
   }
-  __syncthreads();
-  for (int s = tid; s < n; s += nt) {
-    const int i = __float_as_int(m.x2[s].w);
-    m.x2[s] = m.x[i];
-    const float4 vi = m.v[i];
+  big_bar(cl);
+  for (int s = m.lo + tid; s < m.hi; s += nt) {
+    const int i = __float_as_int(big_ldw(m.x2 + s, l2));
+    m.x2[s] = big_ld4(m.x + i, l2);
+    const float4 vi = big_ld4(m.v + i, l2);
     m.v2[s] = make_float4(vi.x, vi.y, vi.z, 0.f);
   }
-  __syncthreads();
+  big_bar(cl);
   {
     float4* t = m.x;
     m.x = m.x2;
@@ -214,30 +299,31 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
     m.v = m.v2;
     m.v2 = t;
   }
-  // Force-pass rounds: slots [q rsz, (q + 1) rsz) lie in cell layers z0..z1 (cells
-  // are z-major), so their neighbours lie in layers z0 - 1 .. z1 + 1 (cyclic; a
-  // neighbour across the y or x boundary can be anywhere in its layer).  The slots of
-  // those whole layers (contiguous, cyclic over the box) are the round's position
-  // window.  The fewest rounds whose windows all fit the shared memory; none if even
-  // kMaxRounds do not.  List entries are stored relative to the window start, so the
-  // pass indexes the window directly.
+  // Force-pass rounds over the CTA's slots: slots [lo + q rsz, lo + (q + 1) rsz) lie
+  // in cell layers z0..z1 (cells are z-major), so their neighbours lie in layers
+  // z0 - 1 .. z1 + 1 (cyclic; a neighbour across the y or x boundary can be anywhere in
+  // its layer).  The slots of those whole layers (contiguous, cyclic over the box) are
+  // the round's position window.  The fewest rounds whose windows all fit the shared
+  // memory; none if even kMaxRounds do not.  List entries are stored relative to the
+  // window start, so the pass indexes the window directly.
+  const int own = m.hi - m.lo;
   if (tid == 0) {
     sh->nround = 0;
-    sh->rsz = n;
-    if (m.sx_cap > 0) {
+    sh->rsz = own;
+    if (m.sx_cap > 0 && own > 0) {
       const int nc2 = nc * nc;
       for (int R = 1; R <= kMaxRounds; ++R) {
-        const int rsz = ((n + R - 1) / R + nt - 1) / nt * nt;
-        const int nr = (n + rsz - 1) / rsz;
+        const int rsz = ((own + R - 1) / R + nt - 1) / nt * nt;
+        const int nr = (own + rsz - 1) / rsz;
         bool fits = true;
         for (int q = 0; q < nr && fits; ++q) {
-          const int s0 = q * rsz, s1 = min(n, s0 + rsz) - 1;
+          const int s0 = m.lo + q * rsz, s1 = min(m.hi, s0 + rsz) - 1;
           const int z0 = cell_of(m.x[s0], cinv, nc) / nc2, z1 = cell_of(m.x[s1], cinv, nc) / nc2;
           int lo = 0, sz = n;
           if (z1 - z0 + 3 < nc) {
             const int lz = (z0 - 1 + nc) % nc, hz = (z1 + 1) % nc;
-            lo = m.start[lz * nc2];
-            const int hi = m.start[(hz + 1) * nc2];
+            lo = big_ldi(m.start + lz * nc2, l2);
+            const int hi = big_ldi(m.start + (hz + 1) * nc2, l2);
             sz = lz <= hz ? hi - lo : (n - lo) + hi;
           }
           fits = sz <= m.sx_cap;
@@ -266,13 +352,13 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
   const bool win = m.nround > 0;
   for (int q = 0; q < (win ? m.nround : 1); ++q) {
     const int wl = win ? m.wlo[q] : 0, ws = win ? m.wsz[q] : n;
-    const int sb = win ? q * m.rsz : 0, se = win ? min(n, sb + m.rsz) : n;
+    const int sb = win ? m.lo + q * m.rsz : m.lo, se = win ? min(m.hi, sb + m.rsz) : m.hi;
     if (win) {
       float4* sx = reinterpret_cast<float4*>(__cvta_shared_to_generic(m.sx_a));
       for (int k = tid; k < ws; k += nt) {
         int g = wl + k;
         if (g >= n) g -= n;
-        sx[k] = m.x[g];
+        sx[k] = big_ld4(m.x + g, l2);
       }
       __syncthreads();
     }
@@ -302,7 +388,7 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
             float sx_ = 0.f;
             if (xx < 0) { xx += nc; sx_ = -L; } else if (xx >= nc) { xx -= nc; sx_ = L; }
             const int c = (zz * nc + yy) * nc + xx;
-            const int j0 = m.start[c], j1 = m.start[c + 1];
+            const int j0 = big_ldi(m.start + c, l2), j1 = big_ldi(m.start + c + 1, l2);
             int jb = j0 - wl;  // window index of the cell's first slot
             if (jb < 0) jb += n;
             if (jb + (j1 - j0) > ws) {
@@ -311,7 +397,7 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
             }
             for (int j = j0; j < j1; ++j) {
               const int e = jb + (j - j0);  // window-relative slot (= j without windows)
-              const float4 xj = win ? ld_shared4(m.sx_a + 16u * (uint32_t)e) : m.x[j];
+              const float4 xj = win ? ld_shared4(m.sx_a + 16u * (uint32_t)e) : big_ld4(m.x + j, l2);
               const float ddx = xi.x - (xj.x + sx_), ddy = xi.y - (xj.y + sy), ddz = xi.z - (xj.z + sz);
               const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
               if (j != s && r2 < rs2) {
@@ -328,6 +414,11 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
     if (win) __syncthreads();  // before the next window overwrites this one
   }
   __syncthreads();
+  // a list overflow anywhere ends the box in every CTA alike
+  const bool ovf = big_or(sh, cl, sh->ctrl[CTRL_OVERFLOW] != 0);
+  if (tid == 0) sh->ctrl[CTRL_OVERFLOW] = ovf ? 1 : 0;
+  __syncthreads();
+  return ovf;
 }
 
 // Forces on every atom (strided over the CTA) from the Verlet list, minimum image
@@ -342,7 +433,7 @@ static __device__ void big_build(BigMem& m, BigShared* sh, int n, int nc, float 
 template <bool EN, bool VIR, bool CNT, bool SM>
 __device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, int s0, int s1,
                                              int wl, float4* f, const uint4* nl, int cap, int n,
-                                             float L, float invL, LJ c) {
+                                             float L, float invL, bool l2, LJ c) {
   unsigned long long es = 0, ws[6] = {0, 0, 0, 0, 0, 0};
   int np = 0, bad = 0;
 #pragma unroll 1
@@ -372,7 +463,7 @@ __device__ __noinline__ FSums big_force_pass(const float4* x, uint32_t sx_a, int
         const int jj = (int)((wd >> (16 * (u & 1))) & 0xffffu);
         const bool ok = u < left;
         const int jr = ok ? jj : si;
-        const float4 xj = SM ? ld_shared4(sx_a + 16u * (uint32_t)jr) : x[jr];
+        const float4 xj = SM ? ld_shared4(sx_a + 16u * (uint32_t)jr) : big_ld4(x + jr, l2);
         const float dx = min_img(xi.x - xj.x, L, invL);
         const float dy = min_img(xi.y - xj.y, L, invL);
         const float dz = min_img(xi.z - xj.z, L, invL);
@@ -420,8 +511,8 @@ __device__ inline BigCtx make_big_ctx(const BoxDesc& bd, const RunParams& rp) {
 template <bool EN, bool VIR, bool CNT>
 __device__ __forceinline__ FSums big_forces_t(const BigMem& m, const BigCtx& b, const LJ& c) {
   if (m.nround == 0)
-    return big_force_pass<EN, VIR, CNT, false>(m.x, 0u, 0, b.n, 0, m.f, m.nl, m.cap, b.n, b.L,
-                                               b.invL, c);
+    return big_force_pass<EN, VIR, CNT, false>(m.x, 0u, m.lo, m.hi, 0, m.f, m.nl, m.cap, b.n, b.L,
+                                               b.invL, m.l2, c);
   FSums t = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   float4* sx = reinterpret_cast<float4*>(__cvta_shared_to_generic(m.sx_a));
   for (int q = 0; q < m.nround; ++q) {
@@ -429,12 +520,12 @@ __device__ __forceinline__ FSums big_forces_t(const BigMem& m, const BigCtx& b, 
     for (int k = threadIdx.x; k < ws; k += blockDim.x) {
       int g = wl + k;
       if (g >= b.n) g -= b.n;
-      sx[k] = m.x[g];
+      sx[k] = big_ld4(m.x + g, m.l2);
     }
     __syncthreads();
-    const int s0 = q * m.rsz, s1 = min(b.n, s0 + m.rsz);
+    const int s0 = m.lo + q * m.rsz, s1 = min(m.hi, s0 + m.rsz);
     const FSums r = big_force_pass<EN, VIR, CNT, true>(m.x, m.sx_a, s0, s1, wl, m.f, m.nl, m.cap,
-                                                       b.n, b.L, b.invL, c);
+                                                       b.n, b.L, b.invL, m.l2, c);
     __syncthreads();
     t.e += r.e;
     t.w0 += r.w0;
@@ -459,13 +550,13 @@ __device__ __forceinline__ FSums big_forces(const BigMem& m, const BigCtx& b, co
 // Maxwell velocities at T (Eq. 9): Philox keyed by the seed, counter = atom id,
 // FP64 Box-Muller, mean removed, exact rescale to T; same arithmetic as
 // init_velocities with the intermediate values kept in v instead of registers.
-static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, int n, unsigned long long seed,
-                                    double T, const RunParams& rp) {
+static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, BigClu& cl, int n,
+                                           unsigned long long seed, double T, const RunParams& rp) {
   const uint32_t k0 = (uint32_t)(seed & 0xffffffffull), k1 = (uint32_t)(seed >> 32);
   const double sd = sqrt(T / rp.mass);
   const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
   long long p[3] = {0, 0, 0};
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+  for (int s = m.lo + threadIdx.x; s < m.hi; s += blockDim.x) {
     const uint32_t id = (uint32_t)__float_as_int(m.x[s].w);
     uint32_t c[4] = {id, 0u, 0u, 0u};
     philox4x32_10(c, k0, k1);
@@ -482,10 +573,10 @@ static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, int n
     p[2] += fxp(vz);
   }
   double ptot[3];
-  block_sum<3>(sh, p, ptot);
+  block_sum<3>(sh, cl, p, ptot);
   const float mx = (float)(ptot[0] / n), my = (float)(ptot[1] / n), mz = (float)(ptot[2] / n);
   long long ke[1] = {0};
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+  for (int s = m.lo + threadIdx.x; s < m.hi; s += blockDim.x) {
     float4 vi = m.v[s];
     vi.x -= mx;
     vi.y -= my;
@@ -494,10 +585,10 @@ static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, int n
     ke[0] += fxp(vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
   }
   double ketot[1];
-  block_sum<1>(sh, ke, ketot);
+  block_sum<1>(sh, cl, ke, ketot);
   const double Tinst = rp.mass * ketot[0] / (3.0 * n - 3.0);
   const float lam = (float)sqrt(T / Tinst);
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+  for (int s = m.lo + threadIdx.x; s < m.hi; s += blockDim.x) {
     const float4 vi = m.v[s];
     m.v[s] = make_float4(lam * vi.x, lam * vi.y, lam * vi.z, 0.f);
   }
@@ -508,7 +599,7 @@ static __device__ void big_init_velocities(const BigMem& m, BigShared* sh, int n
 __device__ __forceinline__ bool big_kick_drift(const BigMem& m, const BigCtx& b,
                                                const RunParams& rp, float lam) {
   bool need = false;
-  for (int s = threadIdx.x; s < b.n; s += blockDim.x) {
+  for (int s = m.lo + threadIdx.x; s < m.hi; s += blockDim.x) {
     const float4 fi = m.f[s];
     float4 vi = m.v[s];
     vi.x = fmaf(lam, vi.x, rp.hdtm * fi.x);
@@ -526,14 +617,19 @@ __device__ __forceinline__ bool big_kick_drift(const BigMem& m, const BigCtx& b,
   return need;
 }
 
-// One big box, start to finish (same schedule and accumulation as run_box).
+// One big box, start to finish (same schedule and accumulation as run_box), on this
+// CTA or on the csize CTAs of its thread-block cluster (rank crank; every CTA passes
+// the scratch of the cluster's box, and all take the same path through it, so they
+// meet at the same cluster barriers).  Rank 0 writes the result.
 static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* sh, const BoxDesc& bd,
-                                     const RunParams& rp, mdeos_result* out) {
+                                            const RunParams& rp, mdeos_result* out, int crank = 0,
+                                            int csize = 1) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = nt >> 5;
   const BigCtx b = make_big_ctx(bd, rp);
   const LJ lj = make_lj(rp);
-  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  BigClu cl = big_clu(b.n, crank, csize);
+  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc, cl);
   // position windows in the CTA's otherwise idle shared memory, behind BigShared
   big_pos_cache(m, reinterpret_cast<const unsigned char*>(sh), kBigSharedBytes);
   const int n = b.n;
@@ -545,15 +641,15 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   for (int k = tid; k < kAccDoubles; k += nt) acc[k] = 0.0;
   for (int k = tid; k < kMaxSeBlocks; k += nt) sh->bcnt[k] = 0;
   big_lattice(m, bd);
-  __syncthreads();
-  big_build(m, sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+  big_bar(cl);
+  big_build(m, sh, cl, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
   int builds = 1;
   double E_cold;
   {
     const FSums r = big_forces(m, b, lj, true, false);
     const long long q[1] = {(long long)r.e};
     double et[1];
-    block_sum<1>(sh, q, et);
+    block_sum<1>(sh, cl, q, et);
     E_cold = et[0];
   }
   double* boxc = acc + ACC_BOX;
@@ -576,7 +672,7 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   int nsamp = max(1, (seg_len + 9) / 10);
   const int total = bd.steps_equil + bd.steps_avg;
   const int nb = rp.se_blocks;
-  if (status == MDEOS_OK) big_init_velocities(m, sh, n, bd.seed, Tk, rp);
+  if (status == MDEOS_OK) big_init_velocities(m, sh, cl, n, bd.seed, Tk, rp);
   const double invV = 1.0 / V, inv3V = 1.0 / (3.0 * V), inv_ndof = 1.0 / ndof;
   float lam = 1.0f;
   for (int step = 0; step < total && status == MDEOS_OK; ++step) {
@@ -585,7 +681,7 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
     const bool seg_end = !avg && (seg_pos == seg_len - 1);
     const bool esamp = !avg && !temp_mode && (seg_pos >= seg_len - nsamp);
     const bool need = big_kick_drift(m, b, rp, lam);
-    const bool rebuild = __syncthreads_or(need) != 0;
+    const bool rebuild = big_or(sh, cl, need);  // also publishes the new positions
     {
       // written by warp 0 last step (non-finite state): stop before a rebuild
       // bins such positions into cells
@@ -596,11 +692,11 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
       }
     }
     if (rebuild) {
-      big_wrap(m, n, b.L, b.invL);
-      __syncthreads();
-      big_build(m, sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+      big_wrap(m, b.L, b.invL);
+      big_bar(cl);
+      const bool ovf = big_build(m, sh, cl, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
       ++builds;
-      if (sh->ctrl[CTRL_OVERFLOW] != 0) {
+      if (ovf) {
         status = MDEOS_ENBR;
         break;
       }
@@ -610,7 +706,7 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
     unsigned long long ke = 0, kt[6] = {0, 0, 0, 0, 0, 0};
     int cand = 0;
     bool bad = r.bad != 0;
-    for (int s = tid; s < n; s += nt) {
+    for (int s = m.lo + tid; s < m.hi; s += nt) {
       const float4 fi = m.f[s];
       float4 vi = m.v[s];
       vi.x = fmaf(rp.hdtm, fi.x, vi.x);
@@ -662,10 +758,14 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
                        (seg_pos + 1) % rp.rescale_every_equil == 0) ||
                       (avg && rp.rescale_every_avg > 0 && (s_avg + 1) % rp.rescale_every_avg == 0);
     __syncthreads();
+    // box sums of the step: exact sums of the warp partials (lane k of warp 0 holds
+    // quantity k), over the cluster's CTAs in rank order; the thermostat's kinetic
+    // temperature comes from the same sum
+    unsigned long long qsum = 0;
+    if (warp == 0) qsum = (unsigned long long)warp_partials_ll(sh->red, nwarps, lane);
+    qsum = big_cluster_total<kRedSlots>(sh, cl, qsum);
     if (warp == 0) {
-      // box sums of the step: exact sums of the warp partials (lane k holds
-      // quantity k); the thermostat's kinetic temperature comes from the same sum
-      const long long qi = warp_partials_ll(sh->red, nwarps, lane);
+      const long long qi = (long long)qsum;
       const double q = lane < 8 ? (double)qi * kFixInv : (double)qi;
       const double s0 = __shfl_sync(0xffffffffu, q, 0), s1 = __shfl_sync(0xffffffffu, q, 1);
       const double s2 = __shfl_sync(0xffffffffu, q, 2), k7 = __shfl_sync(0xffffffffu, q, 7);
@@ -728,7 +828,7 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   }
   __syncthreads();
   if (status == MDEOS_OK && sh->ctrl[CTRL_STATUS] != 0) status = sh->ctrl[CTRL_STATUS];
-  if (tid == 0) {
+  if (tid == 0 && cl.crank == 0) {
     const double m_ = bd.steps_avg;
     mdeos_result res;
     for (int k = 0; k < 6; ++k) res.sigma[k] = acc[ACC_RUN + k] / m_;
@@ -772,7 +872,7 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
     }
     *out = res;
   }
-  __syncthreads();
+  big_bar(cl);  // no CTA leaves while another may still store into its shared memory
 }
 
 }  // namespace mdeos

@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                             float4* f4, double* ew, long long* pairs) {
   __shared__ BigShared sh;
   const BigCtx b = make_big_ctx(bd, rp);
-  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  BigClu cl = big_clu(b.n, 0, 1);
+  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc, cl);
   extern __shared__ __align__(128) unsigned char dyn[];
   big_pos_cache(m, dyn, 0);  // position windows, as in the batch kernel
   if (threadIdx.x < 16) sh.ctrl[threadIdx.x] = 0;
@@ -354,9 +355,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     m.v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  big_wrap(m, b.n, b.L, b.invL);
+  big_wrap(m, b.L, b.invL);
   __syncthreads();
-  big_build(m, &sh, b.n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+  big_build(m, &sh, cl, b.n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
   // forces use the positions as given (the list came from the wrapped ones)
   for (int s = threadIdx.x; s < b.n; s += blockDim.x) {
     const float4 xo = m.x[s];
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                           (long long)r.w3, (long long)r.w4, (long long)r.w5,
                           (long long)r.np * 4294967296LL};
   double out[8];
-  block_sum<8>(&sh, q, out);
+  block_sum<8>(&sh, cl, q, out);
   if (threadIdx.x == 0) {
     for (int k = 0; k < 7; ++k) ew[k] = out[k];
     if (pairs) pairs[0] = (long long)llrint(out[7]);
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   extern __shared__ __align__(128) unsigned char dyn[];
   const BigCtx b = make_big_ctx(bd, rp);
   const LJ lj = make_lj(rp);
-  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc);
+  BigClu cl = big_clu(b.n, 0, 1);
+  BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc, cl);
   big_pos_cache(m, dyn, 0);  // position windows, as in the batch kernel
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
@@ -398,17 +400,17 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     m.v[s] = make_float4(vi.x, vi.y, vi.z, 0.f);
   }
   __syncthreads();
-  big_wrap(m, n, b.L, b.invL);
+  big_wrap(m, b.L, b.invL);
   __syncthreads();
-  big_build(m, &sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+  big_build(m, &sh, cl, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
   big_forces(m, b, lj, false, false);
   __syncthreads();
   for (int st = 0; st < steps; ++st) {
     const bool need = big_kick_drift(m, b, rp, 1.0f);
     if (__syncthreads_or(need)) {
-      big_wrap(m, n, b.L, b.invL);
+      big_wrap(m, b.L, b.invL);
       __syncthreads();
-      big_build(m, &sh, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
+      big_build(m, &sh, cl, n, b.nc, b.L, b.cinv, b.rs2, b.maxnb);
       ++nbuild;
     }
     const FSums r = big_forces(m, b, lj, true, false);
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     }
     const long long q[2] = {(long long)r.e, ke};
     double tot[2];
-    block_sum<2>(&sh, q, tot);
+    block_sum<2>(&sh, cl, q, tot);
     if (threadIdx.x == 0) {
       if (epot) epot[st] = tot[0];
       if (ekin) ekin[st] = tot[1];
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     }
     __syncthreads();
   }
-  big_wrap(m, n, b.L, b.invL);
+  big_wrap(m, b.L, b.invL);
   __syncthreads();
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     const float4 xi = m.x[s], vi = m.v[s];

@@ -91,3 +91,58 @@ def test_cluster_warm_start_and_overflow(m):
         assert (ra["nlist_retries"] > 0).any() and (ra["status"] == 0).all()
         for f in ("P", "T", "e_achieved", "sigma", "status", "nlist_builds"):
             assert np.array_equal(ra[f], rb[f]), f
+
+
+def _big(count, natoms=(5000, 9000, 16384), steps=(40, 40), seed0=0):
+    rng = np.random.default_rng(31 + seed0)
+    out = []
+    for k in range(count):
+        n = int(natoms[k % len(natoms)])
+        out.append(dict(rho=float(rng.uniform(0.5, 1.0)), e=float(rng.uniform(0.5, 1.5)),
+                        natoms=n, steps_equil=steps[0], steps_avg=steps[1], seed=700 + seed0 + k))
+    return out
+
+
+def test_big_boxes_on_clusters_equal_one_cta(m):
+    """Boxes above the shared-memory limit on clusters of 4 and 8 CTAs (each CTA a slab
+    of the cell-ordered slots, box sums exchanged in rank order) give the bytes of the
+    same boxes on one CTA each (max_cluster = 1: no clusters)."""
+    reqs = _big(3)
+    with m.Engine(max_cluster=1) as one, m.Engine() as four, m.Engine(max_cluster=8) as eight:
+        r1 = one.evaluate(reqs)
+        r4 = four.evaluate(reqs)
+        r8 = eight.evaluate(reqs)
+    assert (r1["status"] == 0).all() and (r1["nlist_builds"] > 1).all()
+    assert r4.tobytes() == r1.tobytes()
+    assert r8.tobytes() == r1.tobytes()
+
+
+def test_big_cluster_plan_shape_and_overflow(m):
+    """The batch API reports 2 big boxes as 2 clusters of 4; a list overflow on a
+    clustered big box ends it in every CTA alike and the re-planned run equals the
+    one-CTA run."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    reqs = _big(2, natoms=(6000, 7000), steps=(20, 20), seed0=50)
+    h = m.mdeos_create()
+    try:
+        b = m.mdeos_batch_create(h, reqs)
+        info = m.mdeos_batch_info(b)
+        C = 1
+        while 2 * C <= 4 and 2 * (2 * C) * 2 <= nsm:
+            C *= 2
+        assert info["items"] == 2 and info["ctas"] == 2 * C
+        m.mdeos_batch_launch(b)
+        r = m.mdeos_batch_results(b, 2)
+        m.mdeos_batch_destroy(b)
+    finally:
+        m.mdeos_destroy(h)
+    with m.Engine(max_cluster=1) as one:
+        ref = one.evaluate(reqs)
+    assert (r["status"] == 0).all() and r.tobytes() == ref.tobytes()
+    with m.Engine(nlist_capacity=16) as a, m.Engine(nlist_capacity=16, max_cluster=1) as b1:
+        ra = a.evaluate(reqs)
+        rb = b1.evaluate(reqs)
+    assert (ra["nlist_retries"] > 0).all() and (ra["status"] == 0).all()
+    for f in ("P", "T", "e_achieved", "sigma", "status", "nlist_builds"):
+        assert np.array_equal(ra[f], rb[f]), f
