@@ -87,7 +87,7 @@ typedef struct {
                                   the neighbours within rc + skin at the box density, or at
                                   rho = 0.9 if higher, + 32).  A box whose list overflows is
                                   re-run by mdeos_poll with twice the capacity. */
-  int32_t max_cluster;         /* CTAs per box for batches of few small boxes (thread-block
+  int32_t max_cluster;         /* CTAs per box for batches of few boxes (thread-block
                                   clusters, see mdeos_submit): 0 = up to 4, at most 8,
                                   1 = none */
 } mdeos_config;
@@ -148,7 +148,9 @@ mdeos_status mdeos_create(const mdeos_config* cfg, mdeos_handle** out);
  * CTA; one with no more boxes than SMs gives each box its own CTA; one with fewer
  * boxes than half the SMs, all of at most 768 atoms, runs each box on a
  * thread-block cluster of up to cfg.max_cluster CTAs (each holds the box and computes
- * the forces of its share of the atoms).  Results do not depend on the launch shape.
+ * the forces of its share of the atoms); one with fewer boxes than half the SMs, all
+ * above 4096 atoms, does the same with one state per box in global memory (each CTA
+ * owns a slab of the cell-ordered atoms).  Results do not depend on the launch shape.
  * Errors: MDEOS_EINVAL (n < 1, NULL, or a request field out of range),
  * MDEOS_ENOMEM, MDEOS_ECUDA. */
 mdeos_status mdeos_submit(mdeos_handle* h, const mdeos_request* reqs, int32_t n,
