@@ -534,7 +534,9 @@ def serving(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     m.build()
-    h = m.mdeos_create(m.mdeos_config_default(device=local))
+    # max_cluster: CTAs per thread-block cluster of the serving grid, which runs a box
+    # above 4096 atoms on a whole cluster (0: 4, 1: one CTA per box)
+    h = m.mdeos_create(m.mdeos_config_default(device=local, max_cluster=args.max_cluster))
     gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
     clocks = ClockSampler(gpu_idx)
     clocks.start()
@@ -574,6 +576,7 @@ def serving(args):
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded LJ boxes, Poisson arrivals)",
         "config": {"workload": SERVING, "duration_s": args.duration,
+                   "max_cluster": args.max_cluster,
                    "p99_bound_s": args.p99_bound, "max_wait_s": args.max_wait,
                    "max_inflight": "2048 (sweep), 1024 (overload)", "max_batch": 2048},
         "sustainable": best, "sweep": runs, "capacity_closed_loop": capacity,

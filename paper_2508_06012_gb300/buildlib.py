@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdeos.so")
 SOURCES = ["mdeos_batch.cu", "mdeos_debug.cu", "mdeos_noalloc.cu", "mdeos_api.cu",
-           "mdeos_hydro.cu", "mdeos_serve.cu", "mdeos_mlp.cu"]
+           "mdeos_hydro.cu", "mdeos_serve.cu", "mdeos_mlp.cu", "mdeos_serve_cluster.cu"]
 # per-file flags: the hydro update is FP64 in a fixed operation order, without
 # contracted multiply-adds on the device or the host
 EXTRA = {"mdeos_hydro.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]}

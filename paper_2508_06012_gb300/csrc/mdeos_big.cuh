@@ -24,7 +24,6 @@ constexpr int kMaxRounds = 16;  // force-pass rounds of a big box (position wind
 
 struct BigShared {
   long long red[32 * kRedSlots];
-  long long clu[2 * kMaxCluster * kRedSlots];  // cluster partials, two alternating sets
   double bc[8];
   double acc[kAccDoubles];
   int bcnt[kMaxSeBlocks];
@@ -47,17 +46,23 @@ struct BigShared {
 // integers and takes the same decisions, and every result equals the one-CTA run.
 struct BigClu {
   int crank, csize;
-  int lo, hi;  // the CTA's slots
-  int seq;     // cluster exchanges so far (picks the partials' set)
+  int lo, hi;     // the CTA's slots
+  int seq;        // cluster exchanges so far (picks the partials' set)
+  long long* clu;  // cluster partials, two alternating sets of kMaxCluster x kRedSlots
+                   // (shared memory behind BigShared; only with csize > 1)
 };
 
-__device__ __forceinline__ BigClu big_clu(int n, int crank, int csize) {
+// shared memory of the cluster partials, behind BigShared (position windows follow)
+constexpr int kBigCluBytes = 2 * kMaxCluster * kRedSlots * 8;
+
+__device__ __forceinline__ BigClu big_clu(int n, int crank, int csize, long long* clu = nullptr) {
   BigClu c;
   c.crank = crank;
   c.csize = csize;
   c.lo = (int)((long long)n * crank / csize);
   c.hi = (int)((long long)n * (crank + 1) / csize);
   c.seq = 0;
+  c.clu = clu;
   return c;
 }
 
@@ -86,7 +91,7 @@ __device__ __forceinline__ unsigned long long big_cluster_total(BigShared* sh, B
                                                                 unsigned long long t) {
   if (cl.csize == 1) return t;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long* set = sh->clu + (cl.seq & 1) * (kMaxCluster * kRedSlots);
+  long long* set = cl.clu + (cl.seq & 1) * (kMaxCluster * kRedSlots);
   if (warp == 0 && lane < NQ) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(set + cl.crank * kRedSlots + lane);
     for (int rk = 0; rk < cl.csize; ++rk) st_cluster_s64(cluster_map(a, rk), (long long)t);
@@ -628,10 +633,13 @@ static __device__ __noinline__ void run_big(unsigned char* scratch, BigShared* s
   const int nwarps = nt >> 5;
   const BigCtx b = make_big_ctx(bd, rp);
   const LJ lj = make_lj(rp);
-  BigClu cl = big_clu(b.n, crank, csize);
+  // in a cluster, the partials' sets follow BigShared; then the position windows in
+  // the CTA's otherwise idle shared memory
+  unsigned char* shb = reinterpret_cast<unsigned char*>(sh);
+  BigClu cl = big_clu(b.n, crank, csize,
+                      csize > 1 ? reinterpret_cast<long long*>(shb + kBigSharedBytes) : nullptr);
   BigMem m = big_mem(scratch, b.n, b.nc * b.nc * b.nc, cl);
-  // position windows in the CTA's otherwise idle shared memory, behind BigShared
-  big_pos_cache(m, reinterpret_cast<const unsigned char*>(sh), kBigSharedBytes);
+  big_pos_cache(m, shb, kBigSharedBytes + (csize > 1 ? kBigCluBytes : 0));
   const int n = b.n;
   const double ndof = 3.0 * n - 3.0;
   const double V = bd.L * bd.L * bd.L;

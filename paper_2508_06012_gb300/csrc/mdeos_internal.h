@@ -27,7 +27,7 @@ constexpr int kMaxCluster = 8;        // CTAs of a thread-block cluster that sha
 // boxes above kMaxAtoms run one per CTA with their state in global memory
 constexpr int kMaxAtomsBig = 32768;   // uint16 neighbour indices
 constexpr int kMaxCellsBig = 32768;   // cells of the list build (<= 32 per axis)
-constexpr int kBigSharedBytes = 8192; // shared memory of a big-box CTA (reductions, cluster partials)
+constexpr int kBigSharedBytes = 4096; // shared memory of a big-box CTA (reductions only)
 
 // Cells per axis of a shared-memory box's Verlet-list build: side at least
 // R / 2 (R = rc + skin), at most 12 per axis; 0 = no cell grid (a scan of all

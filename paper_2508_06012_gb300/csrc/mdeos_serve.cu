@@ -37,6 +37,14 @@
 
 using namespace mdeos;
 
+namespace mdeos {
+// the cluster form of the serving kernel (mdeos_serve_cluster.cu)
+cudaError_t set_serve_cluster_attributes(int max_smem);
+cudaError_t launch_eos_serve_cluster(const ServeQueue& q, const RunParams& rp, uint16_t* nl,
+                                     long long nl_elems_per_cta, int grid, int smem,
+                                     cudaStream_t st, int cluster);
+}  // namespace mdeos
+
 namespace {
 
 struct Waiting {
@@ -76,6 +84,7 @@ struct mdeos_server {
   mdeos_handle* h = nullptr;
   mdeos_serve_config cfg;
   int device = 0, grid = 0, smem = 0;
+  int cluster = 1;  // CTAs per thread-block cluster of the serving grid (1: eos_serve_kernel)
   std::chrono::steady_clock::time_point t0;
   std::thread th;
   std::mutex mu;
@@ -475,11 +484,16 @@ static void serve_loop(mdeos_server* s) {
       for (int g = 0; g < mdeos_server::kGrids && free_g < 0; ++g)
         if (!s->running[g]) free_g = g;
       const bool cold = !any_running;
-      if (free_g >= 0 && alive < s->grid && s->outstanding_items > alive &&
+      // (a whole number of clusters)
+      const int nct = (s->grid - alive) / s->cluster * s->cluster;
+      if (free_g >= 0 && nct > 0 && s->outstanding_items > alive &&
           (cold || t - s->last_launch > 0.002)) {
-        const int nct = s->grid - alive;
-        cudaError_t e = launch_eos_serve(s->q, handle_run_params(s->h), s->d_nl, s->nl_per_cta,
-                                         nct, s->smem, s->st[free_g]);
+        cudaError_t e =
+            s->cluster > 1
+                ? launch_eos_serve_cluster(s->q, handle_run_params(s->h), s->d_nl, s->nl_per_cta,
+                                           nct, s->smem, s->st[free_g], s->cluster)
+                : launch_eos_serve(s->q, handle_run_params(s->h), s->d_nl, s->nl_per_cta, nct,
+                                   s->smem, s->st[free_g]);
         if (e == cudaSuccess) e = cudaEventRecord(s->ev[free_g], s->st[free_g]);
         if (e == cudaSuccess) {
           s->running[free_g] = true;
@@ -542,6 +556,15 @@ extern "C" mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_co
   s->device = handle_device(h);
   s->grid = handle_sm_count(h);
   s->smem = handle_smem_max(h);
+  {  // boxes above 4096 atoms on thread-block clusters of the handle's max_cluster CTAs
+     // (0: 4, 1: none), a power of two dividing the grid
+    const int mc = handle_config(h).max_cluster;
+    int c = mc == 0 ? 4 : std::min(mc, kMaxCluster);
+    int p = 1;
+    while (2 * p <= c && s->grid % (2 * p) == 0) p *= 2;
+    s->cluster = p;
+    if (p > 1 && set_serve_cluster_attributes(s->smem) != cudaSuccess) s->cluster = 1;
+  }
   s->t0 = std::chrono::steady_clock::now();
   // per-SM scratch: the largest item, a 32768-atom box with the list capacity of
   // the densest liquid the planner admits (or a full shared-memory item)

@@ -55,6 +55,24 @@ def test_served_results_equal_solo_runs(m, h):
         assert by_id[int(rid)]["result"].tobytes() == solo[i].tobytes(), i
 
 
+def test_served_results_equal_solo_runs_one_cta_per_box(m):
+    """The serving grid without thread-block clusters (max_cluster = 1: boxes above
+    4096 atoms on one CTA each) serves the same bytes as the clustered default."""
+    reqs = _stream_requests(m, 24, 23)
+    h1 = m.mdeos_create(m.mdeos_config_default(max_cluster=1))
+    try:
+        with m.Server(h1, max_batch=8) as srv:
+            ids = srv.enqueue(reqs)
+            got = srv.wait_all(len(reqs), timeout_s=300)
+    finally:
+        m.mdeos_destroy(h1)
+    by_id = {int(g["id"]): g for g in got}
+    with m.Engine() as eng:
+        solo = eng.evaluate(reqs)
+    for i, rid in enumerate(ids):
+        assert by_id[int(rid)]["result"].tobytes() == solo[i].tobytes(), i
+
+
 def test_requests_complete_before_their_launch_ends(m, h):
     """Results are reported per box: small boxes sharing a launch with one large box
     are seen long before it finishes."""
