@@ -87,9 +87,10 @@ typedef struct {
                                   the neighbours within rc + skin at the box density, or at
                                   rho = 0.9 if higher, + 32).  A box whose list overflows is
                                   re-run by mdeos_poll with twice the capacity. */
-  int32_t max_cluster;         /* CTAs per box for batches of few boxes (thread-block
-                                  clusters, see mdeos_submit): 0 = up to 4, at most 8,
-                                  1 = none */
+  int32_t max_cluster;         /* CTAs per box for batches of few boxes and for served
+                                  boxes above 4096 atoms (thread-block clusters, see
+                                  mdeos_submit, mdeos_serve_create): 0 = up to 4, at most
+                                  8, 1 = none */
 } mdeos_config;
 
 /* One EOS query.  Layout is part of the ABI. */
@@ -411,6 +412,10 @@ typedef struct mdeos_server mdeos_server;
 void mdeos_serve_config_default(mdeos_serve_config* cfg);
 
 /* Start a server on handle h (caller-owned, must outlive the server); cfg copied.
+ * The serving grid runs in thread-block clusters of the handle's max_cluster CTAs
+ * (0: 4, 1: no clusters): a cluster takes one request above 4096 atoms for all its
+ * CTAs (each a slab of the box's atoms) or one item of smaller boxes per CTA, so a
+ * large box's latency falls with the cluster size.  Results do not depend on it.
  * Errors: MDEOS_EINVAL, MDEOS_ENOMEM (budget below the scratch), MDEOS_ECUDA. */
 mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_config* cfg,
                                 mdeos_server** out);

@@ -95,7 +95,9 @@ def test_queue_cap_and_wait_limit_shed(m, h):
         got = srv.wait_all(20, timeout_s=120)
     st = got["result"]["status"]
     assert (st == m.MDEOS_ECANCELLED).sum() == 15 and (st == 0).sum() == 5
-    long = dict(rho=0.8, e=1.5, natoms=20000, steps_equil=400, steps_avg=400, seed=6)
+    # long enough to hold the only in-flight slot past the sleep even on a cluster of
+    # 8 CTAs (~0.4 s; ~2.5 s on one CTA)
+    long = dict(rho=0.8, e=1.5, natoms=20000, steps_equil=2000, steps_avg=2000, seed=6)
     with m.Server(h, max_inflight=1, max_batch=4, max_wait_s=0.05) as srv:
         srv.enqueue([long])
         time.sleep(0.2)                      # the only in-flight slot holds the long box
