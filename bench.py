@@ -469,7 +469,7 @@ SERVING = ("EOS serving stream: Poisson arrivals, atom counts log-uniform 256..3
 
 
 def serve_run(m, h, rate, duration, seed, max_wait_s, max_queue, max_inflight=2048,
-              max_batch=2048, drain_s=60.0):
+              max_batch=2048, drain_s=60.0, cluster=1):
     """Drive one Poisson stream through the server; latency = done - arrival (queue
     time included) of the requests that were served."""
     from paper_2508_06012_gb300 import workloads as w
@@ -480,7 +480,7 @@ def serve_run(m, h, rate, duration, seed, max_wait_s, max_queue, max_inflight=20
                               steps_avg=b["steps_avg"], seed=b["seed"]) for b in boxes])
     cfg = m.mdeos_serve_config_default(max_inflight=max_inflight, max_batch=max_batch,
                                        max_wait_s=max_wait_s, max_queue=max_queue,
-                                       hbm_budget_bytes=60 << 30)
+                                       hbm_budget_bytes=60 << 30, cluster=cluster)
     srv = m.Server(h, cfg)
     got = []
     i = 0
@@ -534,9 +534,7 @@ def serving(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     m.build()
-    # max_cluster: CTAs per thread-block cluster of the serving grid, which runs a box
-    # above 4096 atoms on a whole cluster (0: 4, 1: one CTA per box)
-    h = m.mdeos_create(m.mdeos_config_default(device=local, max_cluster=args.max_cluster))
+    h = m.mdeos_create(m.mdeos_config_default(device=local))
     gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
     clocks = ClockSampler(gpu_idx)
     clocks.start()
@@ -558,10 +556,12 @@ def serving(args):
                 "pair_share_big_boxes": float((cap["pairs_per_step"] * steps_c)[big].sum() /
                                               max((cap["pairs_per_step"] * steps_c).sum(), 1.0))}
     rates = [float(r) for r in args.rates.split(",")]
+    # --serve-cluster C: the serving grid in thread-block clusters of C CTAs (a box
+    # above 4096 atoms on a whole cluster; 1: one CTA per box)
     runs = [serve_run(m, h, r, args.duration, 1000 + k, max_wait_s=args.max_wait,
-                      max_queue=0) for k, r in enumerate(rates)]
+                      max_queue=0, cluster=args.serve_cluster) for k, r in enumerate(rates)]
     over = serve_run(m, h, 20000.0, min(args.duration, 10.0), 999, max_wait_s=args.max_wait,
-                     max_queue=4096, max_inflight=1024)
+                     max_queue=4096, max_inflight=1024, cluster=args.serve_cluster)
     clk = clocks.stop()
     m.mdeos_destroy(h)
     # sustainable: nothing shed or left over, steady-state completions keep up with
@@ -576,7 +576,7 @@ def serving(args):
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded LJ boxes, Poisson arrivals)",
         "config": {"workload": SERVING, "duration_s": args.duration,
-                   "max_cluster": args.max_cluster,
+                   "serve_cluster": args.serve_cluster,
                    "p99_bound_s": args.p99_bound, "max_wait_s": args.max_wait,
                    "max_inflight": "2048 (sweep), 1024 (overload)", "max_batch": 2048},
         "sustainable": best, "sweep": runs, "capacity_closed_loop": capacity,
@@ -1047,6 +1047,8 @@ def main():
                     help="uneven: 4096-box batched EOS (default); config1: 16 boxes of 256 "
                          "atoms; coupled: MD-closed hydro; serving: Poisson request stream")
     ap.add_argument("--rates", default="50,100,200,300", help="serving: arrival rates (1/s)")
+    ap.add_argument("--serve-cluster", type=int, default=1,
+                    help="serving: CTAs per thread-block cluster of the serving grid")
     ap.add_argument("--duration", type=float, default=15.0, help="serving: seconds per rate")
     ap.add_argument("--max-wait", type=float, default=10.0, help="serving: shed after (s)")
     ap.add_argument("--p99-bound", type=float, default=10.0, help="serving: p99 bound (s)")

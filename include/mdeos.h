@@ -87,10 +87,9 @@ typedef struct {
                                   the neighbours within rc + skin at the box density, or at
                                   rho = 0.9 if higher, + 32).  A box whose list overflows is
                                   re-run by mdeos_poll with twice the capacity. */
-  int32_t max_cluster;         /* CTAs per box for batches of few boxes and for served
-                                  boxes above 4096 atoms (thread-block clusters, see
-                                  mdeos_submit, mdeos_serve_create): 0 = up to 4, at most
-                                  8, 1 = none */
+  int32_t max_cluster;         /* CTAs per box for batches of few boxes (thread-block
+                                  clusters, see mdeos_submit): 0 = up to 4, at most 8,
+                                  1 = none */
 } mdeos_config;
 
 /* One EOS query.  Layout is part of the ABI. */
@@ -389,7 +388,12 @@ typedef struct {
                                largest box (32768 atoms) plus the element store; creation
                                fails if the scratch alone exceeds it; 0 = no cap */
   int32_t warm;             /* 1: keep element states for warm starts (see above); 0: off */
-  int32_t reserved0;
+  int32_t cluster;          /* CTAs per thread-block cluster of the serving grid (1 = none,
+                               else a power of two up to 8): a cluster takes one request
+                               above 4096 atoms for all its CTAs (each a slab of the
+                               box's atoms) or one item of smaller boxes per CTA in
+                               rounds; large boxes finish sooner (lower p99 below
+                               saturation), the rounds lower the capacity */
   size_t warm_bytes;        /* element store size; 0 = what hbm_budget_bytes leaves after the
                                scratch (1 GiB without a budget) */
 } mdeos_serve_config;
@@ -412,11 +416,10 @@ typedef struct mdeos_server mdeos_server;
 void mdeos_serve_config_default(mdeos_serve_config* cfg);
 
 /* Start a server on handle h (caller-owned, must outlive the server); cfg copied.
- * The serving grid runs in thread-block clusters of the handle's max_cluster CTAs
- * (0: 4, 1: no clusters): a cluster takes one request above 4096 atoms for all its
- * CTAs (each a slab of the box's atoms) or one item of smaller boxes per CTA, so a
- * large box's latency falls with the cluster size.  Results do not depend on it.
- * Errors: MDEOS_EINVAL, MDEOS_ENOMEM (budget below the scratch), MDEOS_ECUDA. */
+ * With cfg->cluster > 1 the serving grid runs in thread-block clusters (see the
+ * field); results do not depend on it.
+ * Errors: MDEOS_EINVAL (cluster not 0, 1, 2, 4 or 8), MDEOS_ENOMEM (budget below the
+ * scratch), MDEOS_ECUDA. */
 mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_config* cfg,
                                 mdeos_server** out);
 

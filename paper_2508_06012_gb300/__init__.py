@@ -106,7 +106,7 @@ class mdeos_serve_config(ctypes.Structure):
         ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("max_wait_s", ctypes.c_double), ("max_queue", ctypes.c_int32),
         ("idle_ms", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
-        ("warm", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("warm_bytes", ctypes.c_size_t),
+        ("warm", ctypes.c_int32), ("cluster", ctypes.c_int32), ("warm_bytes", ctypes.c_size_t),
     ]
 
 

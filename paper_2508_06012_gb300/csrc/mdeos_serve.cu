@@ -539,6 +539,7 @@ extern "C" void mdeos_serve_config_default(mdeos_serve_config* c) {
   c->max_queue = 0;
   c->idle_ms = 20;
   c->hbm_budget_bytes = 0;
+  c->cluster = 1;
 }
 
 extern "C" mdeos_status mdeos_serve_destroy(mdeos_server* s);
@@ -548,7 +549,9 @@ extern "C" mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_co
   if (!h || !cfg || !out) return set_error(MDEOS_EINVAL, "bad serve_create arguments");
   *out = nullptr;
   if (cfg->max_inflight < 1 || cfg->max_inflight > (1 << 20) || cfg->max_batch < 1 ||
-      cfg->max_queue < 0 || !(cfg->max_wait_s >= 0) || cfg->idle_ms < 1 || cfg->idle_ms > 60000)
+      cfg->max_queue < 0 || !(cfg->max_wait_s >= 0) || cfg->idle_ms < 1 || cfg->idle_ms > 60000 ||
+      !(cfg->cluster == 0 || cfg->cluster == 1 || cfg->cluster == 2 || cfg->cluster == 4 ||
+        cfg->cluster == 8))
     return set_error(MDEOS_EINVAL, "serve config out of range");
   mdeos_server* s = new mdeos_server();
   s->h = h;
@@ -556,14 +559,19 @@ extern "C" mdeos_status mdeos_serve_create(mdeos_handle* h, const mdeos_serve_co
   s->device = handle_device(h);
   s->grid = handle_sm_count(h);
   s->smem = handle_smem_max(h);
-  {  // boxes above 4096 atoms on thread-block clusters of the handle's max_cluster CTAs
-     // (0: 4, 1: none), a power of two dividing the grid
-    const int mc = handle_config(h).max_cluster;
-    int c = mc == 0 ? 4 : std::min(mc, kMaxCluster);
+  {  // the serving grid in thread-block clusters of cfg->cluster CTAs (a power of two
+     // dividing the grid; 0 or 1: none)
     int p = 1;
-    while (2 * p <= c && s->grid % (2 * p) == 0) p *= 2;
+    while (2 * p <= cfg->cluster && s->grid % (2 * p) == 0) p *= 2;
     s->cluster = p;
-    if (p > 1 && set_serve_cluster_attributes(s->smem) != cudaSuccess) s->cluster = 1;
+    if (p > 1) {
+      const cudaError_t e = set_serve_cluster_attributes(s->smem);
+      if (e != cudaSuccess) {
+        delete s;
+        return set_error(MDEOS_ECUDA, std::string("serving cluster kernel: ") +
+                                          cudaGetErrorString(e));
+      }
+    }
   }
   s->t0 = std::chrono::steady_clock::now();
   // per-SM scratch: the largest item, a 32768-atom box with the list capacity of

@@ -55,17 +55,16 @@ def test_served_results_equal_solo_runs(m, h):
         assert by_id[int(rid)]["result"].tobytes() == solo[i].tobytes(), i
 
 
-def test_served_results_equal_solo_runs_one_cta_per_box(m):
-    """The serving grid without thread-block clusters (max_cluster = 1: boxes above
-    4096 atoms on one CTA each) serves the same bytes as the clustered default."""
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_served_results_on_clusters_equal_solo_runs(m, h, cluster):
+    """The serving grid in thread-block clusters (boxes above 4096 atoms on a whole
+    cluster, smaller items one per CTA in rounds) serves the bytes of solo runs."""
     reqs = _stream_requests(m, 24, 23)
-    h1 = m.mdeos_create(m.mdeos_config_default(max_cluster=1))
-    try:
-        with m.Server(h1, max_batch=8) as srv:
-            ids = srv.enqueue(reqs)
-            got = srv.wait_all(len(reqs), timeout_s=300)
-    finally:
-        m.mdeos_destroy(h1)
+    with m.Server(h, max_batch=8, cluster=cluster) as srv:
+        ids = srv.enqueue(reqs)
+        got = srv.wait_all(len(reqs), timeout_s=300)
+        st = srv.stats()
+    assert st["cuda_errors"] == 0 and st["shed"] == 0
     by_id = {int(g["id"]): g for g in got}
     with m.Engine() as eng:
         solo = eng.evaluate(reqs)
@@ -95,9 +94,7 @@ def test_queue_cap_and_wait_limit_shed(m, h):
         got = srv.wait_all(20, timeout_s=120)
     st = got["result"]["status"]
     assert (st == m.MDEOS_ECANCELLED).sum() == 15 and (st == 0).sum() == 5
-    # long enough to hold the only in-flight slot past the sleep even on a cluster of
-    # 8 CTAs (~0.4 s; ~2.5 s on one CTA)
-    long = dict(rho=0.8, e=1.5, natoms=20000, steps_equil=2000, steps_avg=2000, seed=6)
+    long = dict(rho=0.8, e=1.5, natoms=20000, steps_equil=400, steps_avg=400, seed=6)
     with m.Server(h, max_inflight=1, max_batch=4, max_wait_s=0.05) as srv:
         srv.enqueue([long])
         time.sleep(0.2)                      # the only in-flight slot holds the long box
