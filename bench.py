@@ -52,7 +52,7 @@ WORKLOAD = ("batched uneven MD-EOS: 4096 LJ boxes, N=4n^3 n~U{3..10} (108-4000 a
             "production steps, one persistent graph-captured launch")
 
 
-CONFIG1 = ("16 independent LJ MD-EOS queries, one box each: N=256 (FCC 4x4x4), rho*~U[0.5,1.0], "
+QUERIES16 = ("16 independent LJ MD-EOS queries, one box each: N=256 (FCC 4x4x4), rho*~U[0.5,1.0], "
            "T*~U[1.0,2.0], rc=2.5, dt=0.005, 1000 lifting + 1000 production steps, one "
            "persistent graph-captured launch")
 
@@ -151,11 +151,11 @@ def cpu_sample(per_class=2, steps_equil=100, steps_avg=100, workload="uneven"):
     count with 200 of the 2000 steps (the 16-box batch: all boxes, 400 of 2000
     steps); EOS/s is scaled by the step fraction."""
     from paper_2508_06012_gb300 import workloads as w
-    if workload == "config1":
-        boxes = [dict(b, steps_equil=200, steps_avg=200) for b in w.config1()]
+    if workload == "queries16x256":
+        boxes = [dict(b, steps_equil=200, steps_avg=200) for b in w.small_queries()]
         return boxes, 400 / 2000.0, ("16 boxes x 400 of 2000 steps (N=256), FP64 linked-cell "
                                      "oracle, OpenMP")
-    boxes = w.stratified(w.config2(), per_class, steps_equil, steps_avg)
+    boxes = w.stratified(w.uneven_batch(), per_class, steps_equil, steps_avg)
     frac = (steps_equil + steps_avg) / 2000.0
     desc = (f"{len(boxes)} boxes ({per_class} per atom count 108..4000) x "
             f"{steps_equil + steps_avg} of 2000 steps, FP64 linked-cell oracle, OpenMP")
@@ -192,7 +192,7 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1000.0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": CONFIG1 if args.workload == "config1" else WORKLOAD,
+        "config": {"workload": QUERIES16 if args.workload == "queries16x256" else WORKLOAD,
                    "sample": desc},
         "cpu_baseline": {"value": value, "unit": "EOS/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
@@ -215,14 +215,14 @@ def ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     m.build()
-    if args.workload == "config1":
-        boxes = w.config1(base_seed=20250806 + rank)
+    if args.workload == "queries16x256":
+        boxes = w.small_queries(base_seed=20250806 + rank)
     elif args.boxes or args.md_steps:
         half = (args.md_steps or 2000) // 2
-        boxes = w.config2(base_seed=20250807 + rank, nbox=args.boxes or 4096,
+        boxes = w.uneven_batch(base_seed=20250807 + rank, nbox=args.boxes or 4096,
                           steps_equil=half, steps_avg=half)
     else:
-        boxes = w.config2(base_seed=20250807 + rank)
+        boxes = w.uneven_batch(base_seed=20250807 + rank)
     reqs = gpu_requests(m, boxes)
     nbox = len(reqs)
     h = m.mdeos_create(m.mdeos_config_default(device=local, max_cluster=args.max_cluster))
@@ -339,7 +339,7 @@ def ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded LJ boxes; no datasets or trained weights)",
-            "config": {"workload": (CONFIG1 if args.workload == "config1" else
+            "config": {"workload": (QUERIES16 if args.workload == "queries16x256" else
                                     WORKLOAD if not (args.boxes or args.md_steps) else
                                     f"reduced: {nbox} boxes x {args.md_steps or 2000} steps of "
                                     + WORKLOAD),
@@ -374,7 +374,7 @@ def coupled_setup(nz=2000):
 
 
 def coupled(args):
-    """Config-3 coupled run: hydro steps/s and EOS/s of the MD-closed hydro."""
+    """Coupled hydro shock tube (2000 zones x 500-atom boxes): hydro steps/s and EOS/s of the MD-closed hydro."""
     import torch
 
     import paper_2508_06012_gb300 as m
@@ -474,7 +474,7 @@ def serve_run(m, h, rate, duration, seed, max_wait_s, max_queue, max_inflight=20
     time included) of the requests that were served."""
     from paper_2508_06012_gb300 import workloads as w
     t_arr = w.poisson_arrivals(rate, duration, seed)
-    boxes = w.config4(seed, len(t_arr))
+    boxes = w.serving_stream(seed, len(t_arr))
     arr = m.as_requests([dict(rho=b["rho"], e=m.e_from_temperature(b["T"], b["natoms"]),
                               natoms=b["natoms"], steps_equil=b["steps_equil"],
                               steps_avg=b["steps_avg"], seed=b["seed"]) for b in boxes])
@@ -527,7 +527,7 @@ def serve_run(m, h, rate, duration, seed, max_wait_s, max_queue, max_inflight=20
 
 
 def serving(args):
-    """Config-4 serving: a sweep of arrival rates and the 20k/s overload case."""
+    """Serving stream (atom counts log-uniform 256..32000): a sweep of arrival rates and the 20k/s overload case."""
     import torch
 
     import paper_2508_06012_gb300 as m
@@ -540,7 +540,7 @@ def serving(args):
     clocks.start()
     # closed-loop capacity: one batch of the serving mix through mdeos_submit
     from paper_2508_06012_gb300 import workloads as w
-    cap_boxes = w.config4(4242, args.capacity_n)
+    cap_boxes = w.serving_stream(4242, args.capacity_n)
     cap_reqs = [dict(rho=b["rho"], e=m.e_from_temperature(b["T"], b["natoms"]),
                      natoms=b["natoms"], steps_equil=b["steps_equil"], steps_avg=b["steps_avg"],
                      seed=b["seed"]) for b in cap_boxes]
@@ -588,14 +588,14 @@ def serving(args):
 
 
 SURROGATE = ("surrogate-gated EOS: ensemble of 4 MLPs 2-128-128-128-2 (BF16 weights, FP32 "
-             "accumulation, tensor-core layers) trained on 1e5 MD samples of the config-2 "
+             "accumulation, tensor-core layers) trained on 1e5 MD samples of the uneven batch's "
              "(rho*, T*) distribution at the fallback's box size (4000 atoms; --train-natoms 0: "
-             "the config-2 size mix); requests above the disagreement threshold fall back to "
+             "the size mix of the uneven batch); requests above the disagreement threshold fall back to "
              "4000-atom MD; threshold tuned to 1% pressure error against 4000-atom MD")
 
 
 def surrogate(args):
-    """Config 5: train the ensemble on MD answers, tune the gate, compare with MD-only."""
+    """Surrogate-gated EOS: train the ensemble on MD answers, tune the gate, compare with MD-only."""
     import torch
 
     import paper_2508_06012_gb300 as m
@@ -608,9 +608,9 @@ def surrogate(args):
     clocks = ClockSampler(gpu_idx)
     clocks.start()
     out = {}
-    # 1. training data: MD answers over the config-2 distribution (with --train-natoms,
+    # 1. training data: MD answers over the uneven batch's distribution (with --train-natoms,
     # its (rho, T) distribution at that one box size)
-    boxes = w.config2(base_seed=777, nbox=args.train_n)
+    boxes = w.uneven_batch(base_seed=777, nbox=args.train_n)
     if args.train_natoms:
         boxes = [dict(b, natoms=args.train_natoms) for b in boxes]
     reqs = gpu_requests(m, boxes)
@@ -628,7 +628,7 @@ def surrogate(args):
     def queries(seed, n):
         return [dict(rho=q["rho"], e=m.e_from_temperature(q["T"], 4000), natoms=4000,
                      steps_equil=1000, steps_avg=1000, seed=q["seed"])
-                for q in w.config2(base_seed=seed, nbox=n)]
+                for q in w.uneven_batch(base_seed=seed, nbox=n)]
     val = queries(778, args.val_n)
     test = queries(779, args.test_n)
     rv = m.mdeos_poll(h, m.mdeos_submit(h, val), len(val), -1)
@@ -823,7 +823,7 @@ def surrogate(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (MD answers of seeded LJ boxes)", "config": {
                 "workload": SURROGATE, "train_n": args.train_n,
-                "train_natoms": args.train_natoms or "config-2 mix", "val_n": args.val_n,
+                "train_natoms": args.train_natoms or "uneven-batch size mix", "val_n": args.val_n,
                 "test_n": args.test_n, "epochs": args.epochs},
             "details": out, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -1027,7 +1027,7 @@ def main():
                     help="surrogate: queries timed as one MD launch each")
     ap.add_argument("--train-natoms", type=int, default=4000,
                     help="surrogate: box size of the training MD (default: the 4000 atoms of "
-                         "the MD fallback; 0: the config-2 size mix)")
+                         "the MD fallback; 0: the uneven batch's size mix)")
     ap.add_argument("--queries", type=int, default=1 << 23, help="surrogate-infer: queries")
     ap.add_argument("--fb-natoms", type=int, default=4000, help="forcepass: atoms per box")
     ap.add_argument("--fb-rho", type=float, default=0.8, help="forcepass: density")
@@ -1040,11 +1040,11 @@ def main():
     ap.add_argument("--big-boxes", type=int, default=0, help="bigbox: boxes (0: one per SM)")
     ap.add_argument("--max-cluster", type=int, default=0,
                     help="CTAs per box for batches of few small boxes (0: up to 4, 1: none)")
-    ap.add_argument("--workload", choices=["uneven", "config1", "coupled", "serving",
+    ap.add_argument("--workload", choices=["uneven", "queries16x256", "coupled", "serving",
                                            "surrogate", "surrogate-infer", "forcepass",
                                            "bigbox"],
                     default="uneven",
-                    help="uneven: 4096-box batched EOS (default); config1: 16 boxes of 256 "
+                    help="uneven: 4096-box batched EOS (default); queries16x256: 16 boxes of 256 "
                          "atoms; coupled: MD-closed hydro; serving: Poisson request stream")
     ap.add_argument("--rates", default="50,100,200,300", help="serving: arrival rates (1/s)")
     ap.add_argument("--serve-cluster", type=int, default=1,

@@ -28,7 +28,7 @@ def box_seed(base: int, index: int) -> int:
     return splitmix64((base * 0x100000001B3 + index) & MASK64)
 
 
-def config1(base_seed: int = 20250806, nbox: int = 16):
+def small_queries(base_seed: int = 20250806, nbox: int = 16):
     """16 independent queries: N = 256 (FCC 4x4x4), rho* ~ U[0.5, 1.0],
     T* ~ U[1.0, 2.0], 1000 equilibration + 1000 averaging steps."""
     rng = np.random.default_rng(base_seed)
@@ -39,7 +39,7 @@ def config1(base_seed: int = 20250806, nbox: int = 16):
             for k in range(nbox)]
 
 
-def config2(base_seed: int = 20250807, nbox: int = 4096, steps_equil: int = 1000,
+def uneven_batch(base_seed: int = 20250807, nbox: int = 4096, steps_equil: int = 1000,
             steps_avg: int = 1000):
     """Batched uneven EOS: N = 4 n^3 with n ~ U{3..10} (108..4000 atoms),
     rho* ~ U[0.3, 1.2], T* log-uniform on [0.7, 3.0], 2000 steps."""
@@ -81,10 +81,10 @@ def random_boxes(seed: int, nbox: int, nmin: int, nmax: int, rho=(0.3, 1.2), T=(
             for k in range(nbox)]
 
 
-def config4(base_seed: int = 20250809, nreq: int = 1000, steps_equil: int = 1000,
+def serving_stream(base_seed: int = 20250809, nreq: int = 1000, steps_equil: int = 1000,
             steps_avg: int = 1000):
     """EOS serving stream: atom counts log-uniform on [256, 32000], rho* ~ U[0.3, 1.2],
-    T* log-uniform on [0.7, 3.0] (the 2000-step schedule of config 2)."""
+    T* log-uniform on [0.7, 3.0] (the 1000 + 1000-step schedule of the uneven batch)."""
     rng = np.random.default_rng(base_seed)
     n = np.exp(rng.uniform(np.log(256.0), np.log(32000.0), nreq)).astype(np.int64)
     rho = rng.uniform(0.3, 1.2, nreq)

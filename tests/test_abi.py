@@ -86,10 +86,10 @@ def test_invalid_config_rejected_before_device(built_lib):
 
 def test_workload_generators_are_seeded():
     from paper_2508_06012_gb300 import workloads as w
-    a, b = w.config2(nbox=64), w.config2(nbox=64)
+    a, b = w.uneven_batch(nbox=64), w.uneven_batch(nbox=64)
     assert a == b
-    assert {r["natoms"] for r in w.config2(nbox=4096)} == {4 * n ** 3 for n in range(3, 11)}
+    assert {r["natoms"] for r in w.uneven_batch(nbox=4096)} == {4 * n ** 3 for n in range(3, 11)}
     assert all(0.3 <= r["rho"] <= 1.2 and 0.7 <= r["T"] <= 3.0 for r in a)
-    c1 = w.config1()
+    c1 = w.small_queries()
     assert len(c1) == 16 and all(r["natoms"] == 256 for r in c1)
-    assert len({r["seed"] for r in w.config2(nbox=4096)}) == 4096
+    assert len({r["seed"] for r in w.uneven_batch(nbox=4096)}) == 4096

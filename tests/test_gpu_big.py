@@ -82,7 +82,7 @@ def _ordered_pairs(x, L, r):
     (4097, 0.8, 1),      # one atom above the shared-memory limit, ragged lattice
     (6912, 0.9, 2),      # 4 x 12^3
     (13500, 0.35, 3),    # dilute, 4 x 15^3
-    (32000, 1.2, 4),     # largest config-4 box, dense
+    (32000, 1.2, 4),     # largest box of the serving stream, dense
     (32768, 0.8, 5),     # maximum atoms per box
 ])
 def test_big_forces_energy_virial_match_oracle(m, orc, n, rho, seed):

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 STATES = [
     (864, 0.85, 1.2, 400, 600),     # shared-memory path, Verlet list
     (2048, 0.6, 2.0, 400, 600),
-    (4000, 1.05, 2.5, 400, 600),    # largest config-2 box
+    (4000, 1.05, 2.5, 400, 600),    # largest box of the uneven batch
     (6912, 0.75, 1.5, 300, 500),    # global-memory path with shared-memory windows
     (32000, 0.9, 1.8, 100, 200),    # largest serving box
 ]

@@ -41,12 +41,12 @@ def oracle_reqs(orc, boxes):
             for b in boxes]
 
 
-def test_config1_statistics_match_oracle_ensemble(m, orc, eng):
-    """Config-1 state points (N = 256, 1000 + 1000 steps), 16 seeds each.  The first
+def test_small_query_statistics_match_oracle_ensemble(m, orc, eng):
+    """State points of the 16 small queries (N = 256, 1000 + 1000 steps), 16 seeds each.  The first
     lies in the liquid-vapour coexistence region (rho = 0.67, T ~ 0.8), where E_pot
     depends on how far the phase separation has gone and runs scatter widely."""
     from paper_2508_06012_gb300 import workloads as w
-    pts = w.config1()[:4]
+    pts = w.small_queries()[:4]
     ns = 16
     boxes = []
     for p in pts:
@@ -69,11 +69,11 @@ def test_config1_statistics_match_oracle_ensemble(m, orc, eng):
         assert abs(g["e_achieved"][sl].mean() - e) <= 0.1 * g["T"][sl].mean()
 
 
-def test_full_config2_batch_in_bench_launch_shape(m, orc):
+def test_full_uneven_batch_in_bench_launch_shape(m, orc):
     """All 4096 boxes of the batched uneven workload in the one-graph launch the
     benchmark times; properties on every box, oracle check on one box per size."""
     from paper_2508_06012_gb300 import workloads as w
-    boxes = w.config2()
+    boxes = w.uneven_batch()
     reqs = gpu_reqs(m, boxes)
     h = m.mdeos_create()
     b = m.mdeos_batch_create(h, reqs)

@@ -113,8 +113,8 @@ CASES = [
     (384, 0.7, 2, 9),      # largest box with 4 threads per atom
     (385, 0.7, 2, 10),     # smallest with 1
     (2048, 1.1, 2, 6),     # Verlet list from the shared-memory cell list
-    (4000, 0.3, 2, 7),     # largest config-2 box, dilute
-    (4000, 1.2, 2, 8),     # largest config-2 box, dense
+    (4000, 0.3, 2, 7),     # largest box of the uneven batch, dilute
+    (4000, 1.2, 2, 8),     # largest box of the uneven batch, dense
     (1111, 0.7, 2, 9),     # ragged: partial lattice, several ragged warps
     (4096, 0.85, 2, 10),   # maximum atoms per box
 ]

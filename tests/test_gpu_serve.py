@@ -32,7 +32,7 @@ def _stream_requests(m, k, seed, steps=(60, 60)):
     from paper_2508_06012_gb300 import workloads as w
     return [dict(rho=b["rho"], e=m.e_from_temperature(b["T"], b["natoms"]), natoms=b["natoms"],
                  steps_equil=b["steps_equil"], steps_avg=b["steps_avg"], seed=b["seed"])
-            for b in w.config4(seed, k, steps[0], steps[1])]
+            for b in w.serving_stream(seed, k, steps[0], steps[1])]
 
 
 def test_served_results_equal_solo_runs(m, h):

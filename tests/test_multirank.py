@@ -28,7 +28,7 @@ def _rank(rank, world, port, q):
     from paper_2508_06012_gb300 import workloads as w
     bench.barrier(world)
     t_max = bench.max_over_ranks(1.5 * (rank + 1), world)      # per-rank seconds
-    boxes = w.config2(base_seed=20250807 + rank, nbox=64)       # as bench.ours() draws them
+    boxes = w.uneven_batch(base_seed=20250807 + rank, nbox=64)       # as bench.ours() draws them
     bench.barrier(world)
     q.put((rank, t_max, [b["seed"] for b in boxes], len(boxes) * world / t_max))
     dist.destroy_process_group()
