@@ -72,6 +72,13 @@ def test_served_results_on_clusters_equal_solo_runs(m, h, cluster):
         assert by_id[int(rid)]["result"].tobytes() == solo[i].tobytes(), i
 
 
+def test_serve_cluster_size_is_checked(m, h):
+    """The serving grid's cluster size is 0, 1, 2, 4 or 8; anything else is rejected."""
+    for bad in (3, 16, -1):
+        with pytest.raises(m.MdeosError):
+            m.Server(h, cluster=bad)
+
+
 def test_requests_complete_before_their_launch_ends(m, h):
     """Results are reported per box: small boxes sharing a launch with one large box
     are seen long before it finishes."""
