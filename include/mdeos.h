@@ -388,11 +388,11 @@ typedef struct {
                                largest box (32768 atoms) plus the element store; creation
                                fails if the scratch alone exceeds it; 0 = no cap */
   int32_t warm;             /* 1: keep element states for warm starts (see above); 0: off */
-  int32_t cluster;          /* CTAs per thread-block cluster of the serving grid (1 = none,
-                               else a power of two up to 8): a cluster takes one request
-                               above 4096 atoms for all its CTAs (each a slab of the
-                               box's atoms) or one item of smaller boxes per CTA in
-                               rounds; large boxes finish sooner (lower p99 below
+  int32_t cluster;          /* CTAs per thread-block cluster of the serving grid (0 or 1 =
+                               none, else 2, 4 or 8): in rounds, a cluster runs one
+                               request above 4096 atoms on all its CTAs (each a slab of
+                               the box's atoms) or lets each CTA claim items of smaller
+                               boxes; large boxes finish sooner (lower p99 below
                                saturation), the rounds lower the capacity */
   size_t warm_bytes;        /* element store size; 0 = what hbm_budget_bytes leaves after the
                                scratch (1 GiB without a budget) */
