@@ -51,19 +51,27 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(mdeos_config), sizeof(mdeos_request), sizeof(mdeos_result));
   printf("%zu %zu %zu %zu\n", offsetof(mdeos_result, sigma), offsetof(mdeos_result, element_id),
          offsetof(mdeos_result, status), offsetof(mdeos_request, seed));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(mdeos_serve_config), offsetof(mdeos_serve_config, warm),
+         offsetof(mdeos_serve_config, cluster), offsetof(mdeos_serve_config, warm_bytes),
+         sizeof(mdeos_served));
   return 0;
 }
 ''')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True,
+                             check=True).stdout.split("\n")[:3]
     sizes = [int(v) for v in a.split()]
     offs = [int(v) for v in b.split()]
     assert sizes == [ctypes.sizeof(m.mdeos_config), ctypes.sizeof(m.mdeos_request),
                      ctypes.sizeof(m.mdeos_result)]
     assert offs == [m.mdeos_result.sigma.offset, m.mdeos_result.element_id.offset,
                     m.mdeos_result.status.offset, m.mdeos_request.seed.offset]
+    serve = [int(v) for v in c.split()]
+    assert serve == [ctypes.sizeof(m.mdeos_serve_config), m.mdeos_serve_config.warm.offset,
+                     m.mdeos_serve_config.cluster.offset, m.mdeos_serve_config.warm_bytes.offset,
+                     m.SERVED_DTYPE.itemsize]
 
 
 def test_create_without_gpu_fails_loudly(built_lib):
