@@ -162,6 +162,40 @@ def test_cell_list_equals_allpairs(orc):
         assert np.abs(W1 - W0).max() < 1e-11 * np.abs(W0).max()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_forces_and_virial_follow_the_box_symmetries(orc, mode):
+    """A periodic cubic box is invariant under a common translation (mod L), a cyclic
+    permutation of the axes and a mirror x -> L - x.  The energy is invariant; the
+    forces translate, permute and flip like vectors; the virial (xx, yy, zz, xy, xz,
+    yz) permutes like a tensor and its xy and xz components change sign under the
+    mirror.  An index or sign slip in the oracle's force or virial (a swapped
+    component, a wrong image near the faces) breaks one of these."""
+    x, L = _liquidish(orc, 500, 0.7, 12, amp=0.25)
+    E, f, W = orc.lj_forces(x, L, mode=mode)
+    tol_f = 1e-11 * np.abs(f).max()
+    tol_w = 1e-11 * np.abs(W).max()
+    shift = np.array([0.37, 0.21 * L, 0.93 * L])
+    Et, ft, Wt = orc.lj_forces((x + shift) % L, L, mode=mode)
+    assert abs(Et - E) < 1e-11 * abs(E)
+    assert np.abs(ft - f).max() < tol_f and np.abs(Wt - W).max() < tol_w
+    # (x, y, z) -> (y, z, x): new axis k is old axis perm[k]
+    perm = [1, 2, 0]
+    Ep, fp, Wp = orc.lj_forces(x[:, perm], L, mode=mode)
+    assert abs(Ep - E) < 1e-11 * abs(E)
+    assert np.abs(fp - f[:, perm]).max() < tol_f
+    full = lambda w: np.array([[w[0], w[3], w[4]], [w[3], w[1], w[5]], [w[4], w[5], w[2]]])
+    Mp, M = full(Wp), full(W)
+    assert np.abs(Mp - M[np.ix_(perm, perm)]).max() < tol_w
+    xm = x.copy()
+    xm[:, 0] = (L - xm[:, 0]) % L
+    Em, fm, Wm = orc.lj_forces(xm, L, mode=mode)
+    assert abs(Em - E) < 1e-11 * abs(E)
+    assert np.abs(fm[:, 0] + f[:, 0]).max() < tol_f
+    assert np.abs(fm[:, 1:] - f[:, 1:]).max() < tol_f
+    sign = np.array([1, 1, 1, -1, -1, 1])
+    assert np.abs(Wm - sign * W).max() < tol_w
+
+
 def test_multi_image_equals_replicated_box(orc):
     """A box with rc <= L < 2 rc (several images of one neighbour in range) must
     give the same energy, forces and virial per atom as the 3x3x3 replica box,
